@@ -1,0 +1,297 @@
+"""ctypes wrapper of the FP64 C oracle (test infrastructure only).
+
+Inputs arrive as float32 arrays from the shared input generators and are widened
+to float64 exactly, so the oracle and the CUDA path see the same numbers.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "dseed_oracle.c")
+_OUT_DIR = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_OUT_DIR, "libdseed_oracle.so")
+_lib = None
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int)
+
+
+class _Robot(C.Structure):
+    _fields_ = [("dh", _dp), ("lim", _dp), ("ns", C.c_int), ("sph_frame", _ip),
+                ("sph_o", _dp), ("sph_r", _dp)]
+
+
+class _CostParams(C.Structure):
+    _fields_ = [(k, C.c_double) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l")]
+
+
+class _Grid(C.Structure):
+    _fields_ = [("phi", _dp), ("origin", C.c_double * 3), ("res", C.c_double), ("n", C.c_int * 3)]
+
+
+class _Problem(C.Structure):
+    _fields_ = [("robot", C.POINTER(_Robot)), ("cp", C.POINTER(_CostParams)),
+                ("grid", C.POINTER(_Grid)), ("q_start", _dp), ("goal", _dp), ("T", C.c_int)]
+
+
+class _Opt(C.Structure):
+    _fields_ = [("iters", C.c_int), ("m", C.c_int), ("c1", C.c_double), ("max_step", C.c_double),
+                ("gamma0", C.c_double), ("alpha_min", C.c_double)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (no fast-math, no FMA contraction)."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    lib = C.CDLL(build())
+    lib.orc_fk.argtypes = [_dp, _dp, _dp]
+    lib.orc_flange_pose.argtypes = [_dp, _dp, _dp]
+    lib.orc_sphere_centres.argtypes = [C.POINTER(_Robot), _dp, _dp]
+    lib.orc_esdf_build.argtypes = [_dp, C.c_int, C.POINTER(_Grid), _dp]
+    lib.orc_esdf_lookup.argtypes = [C.POINTER(_Grid), _dp, _dp]
+    lib.orc_esdf_lookup.restype = C.c_double
+    lib.orc_cost.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+    lib.orc_cost.restype = C.c_double
+    lib.orc_cost_batch.argtypes = [C.POINTER(_Problem), C.c_int, _dp, _dp, _dp]
+    lib.orc_evaluate.argtypes = [C.POINTER(_Problem), _dp, _dp, _dp]
+    lib.orc_evaluate.restype = C.c_int
+    lib.orc_plan.argtypes = [C.POINTER(_Problem), C.c_int, C.c_int, _dp, C.POINTER(_Opt), _dp,
+                             _dp, _dp, _ip, _dp, _dp, _ip]
+    lib.orc_lbfgs_quadratic.argtypes = [_dp, _dp, C.c_int, C.POINTER(_Opt), _dp, _dp, _dp, _dp]
+    lib.orc_lbfgs_quadratic.restype = C.c_int
+    lib.orc_num_threads.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def _d(a) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _ptr(a: np.ndarray):
+    if a is None:
+        return None
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(_dp)
+    if a.dtype == np.int32:
+        return a.ctypes.data_as(_ip)
+    raise TypeError(a.dtype)
+
+
+def num_threads() -> int:
+    return int(load().orc_num_threads())
+
+
+def fk_frames(dh, q) -> np.ndarray:
+    """Frames 0..8 (base, joints 1..7, flange) as [9][4][4] homogeneous transforms."""
+    dh, q = _d(dh), _d(q)
+    out = np.zeros((9, 16))
+    load().orc_fk(_ptr(dh), _ptr(q), _ptr(out))
+    return out.reshape(9, 4, 4)
+
+
+def flange_pose(dh, q) -> np.ndarray:
+    """[N][7] flange poses (x, y, z, qw, qx, qy, qz), qw >= 0, for q [N][7]."""
+    dh = _d(dh)
+    q = _d(q).reshape(-1, 7)
+    out = np.zeros((q.shape[0], 7))
+    lib = load()
+    for i in range(q.shape[0]):
+        row = np.ascontiguousarray(q[i])
+        o = np.zeros(7)
+        lib.orc_flange_pose(_ptr(dh), _ptr(row), _ptr(o))
+        out[i] = o
+    return out
+
+
+def _grid_struct(grid, phi: Optional[np.ndarray]) -> _Grid:
+    g = _Grid()
+    g.phi = _ptr(phi) if phi is not None else None
+    for a in range(3):
+        g.origin[a] = float(grid.origin[a])
+        g.n[a] = int(grid.n[a])
+    g.res = float(grid.res)
+    return g
+
+
+def esdf_build(cuboids, grid) -> np.ndarray:
+    """phi [nz][ny][nx] float64 of a union of cuboids (rows cx,cy,cz,hx,hy,hz)."""
+    boxes = _d(cuboids).reshape(-1, 6)
+    nx, ny, nz = (int(v) for v in grid.n)
+    out = np.zeros((nz, ny, nx))
+    g = _grid_struct(grid, None)
+    load().orc_esdf_build(_ptr(boxes) if boxes.size else None, boxes.shape[0], C.byref(g), _ptr(out))
+    return out
+
+
+def esdf_lookup(phi: np.ndarray, grid, p) -> tuple:
+    """Trilinear value and gradient of phi at points p [N][3]."""
+    phi = _d(phi)
+    g = _grid_struct(grid, phi)
+    p = _d(p).reshape(-1, 3)
+    vals = np.zeros(p.shape[0])
+    grads = np.zeros((p.shape[0], 3))
+    lib = load()
+    for i in range(p.shape[0]):
+        row = np.ascontiguousarray(p[i])
+        gr = np.zeros(3)
+        vals[i] = lib.orc_esdf_lookup(C.byref(g), _ptr(row), _ptr(gr))
+        grads[i] = gr
+    return vals, grads
+
+
+def lbfgs_quadratic(A, b, x0, opt) -> tuple:
+    """L-BFGS on 1/2 x^T A x - b^T x; returns (x, f, trace of accepted f, accepts)."""
+    A, b, x0 = _d(A), _d(b), _d(x0)
+    n = b.shape[0]
+    o = _opt_struct(opt)
+    x = np.zeros(n)
+    f = np.zeros(1)
+    tr = np.zeros(o.iters)
+    acc = load().orc_lbfgs_quadratic(_ptr(A), _ptr(b), n, C.byref(o), _ptr(x0), _ptr(x), _ptr(f), _ptr(tr))
+    return x, float(f[0]), tr, int(acc)
+
+
+def _opt_struct(opt) -> _Opt:
+    o = _Opt()
+    o.iters = int(opt.iters)
+    o.m = int(opt.m)
+    o.c1 = float(opt.c1)
+    o.max_step = float(opt.max_step)
+    o.gamma0 = float(opt.gamma0)
+    o.alpha_min = float(opt.alpha_min)
+    return o
+
+
+class Oracle:
+    """Problems of one workload: robot, cost parameters, per-scene ESDFs (built by
+    the oracle itself from the cuboids), starts and goals."""
+
+    def __init__(self, robot, cost, grids: Sequence, cuboids: Sequence, T: int):
+        self._lib = load()
+        self.T = int(T)
+        self._keep = []
+        self.dh = _d(robot.dh)
+        self.lim = _d(robot.limits)
+        self.sph_frame = np.ascontiguousarray(robot.sph_frame, dtype=np.int32)
+        self.sph_o = _d(robot.sph_o)
+        self.sph_r = _d(robot.sph_r)
+        self.robot = _Robot(_ptr(self.dh), _ptr(self.lim), int(self.sph_r.shape[0]),
+                            _ptr(self.sph_frame), _ptr(self.sph_o), _ptr(self.sph_r))
+        self.cp = _CostParams(*[float(v) for v in cost.as_array()])
+        self.grids_meta = list(grids)
+        self.phis = [esdf_build(c, g) for c, g in zip(cuboids, grids)]
+        self.grids = [_grid_struct(g, phi) for g, phi in zip(self.grids_meta, self.phis)]
+
+    # -- problem descriptors ------------------------------------------------
+    def _problem(self, scene: int, q_start, goal, T: Optional[int] = None) -> _Problem:
+        qs = _d(q_start).reshape(7)
+        gl = _d(goal).reshape(7) if goal is not None else np.array([0, 0, 0, 1, 0, 0, 0], np.float64)
+        self._keep.extend([qs, gl])
+        return _Problem(C.pointer(self.robot), C.pointer(self.cp), C.pointer(self.grids[scene]),
+                        _ptr(qs), _ptr(gl), int(self.T if T is None else T))
+
+    def _problems(self, scenes, q_start, goal, T=None):
+        arr = (_Problem * len(scenes))()
+        for i, s in enumerate(scenes):
+            arr[i] = self._problem(int(s), q_start[i], goal[i], T)
+        return arr
+
+    # -- kinematics -----------------------------------------------------------
+    def sphere_centres(self, q) -> np.ndarray:
+        q = _d(q).reshape(-1, 7)
+        out = np.zeros((q.shape[0], self.robot.ns, 3))
+        for i in range(q.shape[0]):
+            row = np.ascontiguousarray(q[i])
+            o = np.zeros((self.robot.ns, 3))
+            self._lib.orc_sphere_centres(C.byref(self.robot), _ptr(row), _ptr(o))
+            out[i] = o
+        return out
+
+    def flange_pose(self, q) -> np.ndarray:
+        return flange_pose(self.dh, q)
+
+    # -- cost -----------------------------------------------------------------
+    def cost(self, scene: int, q_start, goal, x, grad: bool = True, terms: bool = False):
+        """Cost (and gradient) of trajectories x [B][T][7] of one problem."""
+        x = _d(x)
+        T = x.shape[-2]
+        x = x.reshape(-1, T, 7)
+        pb = self._problem(scene, q_start, goal, T)
+        B = x.shape[0]
+        cost = np.zeros(B)
+        g = np.zeros_like(x) if grad else None
+        if terms:
+            tr = np.zeros((B, 4))
+            for b in range(B):
+                xb = np.ascontiguousarray(x[b])
+                gb = np.zeros_like(xb) if grad else None
+                t4 = np.zeros(4)
+                cost[b] = self._lib.orc_cost(C.byref(pb), _ptr(xb), _ptr(gb), _ptr(t4))
+                tr[b] = t4
+                if grad:
+                    g[b] = gb
+            return (cost, g, tr) if grad else (cost, tr)
+        self._lib.orc_cost_batch(C.byref(pb), B, _ptr(x), _ptr(cost), _ptr(g))
+        return (cost, g) if grad else cost
+
+    def evaluate(self, scene: int, q_start, goal, x, thr=None):
+        """Success flags [B] and metrics [B][7] (see orc_evaluate)."""
+        from_thr = _d(thr if thr is not None else [0.005, 2.86 * np.pi / 180.0])
+        x = _d(x)
+        T = x.shape[-2]
+        x = x.reshape(-1, T, 7)
+        pb = self._problem(scene, q_start, goal, T)
+        ok = np.zeros(x.shape[0], np.int32)
+        met = np.zeros((x.shape[0], 7))
+        for b in range(x.shape[0]):
+            xb = np.ascontiguousarray(x[b])
+            mb = np.zeros(7)
+            ok[b] = self._lib.orc_evaluate(C.byref(pb), _ptr(xb), _ptr(from_thr), _ptr(mb))
+            met[b] = mb
+        return ok.astype(bool), met
+
+    def clearance(self, scene: int, q) -> np.ndarray:
+        """min over spheres of (phi - r) for single configurations q [N][7]."""
+        q = _d(q).reshape(-1, 1, 7)
+        _, met = self.evaluate(scene, q[0, 0], None, q)
+        return met[:, 0]
+
+    # -- optimiser ------------------------------------------------------------
+    def plan(self, scenes, q_start, goal, seeds, opt, thr=None, trace: bool = False) -> dict:
+        """Optimise seeds [P][S][T][7]; scenes[p] indexes the scene of problem p."""
+        seeds = _d(seeds)
+        P, S, T = seeds.shape[0], seeds.shape[1], seeds.shape[2]
+        probs = self._problems(scenes, q_start, goal, T)
+        o = _opt_struct(opt)
+        th = _d(thr if thr is not None else [0.005, 2.86 * np.pi / 180.0])
+        x = np.zeros_like(seeds)
+        f = np.zeros((P, S))
+        ok = np.zeros((P, S), np.int32)
+        met = np.zeros((P, S, 7))
+        tr = np.zeros((P, S, o.iters)) if trace else None
+        best = np.zeros(P, np.int32)
+        self._lib.orc_plan(probs, P, S, _ptr(seeds), C.byref(o), _ptr(th), _ptr(x), _ptr(f),
+                           _ptr(ok), _ptr(met), _ptr(tr), _ptr(best))
+        out = dict(traj=x, cost=f, success=ok.astype(bool), metrics=met, best=best)
+        if trace:
+            out["trace"] = tr
+        return out
