@@ -1,0 +1,335 @@
+"""Benchmark of the seed-parallel trajectory optimiser on one GB300 (or N, as
+independent replicas under torchrun).
+
+One step = the whole hot path over one batch: the brute-force ESDF build of
+every scene, then the fused optimiser (FK -> spheres -> ESDF trilinear + hinge,
+smoothness, goal, limits, hand-written adjoint, L-BFGS update; `iters` times)
+and the success test / best-seed selection.  Default workload: 256 problems,
+each with its own shelf scene (20-60 cuboids, 128^3 ESDF at 1 cm), 64 seeds x
+32 waypoints, 100 iterations.  Metric: seed-timestep cost+grad evaluations per
+second = P * S * T * iters / step time.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
+a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, HERE)
+
+from paper_2410_16727_gb300 import inputs as I  # noqa: E402
+
+METRIC = "seed-timestep cost+grad evals/s"
+UNIT = "ST-evals/s"
+# FP32 operations per seed-timestep evaluation of the fused kernel (cost +
+# adjoint + L-BFGS share), counted from the source; see the design doc.
+FLOP_PER_ST = 5800.0
+# 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="dseed", choices=["dseed", "reference"])
+    ap.add_argument("--workload", default="batched", choices=list(I.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.path = tempfile.mktemp(suffix=".csv")
+        self.proc = None
+        self.gpu = gpu_index
+
+    def __enter__(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(parts)
+                except ValueError:
+                    pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args, rank: int, world: int):
+    import torch
+    from paper_2410_16727_gb300 import api, binding as B
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    spec = I.WORKLOADS[args.workload]
+    robot = I.make_robot()
+    # each rank plans its own problems (replicas of the workload with different seeds)
+    cub, grids = I.make_scenes(spec, seed_offset=rank)
+    planner = api.Planner(robot, I.CostParams(), I.OptParams(iters=spec.iters), dev)
+    planner.set_scenes(cub, grids)
+    clear_fn, pose_fn = api.device_workload_fns(planner)
+    wl = I.build_workload(spec, cub, grids, clear_fn, pose_fn, seed_offset=rank)
+    P, S, T, iters = wl.P, wl.S, wl.T, wl.opt.iters
+    st_evals = P * S * T * iters
+
+    # resident device inputs and outputs
+    batch = planner.batch(wl.q_start, wl.goal, wl.scene_of_problem, S, T)
+    seeds = torch.as_tensor(wl.seeds).to(dev)
+    cub_dev = [torch.as_tensor(c).to(dev) for c in cub]
+    esdfs = planner.esdfs
+    ws = planner.workspace(batch)
+    out = dict(traj=torch.empty((P, S, T, 7), device=dev), cost=torch.empty((P, S), device=dev),
+               success=torch.empty((P, S), dtype=torch.uint8, device=dev),
+               metrics=torch.empty((P, S, B.N_METRICS), device=dev),
+               best=torch.empty((P,), dtype=torch.int32, device=dev))
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(ev=None):
+        if ev:
+            ev[0].record(stream)
+        for c, g, e in zip(cub_dev, grids, esdfs):
+            B.scene_build_esdf(c, g, e)
+        if ev:
+            ev[1].record(stream)
+        B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
+        if ev:
+            ev[2].record(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    sampler = ClockSampler(local)
+    barrier()
+    with sampler:
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()      # L2 flush between steps (outside the events)
+            step(evs[k])
+        barrier()
+        wall = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    esdf_ms = [e[0].elapsed_time(e[1]) for e in evs]
+    plan_ms = [e[1].elapsed_time(e[2]) for e in evs]
+    step_ms = [a + b for a, b in zip(esdf_ms, plan_ms)]
+    ms = sum(step_ms) / len(step_ms)
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    success_rate = float(out["success"].float().mean())
+    solved = float((out["best"] >= 0).float().mean())
+
+    # end to end through the public API with host buffers: H2D of the step's
+    # inputs (cuboids, starts, goals, scene ids, seeds) from pinned memory, the
+    # step, D2H of trajectories, costs, success flags and best seeds
+    h_cub = [torch.as_tensor(c).pin_memory() for c in cub]
+    h_q = torch.as_tensor(wl.q_start).pin_memory()
+    h_goal = torch.as_tensor(wl.goal).pin_memory()
+    h_sc = torch.as_tensor(wl.scene_of_problem).pin_memory()
+    h_seeds = torch.as_tensor(wl.seeds).pin_memory()
+    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "metrics"}
+    d_q = batch.q_start
+    d_goal = batch.goal
+    d_sc = batch.scene_of_problem
+    h2d = sum(t.numel() * t.element_size() for t in h_cub) + sum(
+        t.numel() * t.element_size() for t in (h_q, h_goal, h_sc, h_seeds))
+    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+
+    def e2e_step():
+        for hc, dc in zip(h_cub, cub_dev):
+            dc.copy_(hc, non_blocking=True)
+        d_q.copy_(h_q, non_blocking=True)
+        d_goal.copy_(h_goal, non_blocking=True)
+        d_sc.copy_(h_sc, non_blocking=True)
+        seeds.copy_(h_seeds, non_blocking=True)
+        for c, g, e in zip(cub_dev, grids, esdfs):
+            B.scene_build_esdf(c, g, e)
+        B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
+        for k, v in h_out.items():
+            v.copy_(out[k], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = []
+    for _ in range(max(2, args.steps)):
+        flush.zero_()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms.append(a.elapsed_time(b))
+    e2e_ms = sum(e_ms) / len(e_ms)
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    plan_avg = sum(plan_ms) / len(plan_ms)
+    esdf_avg = sum(esdf_ms) / len(esdf_ms)
+    achieved = FLOP_PER_ST * st_evals / (plan_avg * 1e-3) / 1e12
+    res = dict(
+        metric=METRIC, value=st_evals * world / (ms * 1e-3), unit=UNIT, n_gpus=world, steps=args.steps,
+        warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
+        dtype="f32", data="synthetic",
+        config={"workload": f"{spec.name}: {P} problems x {S} seeds x {T} waypoints, {iters} L-BFGS iterations, "
+                            f"{spec.scene} scenes, ESDF {spec.grid.n[0]}^3 at {spec.grid.res * 100:g} cm",
+                "problems": P, "seeds": S, "waypoints": T, "iters": iters, "scenes": len(cub),
+                "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
+        plans_per_s=P * world / (ms * 1e-3),
+        breakdown_ms={"esdf_build": esdf_avg, "plan": plan_avg},
+        success_rate=success_rate, problems_solved=solved,
+        wall_s_timed=wall,
+        gpu_launches=len(cub) + 2,
+        e2e={"value": st_evals * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
+                  "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+                  "traffic": None},
+        clocks=sampler.summary(),
+    )
+    return res, wl
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(spec, budget_s: float, seed_offset: int = 0):
+    """Time the FP64 oracle on whole problems of the workload (ESDF build of the
+    problem's scene + all seeds x iterations + success test) until the budget is
+    spent.  Inputs are drawn with the oracle's own callbacks."""
+    import oracle
+    robot = I.make_robot()
+    done = 0
+    t_total = 0.0
+    k = 0
+    chunk = max(1, min(spec.n_problems, oracle.num_threads() // 4 or 1))
+    cub_all, grids_all = I.make_scenes(spec, seed_offset=seed_offset)
+    while t_total < budget_s and k < spec.n_problems:
+        idx = list(range(k, min(k + chunk, spec.n_problems)))
+        scenes = sorted({int(p * len(cub_all) // spec.n_problems) for p in idx})
+        t0 = time.perf_counter()
+        orc = oracle.Oracle(robot, I.CostParams(), [grids_all[s] for s in scenes], [cub_all[s] for s in scenes],
+                            T=spec.T)
+        t_esdf = time.perf_counter() - t0
+        # problem generation (not timed) draws each problem's own stream, as in the full workload
+        wl = I.build_workload(spec, [cub_all[s] for s in scenes], [grids_all[s] for s in scenes],
+                              orc.clearance, orc.flange_pose, n_problems=len(idx), seed_offset=seed_offset)
+        t0 = time.perf_counter()
+        orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
+        t_total += t_esdf + (time.perf_counter() - t0)
+        done += len(idx) * spec.S * spec.T * spec.iters
+        k += len(idx)
+    return done / t_total, k, t_total, oracle.num_threads()
+
+
+def run_reference(args, rank: int, world: int):
+    spec = I.WORKLOADS[args.workload]
+    vals = []
+    sample = None
+    for _ in range(args.warmup):
+        oracle_sample(spec, min(2.0, args.cpu_seconds / 4))
+    for _ in range(args.steps):
+        v, k, t, cores = oracle_sample(spec, args.cpu_seconds / max(1, args.steps) * 2)
+        vals.append(v)
+        sample = f"{k} of {spec.n_problems} problems (ESDF build + {spec.S} seeds x {spec.iters} iterations each)"
+    v = statistics.mean(vals)
+    st_evals = spec.n_problems * spec.S * spec.T * spec.iters
+    return dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=world, steps=args.steps,
+                warmup=args.warmup, ms_per_step=st_evals / v * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic",
+                config={"workload": spec.name, "problems": spec.n_problems, "seeds": spec.S, "waypoints": spec.T,
+                        "iters": spec.iters},
+                cpu_baseline={"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    res, wl = run_gpu(args, rank, world)
+    if rank == 0 and not args.no_cpu_baseline:
+        v, k, t, cores = oracle_sample(I.WORKLOADS[args.workload], args.cpu_seconds)
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": f"{k} of {wl.P} problems (ESDF build + {wl.S} seeds x {wl.opt.iters} "
+                                         f"iterations each), {t:.1f} s"}
+    if rank == 0:
+        print(json.dumps(res), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,261 @@
+/*
+ * dseed.h -- C ABI of libdseed: seed-parallel trajectory optimisation for a
+ * 7-DoF arm on one NVIDIA GB300 (sm_103a).
+ *
+ * The library optimises many seed trajectories per planning problem in
+ * parallel, as the motion optimiser of the paper does (Sec. 4.4
+ * "Optimization", Appendix A.5 "Optimization Problem"):
+ *
+ *     min over x_1..x_T   C_goal(X_d, FK(x_T)) + C_smooth + C_world + C_limit
+ *
+ * with y_0 = q_start held fixed.  Per waypoint t and collision sphere k the
+ * world cost is w_c * max(0, r_k + eta - phi(c_k)), phi the trilinear
+ * interpolation of a voxel ESDF (Euclidean signed distance field) at the
+ * sphere centre c_k placed by forward kinematics; C_smooth is the weighted sum
+ * of squared backward-difference velocities, accelerations and jerks at
+ * spacing dt (start at rest: y_-1 = y_-2 = y_0); C_goal = w_p |p - p*|^2 +
+ * w_R (1 - <q, q*>^2) on the flange pose at waypoint T; C_limit is a quadratic
+ * penalty outside the joint limits.  Each iteration evaluates cost and
+ * gradient (hand-written adjoint) of every seed and takes one L-BFGS step
+ * with Armijo accept/reject.  Success (Sec. 5.1): collision free, translation
+ * error below delta_t, rotation error below delta_r, within the limits.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are device pointers, *_host host pointers; all
+ *     other pointers are host pointers to small descriptors, read during the
+ *     call and not retained.
+ *   - The caller owns every buffer.  Only dseed_robot_create allocates (a
+ *     small host object).  No call allocates device memory.
+ *   - Calls taking a stream are asynchronous and stream ordered: they enqueue
+ *     kernels on `stream` and return; outputs are valid once the stream has
+ *     reached that point.  Inputs must stay valid until then.
+ *   - Return 0 (DSEED_OK) on success or a negative status; the thread-local
+ *     message of the last failure is returned by dseed_last_error().  Errors of
+ *     kernels that have already been enqueued surface as DSEED_ECUDA on a
+ *     later call or on the caller's stream synchronisation.
+ *   - Arrays are dense, row-major, float32 unless stated, last index fastest.
+ *     Trajectories are [P][S][T][7]: problem, seed, waypoint (t = 1..T), joint.
+ *     Poses are [x, y, z, qw, qx, qy, qz] (metres, unit quaternion; the
+ *     library normalises goal quaternions and treats q and -q alike).
+ */
+#ifndef DSEED_H
+#define DSEED_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DSEED_ABI_VERSION 1
+
+#define DSEED_MAX_SPHERES 64    /* collision spheres per robot */
+#define DSEED_MAX_T 128         /* waypoints per trajectory */
+#define DSEED_MAX_HISTORY 8     /* L-BFGS history length m */
+#define DSEED_ESDF_FAR 1000.0f  /* ESDF value of a scene with no cuboid (m) */
+
+/* status codes */
+#define DSEED_OK 0
+#define DSEED_EINVAL (-1)       /* bad argument: null pointer, size out of range, NaN parameter */
+#define DSEED_ENOMEM (-2)       /* host allocation failed, or a caller buffer is too small */
+#define DSEED_ECUDA (-3)        /* a CUDA call or kernel launch failed (message has the CUDA error) */
+
+/* Robot: a serial 7-joint arm in modified Denavit-Hartenberg form plus a
+ * fixed flange frame, and its collision spheres.  Frame i (i = 1..7) turns
+ * with joint i; frame 8 is the flange:
+ *   T_i = T_{i-1} RotX(alpha_i) TransX(a_i) RotZ(q_i + theta_offset_i) TransZ(d_i)
+ * (the forward kinematics FK of Eq. 2 and of C_goal in Appendix A.5). */
+typedef struct {
+    float dh[8][4];                          /* rows i = 1..8: a, d, alpha, theta_offset */
+    float limits[7][2];                      /* lower, upper (rad) */
+    int   n_spheres;                         /* 1..DSEED_MAX_SPHERES */
+    int   sphere_frame[DSEED_MAX_SPHERES];   /* frame 1..8 the sphere is fixed to */
+    float sphere_offset[DSEED_MAX_SPHERES][3]; /* centre in that frame (m) */
+    float sphere_radius[DSEED_MAX_SPHERES];  /* radius (m), > 0 */
+} DseedRobotDesc;
+
+typedef struct DseedRobot DseedRobot;        /* opaque, host memory */
+
+/* Voxel grid: voxel (i, j, k) has its centre at origin + (i, j, k) * res +
+ * res / 2 and is stored at index ((k * ny) + j) * nx + i.  nx, ny, nz >= 2. */
+typedef struct {
+    float origin[3];
+    float res;
+    int   nx, ny, nz;
+} DseedGrid;
+
+/* One scene as the optimiser reads it: its ESDF on the device and the grid. */
+typedef struct {
+    const float *esdf_dev;                   /* [nz][ny][nx] */
+    DseedGrid    grid;
+} DseedScene;
+
+/* Cost weights (Appendix A.5 objective; values are the caller's choice). */
+typedef struct {
+    float w_c;    /* collision hinge weight */
+    float eta;    /* collision margin (m) */
+    float dt;     /* waypoint spacing (s) */
+    float w_v, w_a, w_j;   /* squared velocity / acceleration / jerk weights */
+    float w_p;    /* goal position weight */
+    float w_R;    /* goal orientation weight */
+    float w_l;    /* joint-limit weight */
+} DseedCostParams;
+
+/* L-BFGS settings.  One iteration = one cost+gradient evaluation of the trial
+ * point followed by one update: accept the trial when f_trial <= f + c1 *
+ * g^T (x_trial - x) (always on the first evaluation), pushing (s, y) into the
+ * history when s^T y > 1e-10 |s| |y|, and doubling alpha up to 1; otherwise
+ * halve alpha (below alpha_min: clear the history, alpha = 1).  Then
+ * d = -H g by the two-loop recursion (H0 = gamma I with gamma = s^T y / y^T y
+ * of the newest pair, gamma0 when the history is empty; d = -g when not a
+ * descent direction), step = alpha d scaled so that max |step| <= max_step,
+ * next trial = x + step.  The result is the last accepted point. */
+typedef struct {
+    int   iters;      /* evaluations, >= 1 */
+    int   m;          /* history length, 1..DSEED_MAX_HISTORY */
+    float c1;
+    float max_step;   /* rad */
+    float gamma0;
+    float alpha_min;
+} DseedOptParams;
+
+/* Shape and settings of one batch: P problems of S seeds of T waypoints. */
+typedef struct {
+    int P;            /* >= 0 */
+    int S;            /* >= 1 */
+    int T;            /* 1..DSEED_MAX_T */
+    DseedCostParams cost;
+    DseedOptParams  opt;
+    float delta_t;    /* success: translation error below (m), Sec. 5.1 uses 0.005 */
+    float delta_r;    /* success: rotation error below (rad), Sec. 5.1 uses 2.86 deg */
+} DseedPlanDesc;
+
+/* The problems of a batch, all in device memory. */
+typedef struct {
+    const float      *q_start_dev;            /* [P][7] y_0 */
+    const float      *goal_dev;               /* [P][7] goal flange pose X_d */
+    const int        *scene_of_problem_dev;   /* [P] index into scenes_dev */
+    const DseedScene *scenes_dev;             /* [n_scenes] */
+    int               n_scenes;
+} DseedProblems;
+
+/* Per-trajectory metrics written by dseed_evaluate (and by the plan):
+ * min over waypoints and spheres of phi(c_k) - r_k, translation error |p - p*|,
+ * rotation error (rad), max |jerk| over waypoints and joints (Appendix A.6),
+ * worst joint-limit violation (rad), total cost, 1 if collision free else 0. */
+#define DSEED_N_METRICS 7
+
+/* ---------------------------------------------------------------- basics */
+
+int dseed_abi_version(void);
+const char *dseed_last_error(void);
+
+/* Copy and check a robot description.  *out receives a handle owned by the
+ * caller until dseed_robot_destroy.  EINVAL on a null pointer, a sphere count
+ * outside 1..DSEED_MAX_SPHERES, a frame outside 1..8, a non-positive radius,
+ * lower > upper or a non-finite entry. */
+int  dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out);
+void dseed_robot_destroy(DseedRobot *robot);
+
+/* ------------------------------------------------------------------ ESDF */
+
+/* Per-voxel brute-force ESDF of a union of axis-aligned cuboids (the
+ * optimiser's collision field, Sec. 4.4).  For every voxel centre p:
+ *   phi(p) = min(DSEED_ESDF_FAR, min_k sdf_k(p)),
+ *   sdf_k(p) = |max(|p - c_k| - h_k, 0)| + min(max_i(|p - c_k|_i - h_k,i), 0),
+ * positive outside all cuboids, minus the deepest penetration inside one.
+ * cuboids_dev: [n][6] = cx, cy, cz, hx, hy, hz (centre, half extents, m);
+ * may be NULL when n == 0.  esdf_dev: [nz][ny][nx], written in full.
+ * EINVAL on n < 0, a grid dimension < 2, res <= 0 or a null output. */
+int dseed_scene_build_esdf(const float *cuboids_dev, int n, const DseedGrid *grid,
+                           float *esdf_dev, cudaStream_t stream);
+
+/* ------------------------------------------------------------ kinematics */
+
+/* Forward kinematics of N configurations q_dev [N][7]: flange poses
+ * pose_dev [N][7] (qw >= 0) and, when spheres_dev is not NULL, the sphere
+ * centres [N][n_spheres][3] in the order of the robot description. */
+int dseed_fk(const DseedRobot *robot, const float *q_dev, int N, float *pose_dev,
+             float *spheres_dev, cudaStream_t stream);
+
+/* ---------------------------------------------------------- cost, adjoint */
+
+/* Cost of trajectories x_dev [P][S][T][7] of the problems in `pr`:
+ * cost_dev [P][S]; terms_dev (optional) [P][S][4] = C_world, C_smooth,
+ * C_goal, C_limit. */
+int dseed_cost(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+               const float *x_dev, float *cost_dev, float *terms_dev, cudaStream_t stream);
+
+/* Cost and its gradient dC/dx by the hand-written adjoint (reverse pass
+ * through the hinge, the trilinear lookup, the sphere placement and the
+ * kinematic chain, plus the transposed finite-difference stencils):
+ * cost_dev [P][S], grad_dev [P][S][T][7].  grad_scale_dev (optional) [P][S]
+ * multiplies each trajectory's gradient (the incoming adjoint of a
+ * reverse-mode caller). */
+int dseed_cost_grad(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                    const float *x_dev, const float *grad_scale_dev, float *cost_dev,
+                    float *grad_dev, cudaStream_t stream);
+
+/* Success flags success_dev [P][S] (1 = success) and metrics_dev (optional)
+ * [P][S][DSEED_N_METRICS] of trajectories x_dev [P][S][T][7]. */
+int dseed_evaluate(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                   const float *x_dev, uint8_t *success_dev, float *metrics_dev,
+                   cudaStream_t stream);
+
+/* ---------------------------------------------------------------- L-BFGS */
+
+/* L-BFGS state of B = P * S seeds of n = 7 T unknowns in one caller buffer.
+ * Byte offsets of the arrays inside it (all 256-byte aligned): */
+typedef struct {
+    size_t x;         /* float [B][n] accepted point */
+    size_t g;         /* float [B][n] gradient at x */
+    size_t x_trial;   /* float [B][n] next trial point (read by the caller's evaluation) */
+    size_t s;         /* float [B][m][n] history s_i */
+    size_t y;         /* float [B][m][n] history y_i */
+    size_t rho;       /* float [B][m] 1 / s_i^T y_i */
+    size_t f;         /* float [B] cost at x (+inf before the first evaluation) */
+    size_t alpha;     /* float [B] step length */
+    size_t gts;       /* float [B] g^T (x_trial - x) */
+    size_t yy;        /* float [B] y^T y of the newest pair */
+    size_t meta;      /* int [B][4] history count, newest slot, first-evaluation flag, accepts */
+    size_t total;     /* bytes of the whole state */
+} DseedLbfgsLayout;
+
+int dseed_lbfgs_layout(const DseedPlanDesc *desc, DseedLbfgsLayout *out);
+
+/* Start every seed at x0_dev [B][n]: x_trial = x0, f = +inf, alpha = 1, empty
+ * history.  state_dev: caller buffer of at least layout.total bytes. */
+int dseed_lbfgs_init(const DseedPlanDesc *desc, const float *x0_dev, void *state_dev,
+                     cudaStream_t stream);
+
+/* One L-BFGS update (K4) of every seed, given the cost f_trial_dev [B] and
+ * gradient g_trial_dev [B][n] of the current trial point: accept/reject, history
+ * update, two-loop direction, next trial point (see DseedOptParams). */
+int dseed_lbfgs_step(const DseedPlanDesc *desc, const float *f_trial_dev,
+                     const float *g_trial_dev, void *state_dev, cudaStream_t stream);
+
+/* ------------------------------------------------------------------ plan */
+
+/* Bytes of device workspace dseed_plan_batch needs for `desc`. */
+int dseed_plan_workspace_bytes(const DseedPlanDesc *desc, size_t *bytes);
+
+/* Optimise every seed of every problem for desc->opt.iters iterations, on
+ * the device in one pass, then test success.
+ * seeds_dev [P][S][T][7] initial trajectories; workspace_dev at least
+ * dseed_plan_workspace_bytes (256-byte aligned; contents need not be set).
+ * Outputs: traj_dev [P][S][T][7] last accepted point of each seed, cost_dev
+ * [P][S] its cost, success_dev [P][S] (1 = success), metrics_dev (optional)
+ * [P][S][DSEED_N_METRICS], best_dev [P] index of the lowest-cost successful
+ * seed (ties -> lowest index), -1 when no seed succeeds.  traj_dev may alias
+ * seeds_dev. */
+int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                     const float *seeds_dev, void *workspace_dev, size_t workspace_bytes,
+                     float *traj_dev, float *cost_dev, uint8_t *success_dev, float *metrics_dev,
+                     int *best_dev, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DSEED_H */

@@ -1,0 +1,126 @@
+"""User-level API over the C ABI: scenes, problem batches, planning and an
+autograd wrapper of the cost.  Argument marshalling only; the arithmetic runs
+in libdseed's kernels."""
+from __future__ import annotations
+
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import inputs as I
+
+
+class Batch:
+    """Device copies of a batch of problems plus the C descriptors that point at them."""
+
+    def __init__(self, q_start, goal, scene_of_problem, scenes: B.SceneTable, S: int, T: int,
+                 cost: I.CostParams, opt: Optional[I.OptParams] = None, device="cuda",
+                 delta_t: float = I.DELTA_T, delta_r: float = I.DELTA_R):
+        dev = torch.device(device)
+        self.q_start = _to(q_start, torch.float32, dev)
+        self.goal = _to(goal, torch.float32, dev)
+        self.scene_of_problem = _to(scene_of_problem, torch.int32, dev)
+        self.scenes = scenes
+        self.P = int(self.q_start.shape[0])
+        self.S, self.T = int(S), int(T)
+        self.desc = B.plan_desc(self.P, self.S, self.T, cost, opt, delta_t, delta_r)
+        self.pr = B.make_problems(self.q_start, self.goal, self.scene_of_problem, scenes)
+        self.device = dev
+
+
+def _to(a, dtype, dev):
+    if isinstance(a, torch.Tensor):
+        return a.to(device=dev, dtype=dtype, non_blocking=True).contiguous()
+    return torch.as_tensor(np.ascontiguousarray(a)).to(device=dev, dtype=dtype).contiguous()
+
+
+class CostFn(torch.autograd.Function):
+    """cost [P][S] of x [P][S][T][7]; backward runs the adjoint kernel with the
+    incoming gradient as per-trajectory scale (forward state is recomputed)."""
+
+    @staticmethod
+    def forward(ctx, x, robot: B.Robot, batch: Batch):
+        x = x.contiguous()
+        ctx.save_for_backward(x)
+        ctx.robot, ctx.batch = robot, batch
+        return B.cost(robot, batch.desc, batch.pr, x)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (x,) = ctx.saved_tensors
+        _, g = B.cost_grad(ctx.robot, ctx.batch.desc, ctx.batch.pr, x,
+                           grad_scale=grad_out.contiguous().to(torch.float32))
+        return g, None, None
+
+
+def trajectory_cost(x: torch.Tensor, robot: B.Robot, batch: Batch) -> torch.Tensor:
+    return CostFn.apply(x, robot, batch)
+
+
+class Planner:
+    """Robot + resident scenes; plans batches of problems with the fused optimiser."""
+
+    def __init__(self, robot: I.Robot, cost: Optional[I.CostParams] = None,
+                 opt: Optional[I.OptParams] = None, device="cuda"):
+        self.device = torch.device(device)
+        self.robot_desc = robot
+        self.robot = B.Robot(robot)
+        self.cost = cost or I.CostParams()
+        self.opt = opt or I.OptParams()
+        self.esdfs: List[torch.Tensor] = []
+        self.grids: List = []
+        self.table: Optional[B.SceneTable] = None
+        self._ws: Optional[torch.Tensor] = None
+
+    # -- scenes ---------------------------------------------------------------
+    def set_scenes(self, cuboids: Sequence, grids: Sequence, out: Optional[List[torch.Tensor]] = None):
+        """Build (or rebuild in place, when `out` is given) one ESDF per scene on the device."""
+        esdfs = []
+        for i, (c, g) in enumerate(zip(cuboids, grids)):
+            ct = _to(c, torch.float32, self.device).reshape(-1, 6)
+            esdfs.append(B.scene_build_esdf(ct, g, out[i] if out is not None else None))
+        self.esdfs, self.grids = esdfs, list(grids)
+        self.table = B.SceneTable(esdfs, grids, self.device)
+        return esdfs
+
+    # -- kinematics -----------------------------------------------------------
+    def fk(self, q, spheres: bool = False):
+        return B.fk(self.robot, _to(q, torch.float32, self.device).reshape(-1, 7), spheres)
+
+    def clearance(self, scene: int, q) -> torch.Tensor:
+        """min over spheres of (phi - r) of single configurations q [N][7] in one scene."""
+        q = _to(q, torch.float32, self.device).reshape(-1, 7)
+        N = q.shape[0]
+        batch = Batch(q, torch.tensor([[0, 0, 0, 1, 0, 0, 0]], dtype=torch.float32).expand(N, 7).contiguous(),
+                      torch.full((N,), scene, dtype=torch.int32), self.table, 1, 1, self.cost, None, self.device)
+        _, met = B.evaluate(self.robot, batch.desc, batch.pr, q.reshape(N, 1, 1, 7))
+        return met[:, 0, 0]
+
+    # -- planning -------------------------------------------------------------
+    def batch(self, q_start, goal, scene_of_problem, S: int, T: int) -> Batch:
+        return Batch(q_start, goal, scene_of_problem, self.table, S, T, self.cost, self.opt, self.device)
+
+    def workspace(self, batch: Batch) -> torch.Tensor:
+        need = B.plan_workspace_bytes(batch.desc)
+        if self._ws is None or self._ws.numel() < need:
+            self._ws = B.alloc_workspace(need, self.device)
+        return self._ws
+
+    def plan(self, batch: Batch, seeds, out: Optional[dict] = None) -> dict:
+        seeds = _to(seeds, torch.float32, self.device)
+        return B.plan_batch(self.robot, batch.desc, batch.pr, seeds, self.workspace(batch), out)
+
+
+def device_workload_fns(planner: Planner):
+    """clearance_fn / pose_fn for inputs.build_workload computed by the CUDA path."""
+
+    def clearance(scene, q):
+        return planner.clearance(scene, q).cpu().numpy()
+
+    def pose(q):
+        return planner.fk(q).cpu().numpy()
+
+    return clearance, pose

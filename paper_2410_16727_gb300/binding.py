@@ -1,0 +1,351 @@
+"""Thin Python binding of libdseed (include/dseed.h).
+
+Argument marshalling only: every function checks tensor devices, dtypes and
+shapes, packs the C descriptors and calls the entry point of the same name on
+the current CUDA stream.  All arithmetic runs in the library's kernels.  There
+is no fallback: if libdseed.so is missing or a call fails, an exception says so.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from . import build as _build
+
+MAX_SPHERES = 64
+MAX_T = 128
+MAX_HISTORY = 8
+N_METRICS = 7
+ESDF_FAR = 1000.0
+
+_lib = None
+
+
+class RobotDesc(C.Structure):
+    _fields_ = [("dh", (C.c_float * 4) * 8), ("limits", (C.c_float * 2) * 7), ("n_spheres", C.c_int),
+                ("sphere_frame", C.c_int * MAX_SPHERES), ("sphere_offset", (C.c_float * 3) * MAX_SPHERES),
+                ("sphere_radius", C.c_float * MAX_SPHERES)]
+
+
+class Grid(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("res", C.c_float), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("esdf_dev", C.c_void_p), ("grid", Grid)]
+
+
+class CostParams(C.Structure):
+    _fields_ = [(k, C.c_float) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l")]
+
+
+class OptParams(C.Structure):
+    _fields_ = [("iters", C.c_int), ("m", C.c_int), ("c1", C.c_float), ("max_step", C.c_float),
+                ("gamma0", C.c_float), ("alpha_min", C.c_float)]
+
+
+class PlanDesc(C.Structure):
+    _fields_ = [("P", C.c_int), ("S", C.c_int), ("T", C.c_int), ("cost", CostParams), ("opt", OptParams),
+                ("delta_t", C.c_float), ("delta_r", C.c_float)]
+
+
+class Problems(C.Structure):
+    _fields_ = [("q_start_dev", C.c_void_p), ("goal_dev", C.c_void_p), ("scene_of_problem_dev", C.c_void_p),
+                ("scenes_dev", C.c_void_p), ("n_scenes", C.c_int)]
+
+
+class LbfgsLayout(C.Structure):
+    _fields_ = [(k, C.c_size_t) for k in ("x", "g", "x_trial", "s", "y", "rho", "f", "alpha", "gts", "yy",
+                                          "meta", "total")]
+
+
+class DseedError(RuntimeError):
+    pass
+
+
+_SIGS = {
+    "dseed_abi_version": ([], C.c_int),
+    "dseed_last_error": ([], C.c_char_p),
+    "dseed_robot_create": ([C.POINTER(RobotDesc), C.POINTER(C.c_void_p)], C.c_int),
+    "dseed_robot_destroy": ([C.c_void_p], None),
+    "dseed_scene_build_esdf": ([C.c_void_p, C.c_int, C.POINTER(Grid), C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_fk": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_cost": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_void_p,
+                    C.c_void_p], C.c_int),
+    "dseed_cost_grad": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_evaluate": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_void_p,
+                        C.c_void_p], C.c_int),
+    "dseed_lbfgs_layout": ([C.POINTER(PlanDesc), C.POINTER(LbfgsLayout)], C.c_int),
+    "dseed_lbfgs_init": ([C.POINTER(PlanDesc), C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_lbfgs_step": ([C.POINTER(PlanDesc), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_plan_workspace_bytes": ([C.POINTER(PlanDesc), C.POINTER(C.c_size_t)], C.c_int),
+    "dseed_plan_batch": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_size_t,
+                          C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load libdseed.so (built by paper_2410_16727_gb300.build / __graft_entry__.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise DseedError(f"libdseed.so is not built ({path}); run `python -m paper_2410_16727_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        msg = load().dseed_last_error().decode(errors="replace")
+        raise DseedError(f"{what} failed with status {rc}: {msg}")
+
+
+def _stream() -> int:
+    return torch.cuda.current_stream().cuda_stream
+
+
+def _dev(t: Optional[torch.Tensor], dtype, name: str, shape=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise DseedError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise DseedError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise DseedError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise DseedError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+# ---------------------------------------------------------------------------- descriptors
+
+def abi_version() -> int:
+    return int(load().dseed_abi_version())
+
+
+def last_error() -> str:
+    return load().dseed_last_error().decode(errors="replace")
+
+
+class Robot:
+    """Owning wrapper of a DseedRobot handle built from an inputs.Robot-like object."""
+
+    def __init__(self, robot):
+        d = RobotDesc()
+        dh = robot.dh.tolist()
+        lim = robot.limits.tolist()
+        for i in range(8):
+            for c in range(4):
+                d.dh[i][c] = float(dh[i][c])
+        for j in range(7):
+            d.limits[j][0], d.limits[j][1] = float(lim[j][0]), float(lim[j][1])
+        ns = int(len(robot.sph_r))
+        if ns > MAX_SPHERES:
+            raise DseedError(f"{ns} spheres exceed the limit of {MAX_SPHERES}")
+        d.n_spheres = ns
+        for k in range(ns):
+            d.sphere_frame[k] = int(robot.sph_frame[k])
+            for c in range(3):
+                d.sphere_offset[k][c] = float(robot.sph_o[k][c])
+            d.sphere_radius[k] = float(robot.sph_r[k])
+        h = C.c_void_p()
+        _check(load().dseed_robot_create(C.byref(d), C.byref(h)), "dseed_robot_create")
+        self.handle = h
+        self.n_spheres = ns
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dseed_robot_destroy(self.handle)
+            self.handle = None
+
+
+def make_grid(g) -> Grid:
+    out = Grid()
+    for a in range(3):
+        out.origin[a] = float(g.origin[a])
+    out.res = float(g.res)
+    out.nx, out.ny, out.nz = (int(v) for v in g.n)
+    return out
+
+
+def plan_desc(P: int, S: int, T: int, cost, opt=None, delta_t: float = 0.005,
+              delta_r: float = 2.86 * math.pi / 180.0) -> PlanDesc:
+    d = PlanDesc()
+    d.P, d.S, d.T = int(P), int(S), int(T)
+    for k, v in zip(("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l"), cost.as_array()):
+        setattr(d.cost, k, float(v))
+    if opt is not None:
+        d.opt.iters, d.opt.m = int(opt.iters), int(opt.m)
+        d.opt.c1, d.opt.max_step = float(opt.c1), float(opt.max_step)
+        d.opt.gamma0, d.opt.alpha_min = float(opt.gamma0), float(opt.alpha_min)
+    d.delta_t, d.delta_r = float(delta_t), float(delta_r)
+    return d
+
+
+class SceneTable:
+    """Device table of DseedScene entries (ESDF pointer + grid) for a list of
+    ESDF tensors; keeps the tensors alive."""
+
+    def __init__(self, esdfs: Sequence[torch.Tensor], grids: Sequence, device=None):
+        if len(esdfs) != len(grids) or not esdfs:
+            raise DseedError("need one grid per ESDF and at least one scene")
+        arr = (Scene * len(esdfs))()
+        for i, (e, g) in enumerate(zip(esdfs, grids)):
+            gg = make_grid(g)
+            _dev(e, torch.float32, f"esdf[{i}]", (gg.nz, gg.ny, gg.nx))
+            arr[i].esdf_dev = e.data_ptr()
+            arr[i].grid = gg
+        raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
+        self.table = raw.to(device or esdfs[0].device)
+        self.esdfs = list(esdfs)
+        self.grids = list(grids)
+        self.n = len(esdfs)
+
+
+def make_problems(q_start: torch.Tensor, goal: torch.Tensor, scene_of_problem: torch.Tensor,
+                  scenes: SceneTable) -> Problems:
+    P = q_start.shape[0]
+    pr = Problems()
+    pr.q_start_dev = _dev(q_start, torch.float32, "q_start", (P, 7))
+    pr.goal_dev = _dev(goal, torch.float32, "goal", (P, 7))
+    pr.scene_of_problem_dev = _dev(scene_of_problem, torch.int32, "scene_of_problem", (P,))
+    pr.scenes_dev = scenes.table.data_ptr()
+    pr.n_scenes = scenes.n
+    return pr
+
+
+# ---------------------------------------------------------------------------- entry points
+
+def scene_build_esdf(cuboids: torch.Tensor, grid, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """ESDF [nz][ny][nx] of cuboids [n][6] (device tensors)."""
+    g = make_grid(grid)
+    n = int(cuboids.shape[0])
+    if out is None:
+        out = torch.empty((g.nz, g.ny, g.nx), dtype=torch.float32, device=cuboids.device)
+    cp = _dev(cuboids, torch.float32, "cuboids", (n, 6)) if n > 0 else None
+    _check(load().dseed_scene_build_esdf(cp, n, C.byref(g), _dev(out, torch.float32, "esdf"), _stream()),
+           "dseed_scene_build_esdf")
+    return out
+
+
+def fk(robot: Robot, q: torch.Tensor, spheres: bool = False):
+    """Flange poses [N][7] (and sphere centres [N][Ns][3]) of q [N][7]."""
+    N = int(q.shape[0])
+    pose = torch.empty((N, 7), dtype=torch.float32, device=q.device)
+    sph = torch.empty((N, robot.n_spheres, 3), dtype=torch.float32, device=q.device) if spheres else None
+    _check(load().dseed_fk(robot.handle, _dev(q, torch.float32, "q", (N, 7)), N, pose.data_ptr(),
+                           sph.data_ptr() if sph is not None else None, _stream()), "dseed_fk")
+    return (pose, sph) if spheres else pose
+
+
+def cost(robot: Robot, desc: PlanDesc, pr: Problems, x: torch.Tensor, terms: bool = False):
+    P, S, T = desc.P, desc.S, desc.T
+    out = torch.empty((P, S), dtype=torch.float32, device=x.device)
+    tr = torch.empty((P, S, 4), dtype=torch.float32, device=x.device) if terms else None
+    _check(load().dseed_cost(robot.handle, C.byref(desc), C.byref(pr), _dev(x, torch.float32, "x", (P, S, T, 7)),
+                             out.data_ptr(), tr.data_ptr() if tr is not None else None, _stream()), "dseed_cost")
+    return (out, tr) if terms else out
+
+
+def cost_grad(robot: Robot, desc: PlanDesc, pr: Problems, x: torch.Tensor,
+              grad_scale: Optional[torch.Tensor] = None):
+    P, S, T = desc.P, desc.S, desc.T
+    c = torch.empty((P, S), dtype=torch.float32, device=x.device)
+    g = torch.empty((P, S, T, 7), dtype=torch.float32, device=x.device)
+    _check(load().dseed_cost_grad(robot.handle, C.byref(desc), C.byref(pr),
+                                  _dev(x, torch.float32, "x", (P, S, T, 7)),
+                                  _dev(grad_scale, torch.float32, "grad_scale", (P, S)), c.data_ptr(), g.data_ptr(),
+                                  _stream()), "dseed_cost_grad")
+    return c, g
+
+
+def evaluate(robot: Robot, desc: PlanDesc, pr: Problems, x: torch.Tensor):
+    P, S, T = desc.P, desc.S, desc.T
+    ok = torch.empty((P, S), dtype=torch.uint8, device=x.device)
+    met = torch.empty((P, S, N_METRICS), dtype=torch.float32, device=x.device)
+    _check(load().dseed_evaluate(robot.handle, C.byref(desc), C.byref(pr),
+                                 _dev(x, torch.float32, "x", (P, S, T, 7)), ok.data_ptr(), met.data_ptr(), _stream()),
+           "dseed_evaluate")
+    return ok, met
+
+
+def lbfgs_layout(desc: PlanDesc) -> LbfgsLayout:
+    lay = LbfgsLayout()
+    _check(load().dseed_lbfgs_layout(C.byref(desc), C.byref(lay)), "dseed_lbfgs_layout")
+    return lay
+
+
+def lbfgs_init(desc: PlanDesc, x0: torch.Tensor, state: torch.Tensor):
+    _check(load().dseed_lbfgs_init(C.byref(desc), _dev(x0, torch.float32, "x0"), _dev(state, torch.uint8, "state"),
+                                   _stream()), "dseed_lbfgs_init")
+
+
+def lbfgs_step(desc: PlanDesc, f_trial: torch.Tensor, g_trial: torch.Tensor, state: torch.Tensor):
+    _check(load().dseed_lbfgs_step(C.byref(desc), _dev(f_trial, torch.float32, "f_trial"),
+                                   _dev(g_trial, torch.float32, "g_trial"), _dev(state, torch.uint8, "state"),
+                                   _stream()), "dseed_lbfgs_step")
+
+
+def lbfgs_view(state: torch.Tensor, lay: LbfgsLayout, desc: PlanDesc, name: str) -> torch.Tensor:
+    """A typed view of one array of the L-BFGS state buffer."""
+    B, n, m = desc.P * desc.S, 7 * desc.T, desc.opt.m
+    shapes = {"x": (B, n), "g": (B, n), "x_trial": (B, n), "s": (B, m, n), "y": (B, m, n), "rho": (B, m),
+              "f": (B,), "alpha": (B,), "gts": (B,), "yy": (B,), "meta": (B, 4)}
+    shape = shapes[name]
+    count = 1
+    for s in shape:
+        count *= s
+    off = getattr(lay, name)
+    dtype = torch.int32 if name == "meta" else torch.float32
+    return state[off:off + 4 * count].view(dtype).view(shape)
+
+
+def plan_workspace_bytes(desc: PlanDesc) -> int:
+    b = C.c_size_t()
+    _check(load().dseed_plan_workspace_bytes(C.byref(desc), C.byref(b)), "dseed_plan_workspace_bytes")
+    return int(b.value)
+
+
+def alloc_workspace(nbytes: int, device) -> torch.Tensor:
+    # torch's caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(nbytes, 1), dtype=torch.uint8, device=device)
+
+
+def plan_batch(robot: Robot, desc: PlanDesc, pr: Problems, seeds: torch.Tensor, workspace: torch.Tensor,
+               out: Optional[dict] = None) -> dict:
+    """Run the fused optimiser; returns dict(traj, cost, success, metrics, best)."""
+    P, S, T = desc.P, desc.S, desc.T
+    dev = seeds.device
+    if out is None:
+        out = dict(traj=torch.empty((P, S, T, 7), dtype=torch.float32, device=dev),
+                   cost=torch.empty((P, S), dtype=torch.float32, device=dev),
+                   success=torch.empty((P, S), dtype=torch.uint8, device=dev),
+                   metrics=torch.empty((P, S, N_METRICS), dtype=torch.float32, device=dev),
+                   best=torch.empty((P,), dtype=torch.int32, device=dev))
+    met = out.get("metrics")
+    _check(load().dseed_plan_batch(robot.handle, C.byref(desc), C.byref(pr),
+                                   _dev(seeds, torch.float32, "seeds", (P, S, T, 7)),
+                                   _dev(workspace, torch.uint8, "workspace"), workspace.numel(),
+                                   _dev(out["traj"], torch.float32, "traj", (P, S, T, 7)),
+                                   _dev(out["cost"], torch.float32, "cost", (P, S)),
+                                   _dev(out["success"], torch.uint8, "success", (P, S)),
+                                   met.data_ptr() if met is not None else None,
+                                   _dev(out["best"], torch.int32, "best", (P,)), _stream()), "dseed_plan_batch")
+    return out

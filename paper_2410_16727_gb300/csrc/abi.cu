@@ -1,0 +1,353 @@
+// abi.cu -- host side of the C ABI declared in include/dseed.h: argument
+// checks, robot handles, workspace layouts and kernel launches.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "internal.h"
+
+struct DseedRobot {
+    dseed::KRobot k;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_status(int err, const char *what) {
+    if (err == cudaSuccess) return DSEED_OK;
+    return fail(DSEED_ECUDA, "%s: %s", what, cudaGetErrorString((cudaError_t)err));
+}
+
+bool finite(float v) { return std::isfinite(v); }
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+int check_desc(const DseedPlanDesc *d, bool need_opt) {
+    if (!d) return fail(DSEED_EINVAL, "desc is NULL");
+    if (d->P < 0) return fail(DSEED_EINVAL, "P = %d < 0", d->P);
+    if (d->S < 1) return fail(DSEED_EINVAL, "S = %d < 1", d->S);
+    if (d->T < 1 || d->T > DSEED_MAX_T) return fail(DSEED_EINVAL, "T = %d outside 1..%d", d->T, DSEED_MAX_T);
+    if ((long long)d->P * d->S > (1LL << 31) - 1) return fail(DSEED_EINVAL, "P * S too large");
+    const DseedCostParams &c = d->cost;
+    const float cv[] = {c.w_c, c.eta, c.dt, c.w_v, c.w_a, c.w_j, c.w_p, c.w_R, c.w_l, d->delta_t, d->delta_r};
+    for (float v : cv)
+        if (!finite(v)) return fail(DSEED_EINVAL, "non-finite cost or success parameter");
+    if (!(c.dt > 0.f)) return fail(DSEED_EINVAL, "dt must be > 0");
+    if (need_opt) {
+        const DseedOptParams &o = d->opt;
+        if (o.iters < 1) return fail(DSEED_EINVAL, "iters = %d < 1", o.iters);
+        if (o.m < 1 || o.m > DSEED_MAX_HISTORY) return fail(DSEED_EINVAL, "m = %d outside 1..%d", o.m, DSEED_MAX_HISTORY);
+        const float ov[] = {o.c1, o.max_step, o.gamma0, o.alpha_min};
+        for (float v : ov)
+            if (!finite(v)) return fail(DSEED_EINVAL, "non-finite optimiser parameter");
+        if (!(o.max_step > 0.f) || !(o.gamma0 > 0.f) || !(o.alpha_min > 0.f))
+            return fail(DSEED_EINVAL, "max_step, gamma0 and alpha_min must be > 0");
+    }
+    return DSEED_OK;
+}
+
+int check_problems(const DseedPlanDesc *d, const DseedProblems *pr) {
+    if (!pr) return fail(DSEED_EINVAL, "problems is NULL");
+    if (d->P == 0) return DSEED_OK;
+    if (!pr->q_start_dev || !pr->goal_dev || !pr->scene_of_problem_dev || !pr->scenes_dev)
+        return fail(DSEED_EINVAL, "a problem array is NULL");
+    if (pr->n_scenes < 1) return fail(DSEED_EINVAL, "n_scenes = %d < 1", pr->n_scenes);
+    return DSEED_OK;
+}
+
+dseed::KCost make_cost(const DseedCostParams &c) {
+    dseed::KCost k;
+    k.w_c = c.w_c;
+    k.eta = c.eta;
+    k.inv_dt = (float)(1.0 / (double)c.dt);
+    k.w_v = c.w_v;
+    k.w_a = c.w_a;
+    k.w_j = c.w_j;
+    k.w_p = c.w_p;
+    k.w_R = c.w_R;
+    k.w_l = c.w_l;
+    return k;
+}
+
+dseed::KOpt make_opt(const DseedOptParams &o) {
+    dseed::KOpt k;
+    k.iters = o.iters;
+    k.m = o.m;
+    k.c1 = o.c1;
+    k.max_step = o.max_step;
+    k.gamma0 = o.gamma0;
+    k.alpha_min = o.alpha_min;
+    return k;
+}
+
+dseed::KBatch make_batch(const DseedPlanDesc *d, const DseedProblems *pr) {
+    dseed::KBatch k;
+    k.P = d->P;
+    k.S = d->S;
+    k.T = d->T;
+    k.q_start = pr->q_start_dev;
+    k.goal = pr->goal_dev;
+    k.scene_of_problem = pr->scene_of_problem_dev;
+    k.scenes = pr->scenes_dev;
+    k.n_scenes = pr->n_scenes;
+    k.delta_t = d->delta_t;
+    k.delta_r = d->delta_r;
+    return k;
+}
+
+DseedLbfgsLayout lbfgs_layout(long long B, int n, int m) {
+    DseedLbfgsLayout l;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    l.x = take(sizeof(float) * B * n);
+    l.g = take(sizeof(float) * B * n);
+    l.x_trial = take(sizeof(float) * B * n);
+    l.s = take(sizeof(float) * B * m * n);
+    l.y = take(sizeof(float) * B * m * n);
+    l.rho = take(sizeof(float) * B * m);
+    l.f = take(sizeof(float) * B);
+    l.alpha = take(sizeof(float) * B);
+    l.gts = take(sizeof(float) * B);
+    l.yy = take(sizeof(float) * B);
+    l.meta = take(sizeof(int) * B * 4);
+    l.total = off;
+    return l;
+}
+
+dseed::KLbfgsPtrs lbfgs_ptrs(void *base, const DseedLbfgsLayout &l) {
+    char *c = static_cast<char *>(base);
+    dseed::KLbfgsPtrs p;
+    p.x = reinterpret_cast<float *>(c + l.x);
+    p.g = reinterpret_cast<float *>(c + l.g);
+    p.x_trial = reinterpret_cast<float *>(c + l.x_trial);
+    p.s = reinterpret_cast<float *>(c + l.s);
+    p.y = reinterpret_cast<float *>(c + l.y);
+    p.rho = reinterpret_cast<float *>(c + l.rho);
+    p.f = reinterpret_cast<float *>(c + l.f);
+    p.alpha = reinterpret_cast<float *>(c + l.alpha);
+    p.gts = reinterpret_cast<float *>(c + l.gts);
+    p.yy = reinterpret_cast<float *>(c + l.yy);
+    p.meta = reinterpret_cast<int *>(c + l.meta);
+    return p;
+}
+
+// Plan workspace: history s [B][m][n], history y [B][m][n], best keys [P].
+struct PlanLayout {
+    size_t s, y, key, total;
+};
+
+PlanLayout plan_layout(const DseedPlanDesc *d) {
+    const long long B = (long long)d->P * d->S;
+    const size_t n = 7 * (size_t)d->T, m = (size_t)d->opt.m;
+    PlanLayout l;
+    l.s = 0;
+    l.y = align256(sizeof(float) * B * m * n);
+    l.key = l.y + align256(sizeof(float) * B * m * n);
+    l.total = l.key + align256(sizeof(unsigned long long) * std::max(d->P, 1));
+    return l;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dseed_abi_version(void) { return DSEED_ABI_VERSION; }
+
+const char *dseed_last_error(void) { return g_last_error.c_str(); }
+
+int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
+    if (!desc || !out) return fail(DSEED_EINVAL, "desc or out is NULL");
+    *out = nullptr;
+    const int ns = desc->n_spheres;
+    if (ns < 1 || ns > DSEED_MAX_SPHERES) return fail(DSEED_EINVAL, "n_spheres = %d outside 1..%d", ns, DSEED_MAX_SPHERES);
+    for (int i = 0; i < 8; ++i)
+        for (int c = 0; c < 4; ++c)
+            if (!finite(desc->dh[i][c])) return fail(DSEED_EINVAL, "non-finite DH entry (%d, %d)", i, c);
+    for (int j = 0; j < 7; ++j) {
+        if (!finite(desc->limits[j][0]) || !finite(desc->limits[j][1]) || desc->limits[j][0] > desc->limits[j][1])
+            return fail(DSEED_EINVAL, "bad limits of joint %d", j + 1);
+    }
+    for (int k = 0; k < ns; ++k) {
+        if (desc->sphere_frame[k] < 1 || desc->sphere_frame[k] > 8)
+            return fail(DSEED_EINVAL, "sphere %d: frame %d outside 1..8", k, desc->sphere_frame[k]);
+        if (!(desc->sphere_radius[k] > 0.f) || !finite(desc->sphere_radius[k]))
+            return fail(DSEED_EINVAL, "sphere %d: radius must be finite and > 0", k);
+        for (int c = 0; c < 3; ++c)
+            if (!finite(desc->sphere_offset[k][c])) return fail(DSEED_EINVAL, "sphere %d: non-finite offset", k);
+    }
+    DseedRobot *r = new (std::nothrow) DseedRobot;
+    if (!r) return fail(DSEED_ENOMEM, "host allocation of the robot failed");
+    std::memset(&r->k, 0, sizeof(r->k));
+    dseed::KRobot &k = r->k;
+    for (int i = 0; i < 8; ++i) {
+        const double al = desc->dh[i][2];
+        k.a[i] = desc->dh[i][0];
+        k.d[i] = desc->dh[i][1];
+        k.ca[i] = (float)std::cos(al);
+        k.sa[i] = (float)std::sin(al);
+        k.ca2[i] = (float)std::cos(0.5 * al);
+        k.sa2[i] = (float)std::sin(0.5 * al);
+        k.off[i] = desc->dh[i][3];
+    }
+    for (int j = 0; j < 7; ++j) {
+        k.lo[j] = desc->limits[j][0];
+        k.hi[j] = desc->limits[j][1];
+    }
+    k.n_spheres = ns;
+    int idx = 0;
+    for (int L = 1; L <= 8; ++L) {
+        k.frame_begin[L - 1] = idx;
+        for (int s = 0; s < ns; ++s)
+            if (desc->sphere_frame[s] == L) {
+                k.sph[idx] = make_float4(desc->sphere_offset[s][0], desc->sphere_offset[s][1],
+                                         desc->sphere_offset[s][2], desc->sphere_radius[s]);
+                k.sph_orig[idx] = s;
+                ++idx;
+            }
+    }
+    k.frame_begin[8] = idx;
+    *out = r;
+    return DSEED_OK;
+}
+
+void dseed_robot_destroy(DseedRobot *robot) { delete robot; }
+
+int dseed_scene_build_esdf(const float *cuboids_dev, int n, const DseedGrid *grid, float *esdf_dev,
+                           cudaStream_t stream) {
+    if (!grid || !esdf_dev) return fail(DSEED_EINVAL, "grid or esdf is NULL");
+    if (n < 0 || (n > 0 && !cuboids_dev)) return fail(DSEED_EINVAL, "bad cuboid count or NULL cuboids");
+    if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2) return fail(DSEED_EINVAL, "grid dimensions must be >= 2");
+    if (!(grid->res > 0.f) || !finite(grid->res) || !finite(grid->origin[0]) || !finite(grid->origin[1]) ||
+        !finite(grid->origin[2]))
+        return fail(DSEED_EINVAL, "bad grid origin or resolution");
+    return cuda_status(dseed::launch_esdf_build(cuboids_dev, n, *grid, esdf_dev, stream), "esdf build");
+}
+
+int dseed_fk(const DseedRobot *robot, const float *q_dev, int N, float *pose_dev, float *spheres_dev,
+             cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    if (N < 0) return fail(DSEED_EINVAL, "N < 0");
+    if (N > 0 && (!q_dev || !pose_dev)) return fail(DSEED_EINVAL, "q or pose is NULL");
+    return cuda_status(dseed::launch_fk(robot->k, q_dev, N, pose_dev, spheres_dev, stream), "fk");
+}
+
+int dseed_cost(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr, const float *x_dev,
+               float *cost_dev, float *terms_dev, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    int r = check_desc(desc, false);
+    if (r) return r;
+    if ((r = check_problems(desc, pr))) return r;
+    if (desc->P > 0 && (!x_dev || !cost_dev)) return fail(DSEED_EINVAL, "x or cost is NULL");
+    return cuda_status(dseed::launch_cost(robot->k, make_cost(desc->cost), make_batch(desc, pr), x_dev, cost_dev,
+                                          terms_dev, stream),
+                       "cost");
+}
+
+int dseed_cost_grad(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr, const float *x_dev,
+                    const float *grad_scale_dev, float *cost_dev, float *grad_dev, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    int r = check_desc(desc, false);
+    if (r) return r;
+    if ((r = check_problems(desc, pr))) return r;
+    if (desc->P > 0 && (!x_dev || !cost_dev || !grad_dev)) return fail(DSEED_EINVAL, "x, cost or grad is NULL");
+    return cuda_status(dseed::launch_cost_grad(robot->k, make_cost(desc->cost), make_batch(desc, pr), x_dev,
+                                               grad_scale_dev, cost_dev, grad_dev, stream),
+                       "cost_grad");
+}
+
+int dseed_evaluate(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr, const float *x_dev,
+                   uint8_t *success_dev, float *metrics_dev, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    int r = check_desc(desc, false);
+    if (r) return r;
+    if ((r = check_problems(desc, pr))) return r;
+    if (desc->P > 0 && (!x_dev || !success_dev)) return fail(DSEED_EINVAL, "x or success is NULL");
+    return cuda_status(dseed::launch_evaluate(robot->k, make_cost(desc->cost), make_batch(desc, pr), x_dev,
+                                              success_dev, metrics_dev, stream),
+                       "evaluate");
+}
+
+int dseed_lbfgs_layout(const DseedPlanDesc *desc, DseedLbfgsLayout *out) {
+    int r = check_desc(desc, true);
+    if (r) return r;
+    if (!out) return fail(DSEED_EINVAL, "out is NULL");
+    *out = lbfgs_layout((long long)desc->P * desc->S, 7 * desc->T, desc->opt.m);
+    return DSEED_OK;
+}
+
+int dseed_lbfgs_init(const DseedPlanDesc *desc, const float *x0_dev, void *state_dev, cudaStream_t stream) {
+    int r = check_desc(desc, true);
+    if (r) return r;
+    const long long B = (long long)desc->P * desc->S;
+    if (B > 0 && (!x0_dev || !state_dev)) return fail(DSEED_EINVAL, "x0 or state is NULL");
+    const DseedLbfgsLayout l = lbfgs_layout(B, 7 * desc->T, desc->opt.m);
+    return cuda_status(dseed::launch_lbfgs_init((int)B, 7 * desc->T, x0_dev, lbfgs_ptrs(state_dev, l), desc->opt.m,
+                                                stream),
+                       "lbfgs init");
+}
+
+int dseed_lbfgs_step(const DseedPlanDesc *desc, const float *f_trial_dev, const float *g_trial_dev, void *state_dev,
+                     cudaStream_t stream) {
+    int r = check_desc(desc, true);
+    if (r) return r;
+    const long long B = (long long)desc->P * desc->S;
+    if (B > 0 && (!f_trial_dev || !g_trial_dev || !state_dev)) return fail(DSEED_EINVAL, "f, g or state is NULL");
+    const DseedLbfgsLayout l = lbfgs_layout(B, 7 * desc->T, desc->opt.m);
+    return cuda_status(dseed::launch_lbfgs_step(make_opt(desc->opt), (int)B, desc->T, f_trial_dev, g_trial_dev,
+                                                lbfgs_ptrs(state_dev, l), stream),
+                       "lbfgs step");
+}
+
+int dseed_plan_workspace_bytes(const DseedPlanDesc *desc, size_t *bytes) {
+    int r = check_desc(desc, true);
+    if (r) return r;
+    if (!bytes) return fail(DSEED_EINVAL, "bytes is NULL");
+    *bytes = plan_layout(desc).total;
+    return DSEED_OK;
+}
+
+int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                     const float *seeds_dev, void *workspace_dev, size_t workspace_bytes, float *traj_dev,
+                     float *cost_dev, uint8_t *success_dev, float *metrics_dev, int *best_dev, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    int r = check_desc(desc, true);
+    if (r) return r;
+    if ((r = check_problems(desc, pr))) return r;
+    if (desc->P == 0) return DSEED_OK;
+    if (!seeds_dev || !workspace_dev || !traj_dev || !cost_dev || !success_dev || !best_dev)
+        return fail(DSEED_EINVAL, "a plan buffer is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace_dev) % 256 != 0) return fail(DSEED_EINVAL, "workspace not 256-byte aligned");
+    const PlanLayout l = plan_layout(desc);
+    if (workspace_bytes < l.total)
+        return fail(DSEED_ENOMEM, "workspace of %zu bytes, %zu needed", workspace_bytes, l.total);
+    char *w = static_cast<char *>(workspace_dev);
+    return cuda_status(dseed::launch_plan(robot->k, make_cost(desc->cost), make_opt(desc->opt), make_batch(desc, pr),
+                                          seeds_dev, reinterpret_cast<float *>(w + l.s),
+                                          reinterpret_cast<float *>(w + l.y),
+                                          reinterpret_cast<unsigned long long *>(w + l.key), traj_dev, cost_dev,
+                                          success_dev, metrics_dev, best_dev, stream),
+                       "plan");
+}
+
+}  // extern "C"

@@ -1,0 +1,525 @@
+// device.cuh -- device functions of the seed-trajectory optimiser.
+//
+// Mapping: one warp owns one seed trajectory.  During an evaluation lane l
+// owns waypoints l, l + 32, ... (TPL = waypoints per lane); the trajectory,
+// the accepted point and the gradients live in the warp's slice of shared
+// memory, so the L-BFGS update can use a flat mapping (lane l owns vector
+// entries l, l + 32, ...) with conflict-free, coalesced accesses.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "internal.h"
+
+namespace dseed {
+
+// ----------------------------------------------------------------- warp reductions
+// Butterfly (xor) reductions: every lane ends with the same bits, since each
+// stage adds the same two operands in both partner lanes.
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// ----------------------------------------------------------------- scene / ESDF
+struct SceneView {
+    const float *__restrict__ phi;
+    float ox, oy, oz, inv_res;
+    int nx, ny, nz;
+    bool ok;                  // descriptor usable: non-null ESDF, every dimension >= 2, res > 0
+};
+
+// Scene idx of the table (the caller checks 0 <= idx < n_scenes).
+__device__ __forceinline__ SceneView load_scene(const DseedScene *scenes, int idx) {
+    const DseedScene &s = scenes[idx];
+    SceneView v;
+    v.ok = s.esdf_dev != nullptr && s.grid.nx >= 2 && s.grid.ny >= 2 && s.grid.nz >= 2 && s.grid.res > 0.0f;
+    v.phi = s.esdf_dev;
+    v.ox = s.grid.origin[0];
+    v.oy = s.grid.origin[1];
+    v.oz = s.grid.origin[2];
+    v.inv_res = 1.0f / s.grid.res;
+    v.nx = s.grid.nx;
+    v.ny = s.grid.ny;
+    v.nz = s.grid.nz;
+    return v;
+}
+
+// Continuous voxel coordinate along one axis, clamped into the grid; cell index
+// and fraction.  Returns true when the point lay outside (gradient zero there).
+// NaN and infinities land on a valid cell (fmaxf/fminf drop NaN), so no access
+// can leave the grid.
+__device__ __forceinline__ bool grid_axis(float p, float o, float inv_res, int n, int &i0, float &f) {
+    float u = (p - o) * inv_res - 0.5f;
+    float hi = (float)(n - 1);
+    bool clamped = !(u >= 0.0f && u <= hi);
+    u = fminf(fmaxf(u, 0.0f), hi);
+    int c = min((int)floorf(u), n - 2);
+    i0 = c;
+    f = u - (float)c;
+    return clamped;
+}
+
+// Trilinear interpolation of the ESDF at (px, py, pz) from the 8 corners of its
+// cell (point loads through the read-only path), with the analytic gradient.
+template <bool GRAD>
+__device__ __forceinline__ float esdf_sample(const SceneView &sv, float px, float py, float pz,
+                                             float &gx, float &gy, float &gz) {
+    int ix, iy, iz;
+    float fx, fy, fz;
+    bool cx = grid_axis(px, sv.ox, sv.inv_res, sv.nx, ix, fx);
+    bool cy = grid_axis(py, sv.oy, sv.inv_res, sv.ny, iy, fy);
+    bool cz = grid_axis(pz, sv.oz, sv.inv_res, sv.nz, iz, fz);
+    const size_t sy = (size_t)sv.nx, sz = (size_t)sv.nx * (size_t)sv.ny;
+    const float *b = sv.phi + (size_t)iz * sz + (size_t)iy * sy + ix;
+    float v000 = __ldg(b), v100 = __ldg(b + 1);
+    float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
+    float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
+    float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
+    float c00 = fmaf(fx, v100 - v000, v000);
+    float c10 = fmaf(fx, v110 - v010, v010);
+    float c01 = fmaf(fx, v101 - v001, v001);
+    float c11 = fmaf(fx, v111 - v011, v011);
+    float c0 = fmaf(fy, c10 - c00, c00);
+    float c1 = fmaf(fy, c11 - c01, c01);
+    float val = fmaf(fz, c1 - c0, c0);
+    if (GRAD) {
+        float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
+        float dx0 = fmaf(fy, d10 - d00, d00), dx1 = fmaf(fy, d11 - d01, d01);
+        float ey0 = c10 - c00, ey1 = c11 - c01;
+        gx = cx ? 0.0f : fmaf(fz, dx1 - dx0, dx0) * sv.inv_res;
+        gy = cy ? 0.0f : fmaf(fz, ey1 - ey0, ey0) * sv.inv_res;
+        gz = cz ? 0.0f : (c1 - c0) * sv.inv_res;
+    }
+    return val;
+}
+
+// ----------------------------------------------------------------- kinematics
+// One step of the modified-DH chain: R <- R RotX(alpha) RotZ(theta),
+// p <- p + a x_prev + d z_new (R row-major, columns x, y, z).
+__device__ __forceinline__ void dh_step(float (&R)[9], float (&p)[3], float a, float d, float ca,
+                                        float sa, float ct, float st) {
+    p[0] = fmaf(a, R[0], p[0]);
+    p[1] = fmaf(a, R[3], p[1]);
+    p[2] = fmaf(a, R[6], p[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        float xr = R[3 * r], yr = R[3 * r + 1], zr = R[3 * r + 2];
+        float y1 = fmaf(ca, yr, sa * zr);
+        float z1 = fmaf(ca, zr, -sa * yr);
+        R[3 * r] = fmaf(ct, xr, st * y1);
+        R[3 * r + 1] = fmaf(ct, y1, -st * xr);
+        R[3 * r + 2] = z1;
+    }
+    p[0] = fmaf(d, R[2], p[0]);
+    p[1] = fmaf(d, R[5], p[1]);
+    p[2] = fmaf(d, R[8], p[2]);
+}
+
+// Goal: position and rotation matrix of the (normalised) goal quaternion.
+struct Goal {
+    float p[3];
+    float R[9];
+};
+
+__device__ __forceinline__ Goal make_goal(const float *g) {
+    Goal G;
+    G.p[0] = g[0];
+    G.p[1] = g[1];
+    G.p[2] = g[2];
+    float w = g[3], x = g[4], y = g[5], z = g[6];
+    float inv = rsqrtf(w * w + x * x + y * y + z * z);
+    w *= inv; x *= inv; y *= inv; z *= inv;
+    G.R[0] = 1.0f - 2.0f * (y * y + z * z); G.R[1] = 2.0f * (x * y - w * z); G.R[2] = 2.0f * (x * z + w * y);
+    G.R[3] = 2.0f * (x * y + w * z); G.R[4] = 1.0f - 2.0f * (x * x + z * z); G.R[5] = 2.0f * (y * z - w * x);
+    G.R[6] = 2.0f * (x * z - w * y); G.R[7] = 2.0f * (y * z + w * x); G.R[8] = 1.0f - 2.0f * (x * x + y * y);
+    return G;
+}
+
+enum { MODE_COST = 0, MODE_GRAD = 1, MODE_EVAL = 2 };
+
+struct WaypointAcc {
+    float c_world, c_goal;
+    float min_clear;          // MODE_EVAL
+    float pos_err, rot_err;   // MODE_EVAL, last waypoint only
+};
+
+// World and goal terms of one waypoint q (and, in MODE_GRAD, their gradient
+// added into gq).  Adjoint by Jacobian-transpose accumulation: each active
+// sphere applies the force g_k = dC/dc_k = -w_c grad(phi) at c_k; joint i
+// receives z_i . sum over spheres beyond joint i of (c_k - p_i) x g_k.  With
+// running sums F = sum g_k and M = sum c_k x g_k over the spheres met so far,
+// that is z_i . (M_all - M_<i) - (z_i x p_i) . (F_all - F_<i): the prefix
+// part b_i is recorded when frame i is reached, the rest once all spheres and
+// the goal wrench are in.
+template <int MODE>
+__device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc, const SceneView &sv,
+                                               const float (&q)[7], bool last, const Goal &G,
+                                               WaypointAcc &acc, float (&gq)[7]) {
+    float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+    float p[3] = {0.f, 0.f, 0.f};
+    float zj[7][3], wj[7][3], bj[7];
+    float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
+#pragma unroll
+    for (int L = 1; L <= 8; ++L) {
+        float st, ct, th = rb.off[L - 1];
+        if (L <= 7) th += q[L <= 7 ? L - 1 : 0];
+        sincosf(th, &st, &ct);
+        dh_step(R, p, rb.a[L - 1], rb.d[L - 1], rb.ca[L - 1], rb.sa[L - 1], ct, st);
+        if (MODE == MODE_GRAD && L <= 7) {
+            float z0 = R[2], z1 = R[5], z2 = R[8];
+            float w0 = z1 * p[2] - z2 * p[1];
+            float w1 = z2 * p[0] - z0 * p[2];
+            float w2 = z0 * p[1] - z1 * p[0];
+            zj[L - 1][0] = z0; zj[L - 1][1] = z1; zj[L - 1][2] = z2;
+            wj[L - 1][0] = w0; wj[L - 1][1] = w1; wj[L - 1][2] = w2;
+            bj[L - 1] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
+        }
+        const int k1 = rb.frame_begin[L];
+        for (int k = rb.frame_begin[L - 1]; k < k1; ++k) {
+            const float4 s = rb.sph[k];
+            float cx = fmaf(R[0], s.x, fmaf(R[1], s.y, fmaf(R[2], s.z, p[0])));
+            float cy = fmaf(R[3], s.x, fmaf(R[4], s.y, fmaf(R[5], s.z, p[1])));
+            float cz = fmaf(R[6], s.x, fmaf(R[7], s.y, fmaf(R[8], s.z, p[2])));
+            float gx, gy, gz;
+            float phi = esdf_sample<MODE == MODE_GRAD>(sv, cx, cy, cz, gx, gy, gz);
+            if (MODE == MODE_EVAL) acc.min_clear = fminf(acc.min_clear, phi - s.w);
+            float h = s.w + kc.eta - phi;
+            if (h > 0.0f) {
+                acc.c_world = fmaf(kc.w_c, h, acc.c_world);
+                if (MODE == MODE_GRAD) {
+                    float fx = -kc.w_c * gx, fy = -kc.w_c * gy, fz = -kc.w_c * gz;
+                    Fx += fx; Fy += fy; Fz += fz;
+                    Mx += cy * fz - cz * fy;
+                    My += cz * fx - cx * fz;
+                    Mz += cx * fy - cy * fx;
+                }
+            }
+        }
+    }
+    if (last) {
+        // C_goal = w_p |p - p*|^2 + w_R (1 - <q, q*>^2), with
+        // 1 - <q, q*>^2 = (3 - tr(R*^T R)) / 4 for unit quaternions.
+        float e0 = p[0] - G.p[0], e1 = p[1] - G.p[1], e2 = p[2] - G.p[2];
+        // A = R R*^T
+        float A[9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                A[3 * i + j] = R[3 * i] * G.R[3 * j] + R[3 * i + 1] * G.R[3 * j + 1] + R[3 * i + 2] * G.R[3 * j + 2];
+        float tr = A[0] + A[4] + A[8];
+        acc.c_goal = kc.w_p * (e0 * e0 + e1 * e1 + e2 * e2) + kc.w_R * 0.25f * (3.0f - tr);
+        float v0 = A[5] - A[7], v1 = A[6] - A[2], v2 = A[1] - A[3];
+        if (MODE == MODE_EVAL) {
+            acc.pos_err = sqrtf(e0 * e0 + e1 * e1 + e2 * e2);
+            acc.rot_err = atan2f(0.5f * sqrtf(v0 * v0 + v1 * v1 + v2 * v2), 0.5f * (tr - 1.0f));
+        }
+        if (MODE == MODE_GRAD) {
+            // position: force 2 w_p e at the flange origin; orientation: torque
+            // -(w_R / 4) (A12 - A21, A20 - A02, A01 - A10) (d tr(A) = dw . v)
+            float fx = 2.0f * kc.w_p * e0, fy = 2.0f * kc.w_p * e1, fz = 2.0f * kc.w_p * e2;
+            Fx += fx; Fy += fy; Fz += fz;
+            Mx += p[1] * fz - p[2] * fy;
+            My += p[2] * fx - p[0] * fz;
+            Mz += p[0] * fy - p[1] * fx;
+            float tq = -0.25f * kc.w_R;
+            Mx = fmaf(tq, v0, Mx);
+            My = fmaf(tq, v1, My);
+            Mz = fmaf(tq, v2, Mz);
+        }
+    }
+    if (MODE == MODE_GRAD) {
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+            gq[i] += (zj[i][0] * Mx + zj[i][1] * My + zj[i][2] * Mz)
+                     - (wj[i][0] * Fx + wj[i][1] * Fy + wj[i][2] * Fz) - bj[i];
+    }
+}
+
+// ----------------------------------------------------------------- one trajectory
+// Shared-memory slice of one warp (floats):
+//   xs [(T + 3) * 7]   y_-2, y_-1, y_0 (= q_start) then the trial waypoints 1..T
+//   es [3 * (T + 3) * 7] velocity / acceleration / jerk adjoint weights, rows >= T zero
+//   gs [T * 7]         gradient of the trial point
+//   xa [T * 7], ga [T * 7]  accepted point and its gradient (optimiser only)
+//   rho [8], al [8]    L-BFGS scalars
+__host__ __device__ constexpr int warp_smem_floats(int T) { return 4 * (T + kPad) * 7 + 3 * 7 * T + 16; }
+
+struct WarpSmem {
+    float *xs, *es, *gs, *xa, *ga, *rho, *al;
+};
+
+__device__ __forceinline__ WarpSmem carve(float *base, int T) {
+    WarpSmem w;
+    w.xs = base;
+    w.es = w.xs + (T + kPad) * 7;
+    w.gs = w.es + 3 * (T + kPad) * 7;
+    w.xa = w.gs + T * 7;
+    w.ga = w.xa + T * 7;
+    w.rho = w.ga + T * 7;
+    w.al = w.rho + 8;
+    return w;
+}
+
+struct EvalOut {
+    float cost;
+    float terms[4];                       // world, smooth, goal, limit
+    float min_clear, pos_err, rot_err, max_jerk, lim_viol;
+};
+
+// Cost (MODE_COST), cost and gradient into ws.gs (MODE_GRAD), or cost and
+// success metrics (MODE_EVAL) of the trajectory held in ws.xs.  Warp-uniform
+// result.  ws.es rows T..T+2 must be zero (MODE_GRAD).
+template <int TPL, int MODE>
+__device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, const SceneView &sv,
+                                             int T, const Goal &G, const WarpSmem &ws, bool want_terms) {
+    const int lane = threadIdx.x & 31;
+    float c_world = 0.f, c_smooth = 0.f, c_goal = 0.f, c_limit = 0.f;
+    float min_clear = CUDART_INF_F, pos_err = 0.f, rot_err = 0.f, max_jerk = 0.f, lim_viol = 0.f;
+    float gq[TPL][7];
+    const float inv_dt = kc.inv_dt;
+    const int R3 = (T + kPad) * 7;
+#pragma unroll
+    for (int u = 0; u < TPL; ++u) {
+        const int t0 = lane + 32 * u;   // waypoint t = t0 + 1
+#pragma unroll
+        for (int j = 0; j < 7; ++j) gq[u][j] = 0.f;
+        if (t0 < T) {
+            const float *y = ws.xs + (t0 + kPad) * 7;   // y_t; y - 7 = y_{t-1}, ...
+            float q[7];
+#pragma unroll
+            for (int j = 0; j < 7; ++j) q[j] = y[j];
+            WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
+            waypoint_terms<MODE>(rb, kc, sv, q, t0 == T - 1, G, acc, gq[u]);
+            c_world += acc.c_world;
+            c_goal += acc.c_goal;
+            if (MODE == MODE_EVAL) {
+                min_clear = fminf(min_clear, acc.min_clear);
+                if (t0 == T - 1) { pos_err = acc.pos_err; rot_err = acc.rot_err; }
+            }
+#pragma unroll
+            for (int j = 0; j < 7; ++j) {
+                const float y0 = y[j], y1 = y[j - 7], y2 = y[j - 14], y3 = y[j - 21];
+                const float v = (y0 - y1) * inv_dt;
+                const float a = (y0 - 2.0f * y1 + y2) * (inv_dt * inv_dt);
+                const float jk = (y0 - 3.0f * y1 + 3.0f * y2 - y3) * (inv_dt * inv_dt * inv_dt);
+                c_smooth += kc.w_v * v * v + kc.w_a * a * a + kc.w_j * jk * jk;
+                const float hi = rb.hi[j], lo = rb.lo[j];
+                float viol = 0.f;
+                if (y0 > hi) {
+                    viol = y0 - hi;
+                    c_limit += kc.w_l * viol * viol;
+                    gq[u][j] += 2.0f * kc.w_l * viol;
+                } else if (y0 < lo) {
+                    viol = lo - y0;
+                    c_limit += kc.w_l * viol * viol;
+                    gq[u][j] -= 2.0f * kc.w_l * viol;
+                }
+                if (MODE == MODE_EVAL) {
+                    max_jerk = fmaxf(max_jerk, fabsf(jk));
+                    lim_viol = fmaxf(lim_viol, viol);
+                }
+                if (MODE == MODE_GRAD) {
+                    ws.es[t0 * 7 + j] = 2.0f * kc.w_v * v * inv_dt;
+                    ws.es[R3 + t0 * 7 + j] = 2.0f * kc.w_a * a * (inv_dt * inv_dt);
+                    ws.es[2 * R3 + t0 * 7 + j] = 2.0f * kc.w_j * jk * (inv_dt * inv_dt * inv_dt);
+                }
+            }
+        }
+    }
+    if (MODE == MODE_GRAD) {
+        __syncwarp();
+        // transposed stencils: waypoint s receives e_v(s) - e_v(s+1),
+        // e_a(s) - 2 e_a(s+1) + e_a(s+2), e_j(s) - 3 e_j(s+1) + 3 e_j(s+2) - e_j(s+3)
+#pragma unroll
+        for (int u = 0; u < TPL; ++u) {
+            const int t0 = lane + 32 * u;
+            if (t0 < T) {
+                const float *ev = ws.es + t0 * 7, *ea = ev + R3, *ej = ev + 2 * R3;
+#pragma unroll
+                for (int j = 0; j < 7; ++j) {
+                    float g = gq[u][j];
+                    g += ev[j] - ev[j + 7];
+                    g += ea[j] - 2.0f * ea[j + 7] + ea[j + 14];
+                    g += ej[j] - 3.0f * ej[j + 7] + 3.0f * ej[j + 14] - ej[j + 21];
+                    ws.gs[t0 * 7 + j] = g;
+                }
+            }
+        }
+    }
+    EvalOut o;
+    o.cost = warp_sum(c_world + c_smooth + c_goal + c_limit);
+    if (want_terms) {
+        o.terms[0] = warp_sum(c_world);
+        o.terms[1] = warp_sum(c_smooth);
+        o.terms[2] = warp_sum(c_goal);
+        o.terms[3] = warp_sum(c_limit);
+    }
+    if (MODE == MODE_EVAL) {
+        o.min_clear = warp_min(min_clear);
+        o.max_jerk = warp_max(max_jerk);
+        o.lim_viol = warp_max(lim_viol);
+        const int src = (T - 1) & 31;
+        o.pos_err = __shfl_sync(0xffffffffu, pos_err, src);
+        o.rot_err = __shfl_sync(0xffffffffu, rot_err, src);
+    }
+    return o;
+}
+
+// ----------------------------------------------------------------- L-BFGS
+// Warp-uniform scalars of one seed's optimiser state.
+struct LbUni {
+    float f, alpha, gts, yy;
+    int hist, newest, first, accepts;
+};
+
+// One L-BFGS update in the flat mapping (lane owns entries lane + 32 i of the
+// n = 7T vector; NPL >= ceil(n / 32)).  Reads the trial point xt and its
+// gradient gt and cost ft; updates the accepted point xa / ga and the history
+// S, Y ([m][n], global) with rho (shared); writes the next trial point into
+// xt_next (may alias xt).  Matches DseedOptParams.
+template <int NPL>
+__device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, const float *xt,
+                                             const float *gt, float ft, float *xa, float *ga,
+                                             float *__restrict__ S, float *__restrict__ Y, float *rho,
+                                             float *al, float *xt_next) {
+    const int lane = threadIdx.x & 31;
+    const int m = ko.m;
+    if (st.first) {
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) { xa[e] = xt[e]; ga[e] = gt[e]; }
+        }
+        st.f = ft;
+        st.first = 0;
+        st.accepts += 1;
+    } else if (ft <= st.f + ko.c1 * st.gts) {
+        float sy = 0.f, ss = 0.f, yy = 0.f;
+        float sv[NPL], yv[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            sv[i] = 0.f; yv[i] = 0.f;
+            if (e < n) { sv[i] = xt[e] - xa[e]; yv[i] = gt[e] - ga[e]; }
+            sy = fmaf(sv[i], yv[i], sy);
+            ss = fmaf(sv[i], sv[i], ss);
+            yy = fmaf(yv[i], yv[i], yy);
+        }
+        sy = warp_sum(sy);
+        ss = warp_sum(ss);
+        yy = warp_sum(yy);
+        if (sy > 1e-10f * sqrtf(ss) * sqrtf(yy)) {
+            const int k = (st.newest + 1) % m;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) {
+                const int e = lane + 32 * i;
+                if (e < n) { S[(size_t)k * n + e] = sv[i]; Y[(size_t)k * n + e] = yv[i]; }
+            }
+            if (lane == 0) rho[k] = 1.0f / sy;
+            st.newest = k;
+            st.yy = yy;
+            st.hist = min(st.hist + 1, m);
+        }
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) { xa[e] = xt[e]; ga[e] = gt[e]; }
+        }
+        st.f = ft;
+        st.alpha = fminf(1.0f, 2.0f * st.alpha);
+        st.accepts += 1;
+    } else {
+        st.alpha *= 0.5f;
+        if (st.alpha < ko.alpha_min) {
+            st.hist = 0;
+            st.newest = -1;
+            st.alpha = 1.0f;
+        }
+    }
+    __syncwarp();
+    // two-loop recursion: newest to oldest, then oldest to newest
+    float qv[NPL], gv[NPL];
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int e = lane + 32 * i;
+        gv[i] = e < n ? ga[e] : 0.f;
+        qv[i] = gv[i];
+    }
+    for (int h = 0; h < st.hist; ++h) {
+        const int k = ((st.newest - h) % m + m) % m;
+        const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+        float dot = 0.f;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) dot = fmaf(Sk[e], qv[i], dot);
+        }
+        const float a = rho[k] * warp_sum(dot);
+        if (lane == 0) al[k] = a;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) qv[i] = fmaf(-a, Yk[e], qv[i]);
+        }
+    }
+    __syncwarp();
+    const float gamma = st.hist > 0 ? (1.0f / rho[st.newest]) / st.yy : ko.gamma0;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) qv[i] *= gamma;
+    for (int h = st.hist - 1; h >= 0; --h) {
+        const int k = ((st.newest - h) % m + m) % m;
+        const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+        float dot = 0.f;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) dot = fmaf(Yk[e], qv[i], dot);
+        }
+        const float b = rho[k] * warp_sum(dot);
+        const float c = al[k] - b;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int e = lane + 32 * i;
+            if (e < n) qv[i] = fmaf(c, Sk[e], qv[i]);
+        }
+    }
+    float gd = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) gd = fmaf(gv[i], -qv[i], gd);
+    gd = warp_sum(gd);
+    const bool descent = gd < 0.0f;
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        qv[i] = descent ? -qv[i] : -gv[i];          // qv now holds d
+        mx = fmaxf(mx, fabsf(st.alpha * qv[i]));
+    }
+    mx = warp_max(mx);
+    const float scale = mx > ko.max_step ? ko.max_step / mx : 1.0f;
+    float gts = 0.f;
+#pragma unroll
+    for (int i = 0; i < NPL; ++i) {
+        const int e = lane + 32 * i;
+        const float step = st.alpha * qv[i] * scale;
+        if (e < n) xt_next[e] = xa[e] + step;
+        gts = fmaf(gv[i], step, gts);
+    }
+    st.gts = warp_sum(gts);
+    __syncwarp();
+}
+
+}  // namespace dseed

@@ -1,0 +1,72 @@
+"""The C-ABI library builds for sm_103a and exports every entry point that
+include/dseed.h declares (no GPU needed: nothing is called but version/error)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_2410_16727_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "dseed.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(dseed_[a-z0-9_]+)\s*\(", text)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    try:
+        return B.build()
+    except RuntimeError as e:  # pragma: no cover - only without a CUDA toolkit
+        pytest.skip(str(e))
+
+
+def test_header_declares_expected_calls():
+    names = _declared()
+    for want in ("dseed_scene_build_esdf", "dseed_plan_batch", "dseed_cost", "dseed_cost_grad",
+                 "dseed_lbfgs_step", "dseed_fk", "dseed_evaluate", "dseed_plan_workspace_bytes"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    out = subprocess.run(["nm", "-D", "--defined-only", libpath], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\bT\s+(dseed_\w+)", out))
+    missing = [n for n in _declared() if n not in exported]
+    assert not missing, missing
+
+
+def test_library_loads_and_reports_version(libpath):
+    lib = ctypes.CDLL(libpath)
+    lib.dseed_abi_version.restype = ctypes.c_int
+    assert lib.dseed_abi_version() == 1
+    lib.dseed_last_error.restype = ctypes.c_char_p
+    assert lib.dseed_last_error() is not None
+
+
+def test_host_argument_checks_without_gpu(libpath):
+    """Descriptor checks run on the host and need no device."""
+    from paper_2410_16727_gb300 import binding as BD
+    from paper_2410_16727_gb300 import inputs as I
+    BD._lib = None
+    lib = BD.load()
+    d = BD.plan_desc(1, 1, 300, I.CostParams(), I.OptParams())   # T above the maximum
+    n = ctypes.c_size_t()
+    assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1
+    assert "T = 300" in BD.last_error()
+    d = BD.plan_desc(2, 3, 32, I.CostParams(), I.OptParams(iters=5, m=9))
+    assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1
+    d = BD.plan_desc(2, 3, 32, I.CostParams(), I.OptParams(iters=5, m=5))
+    assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == 0
+    assert n.value >= 2 * 2 * 3 * 5 * 224 * 4
+    r = I.make_robot()
+    r.sph_r = r.sph_r.copy()
+    r.sph_r[3] = -1.0
+    with pytest.raises(BD.DseedError, match="radius"):
+        BD.Robot(r)
+    h = BD.Robot(I.make_robot())
+    assert h.n_spheres == 50
