@@ -42,12 +42,15 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dseed", choices=["dseed", "reference"])
     ap.add_argument("--workload", default="batched", choices=list(I.WORKLOADS))
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--problems", type=int, default=None,
+                    help="smaller case for profiling: this many problems (and scenes) of the workload")
     return ap.parse_args()
 
 
@@ -67,7 +70,7 @@ class ClockSampler:
         try:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=self.f, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -117,6 +120,9 @@ def run_gpu(args, rank: int, world: int):
     spec = I.WORKLOADS[args.workload]
     robot = I.make_robot()
     # each rank plans its own problems (replicas of the workload with different seeds)
+    if args.problems:
+        spec = I.WorkloadSpec(spec.name, spec.config_id, min(spec.n_scenes, args.problems), args.problems,
+                              spec.S, spec.T, spec.iters, spec.scene, spec.grid)
     cub, grids = I.make_scenes(spec, seed_offset=rank)
     planner = api.Planner(robot, I.CostParams(), I.OptParams(iters=spec.iters), dev)
     planner.set_scenes(cub, grids)
@@ -209,11 +215,11 @@ def run_gpu(args, rank: int, world: int):
         for k, v in h_out.items():
             v.copy_(out[k], non_blocking=True)
 
-    for _ in range(2):
+    for _ in range(0 if args.no_e2e else 2):
         e2e_step()
     torch.cuda.synchronize()
     e_ms = []
-    for _ in range(max(2, args.steps)):
+    for _ in range(0 if args.no_e2e else max(2, args.steps)):
         flush.zero_()
         torch.cuda.synchronize()
         a = torch.cuda.Event(enable_timing=True)
@@ -223,7 +229,7 @@ def run_gpu(args, rank: int, world: int):
         b.record(stream)
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e2e_ms = sum(e_ms) / len(e_ms)
+    e2e_ms = sum(e_ms) / len(e_ms) if e_ms else float("nan")
     if world > 1:
         t = torch.tensor([e2e_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -245,7 +251,8 @@ def run_gpu(args, rank: int, world: int):
         success_rate=success_rate, problems_solved=solved,
         wall_s_timed=wall,
         gpu_launches=len(cub) + 2,
-        e2e={"value": st_evals * world / (e2e_ms * 1e-3), "unit": UNIT, "ms_per_step": e2e_ms,
+        e2e={"value": st_evals * world / (e2e_ms * 1e-3) if e_ms else None, "unit": UNIT,
+             "ms_per_step": e2e_ms if e_ms else None,
              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,

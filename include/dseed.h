@@ -86,10 +86,19 @@ typedef struct {
     int   nx, ny, nz;
 } DseedGrid;
 
-/* One scene as the optimiser reads it: its ESDF on the device and the grid. */
+/* One scene as the optimiser reads it: its ESDF on the device, the grid, and
+ * a Lipschitz bound L of the field (|phi(a) - phi(b)| <= L |a - b| between voxel
+ * centres).  A true distance field, such as dseed_scene_build_esdf writes, has
+ * L = 1.  With L > 0 the cost and adjoint kernels read only the voxel nearest to
+ * a sphere centre when that value already proves the hinge inactive (value >=
+ * r + eta + L sqrt(3) res + 1e-5), and skip the trilinear interpolation: the
+ * results are the same as with the full interpolation.  L = 0 turns this off
+ * (for fields that are not distance fields).  The success test always
+ * interpolates. */
 typedef struct {
     const float *esdf_dev;                   /* [nz][ny][nx] */
     DseedGrid    grid;
+    float        lipschitz;                  /* L >= 0 */
 } DseedScene;
 
 /* Cost weights (Appendix A.5 objective; values are the caller's choice). */

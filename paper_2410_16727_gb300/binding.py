@@ -36,7 +36,7 @@ class Grid(C.Structure):
 
 
 class Scene(C.Structure):
-    _fields_ = [("esdf_dev", C.c_void_p), ("grid", Grid)]
+    _fields_ = [("esdf_dev", C.c_void_p), ("grid", Grid), ("lipschitz", C.c_float)]
 
 
 class CostParams(C.Structure):
@@ -203,7 +203,7 @@ class SceneTable:
     """Device table of DseedScene entries (ESDF pointer + grid) for a list of
     ESDF tensors; keeps the tensors alive."""
 
-    def __init__(self, esdfs: Sequence[torch.Tensor], grids: Sequence, device=None):
+    def __init__(self, esdfs: Sequence[torch.Tensor], grids: Sequence, device=None, lipschitz: float = 1.0):
         if len(esdfs) != len(grids) or not esdfs:
             raise DseedError("need one grid per ESDF and at least one scene")
         arr = (Scene * len(esdfs))()
@@ -212,6 +212,7 @@ class SceneTable:
             _dev(e, torch.float32, f"esdf[{i}]", (gg.nz, gg.ny, gg.nx))
             arr[i].esdf_dev = e.data_ptr()
             arr[i].grid = gg
+            arr[i].lipschitz = float(lipschitz)
         raw = torch.frombuffer(bytearray(bytes(arr)), dtype=torch.uint8)
         self.table = raw.to(device or esdfs[0].device)
         self.esdfs = list(esdfs)

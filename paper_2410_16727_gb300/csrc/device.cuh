@@ -37,6 +37,7 @@ __device__ __forceinline__ float warp_min(float v) {
 struct SceneView {
     const float *__restrict__ phi;
     float ox, oy, oz, inv_res;
+    float skip_pad;           // L sqrt(3) res + 1e-5, or +inf when the early-out is off
     int nx, ny, nz;
     bool ok;                  // descriptor usable: non-null ESDF, every dimension >= 2, res > 0
 };
@@ -51,6 +52,7 @@ __device__ __forceinline__ SceneView load_scene(const DseedScene *scenes, int id
     v.oy = s.grid.origin[1];
     v.oz = s.grid.origin[2];
     v.inv_res = 1.0f / s.grid.res;
+    v.skip_pad = s.lipschitz > 0.0f ? s.lipschitz * 1.7320508f * s.grid.res + 1e-5f : CUDART_INF_F;
     v.nx = s.grid.nx;
     v.ny = s.grid.ny;
     v.nz = s.grid.nz;
@@ -74,9 +76,16 @@ __device__ __forceinline__ bool grid_axis(float p, float o, float inv_res, int n
 
 // Trilinear interpolation of the ESDF at (px, py, pz) from the 8 corners of its
 // cell (point loads through the read-only path), with the analytic gradient.
-template <bool GRAD>
-__device__ __forceinline__ float esdf_sample(const SceneView &sv, float px, float py, float pz,
-                                             float &gx, float &gy, float &gz) {
+// With SKIP, the corner nearest to the point is read first; when its value is
+// at least `skip_at` the function returns false without touching the other 7
+// corners (phi and the gradient are then not computed).  For an L-Lipschitz
+// field every corner lies within sqrt(3) res of the nearest one, so with
+// skip_at = r + eta + L sqrt(3) res + 1e-5 the interpolated value exceeds
+// r + eta: the hinge is inactive and contributes nothing, exactly as if the
+// interpolation had been done.
+template <bool GRAD, bool SKIP>
+__device__ __forceinline__ bool esdf_sample(const SceneView &sv, float px, float py, float pz, float skip_at,
+                                            float &val, float &gx, float &gy, float &gz) {
     int ix, iy, iz;
     float fx, fy, fz;
     bool cx = grid_axis(px, sv.ox, sv.inv_res, sv.nx, ix, fx);
@@ -84,6 +93,10 @@ __device__ __forceinline__ float esdf_sample(const SceneView &sv, float px, floa
     bool cz = grid_axis(pz, sv.oz, sv.inv_res, sv.nz, iz, fz);
     const size_t sy = (size_t)sv.nx, sz = (size_t)sv.nx * (size_t)sv.ny;
     const float *b = sv.phi + (size_t)iz * sz + (size_t)iy * sy + ix;
+    if (SKIP) {
+        const float *nb = b + (fx >= 0.5f ? 1 : 0) + (fy >= 0.5f ? sy : 0) + (fz >= 0.5f ? sz : 0);
+        if (__ldg(nb) >= skip_at) return false;
+    }
     float v000 = __ldg(b), v100 = __ldg(b + 1);
     float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
     float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
@@ -94,7 +107,7 @@ __device__ __forceinline__ float esdf_sample(const SceneView &sv, float px, floa
     float c11 = fmaf(fx, v111 - v011, v011);
     float c0 = fmaf(fy, c10 - c00, c00);
     float c1 = fmaf(fy, c11 - c01, c01);
-    float val = fmaf(fz, c1 - c0, c0);
+    val = fmaf(fz, c1 - c0, c0);
     if (GRAD) {
         float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
         float dx0 = fmaf(fy, d10 - d00, d00), dx1 = fmaf(fy, d11 - d01, d01);
@@ -103,7 +116,7 @@ __device__ __forceinline__ float esdf_sample(const SceneView &sv, float px, floa
         gy = cy ? 0.0f : fmaf(fz, ey1 - ey0, ey0) * sv.inv_res;
         gz = cz ? 0.0f : (c1 - c0) * sv.inv_res;
     }
-    return val;
+    return true;
 }
 
 // ----------------------------------------------------------------- kinematics
@@ -193,10 +206,13 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             float cx = fmaf(R[0], s.x, fmaf(R[1], s.y, fmaf(R[2], s.z, p[0])));
             float cy = fmaf(R[3], s.x, fmaf(R[4], s.y, fmaf(R[5], s.z, p[1])));
             float cz = fmaf(R[6], s.x, fmaf(R[7], s.y, fmaf(R[8], s.z, p[2])));
-            float gx, gy, gz;
-            float phi = esdf_sample<MODE == MODE_GRAD>(sv, cx, cy, cz, gx, gy, gz);
+            float gx, gy, gz, phi;
+            const float hinge_at = s.w + kc.eta;
+            if (!esdf_sample<MODE == MODE_GRAD, MODE != MODE_EVAL>(sv, cx, cy, cz, hinge_at + sv.skip_pad, phi,
+                                                                   gx, gy, gz))
+                continue;
             if (MODE == MODE_EVAL) acc.min_clear = fminf(acc.min_clear, phi - s.w);
-            float h = s.w + kc.eta - phi;
+            float h = hinge_at - phi;
             if (h > 0.0f) {
                 acc.c_world = fmaf(kc.w_c, h, acc.c_world);
                 if (MODE == MODE_GRAD) {

@@ -1,12 +1,22 @@
 // kernels_esdf.cu -- per-voxel brute-force ESDF of a union of axis-aligned cuboids.
 //
-// One thread per voxel; the cuboids stream through shared memory in chunks, so
-// every box is read from global memory once per block.  For each voxel centre
-// p the kernel keeps, over all boxes, the smallest squared outside distance
+// phi(p) = min(FAR, min_k sdf_k(p)) at every voxel centre p.  For each voxel the
+// kernel keeps, over the boxes, the smallest squared outside distance
 // |max(|p - c| - h, 0)|^2 and the smallest max_i(|p - c|_i - h_i).  If the
 // latter is <= 0 some box contains p and it is the union's signed distance (the
 // deepest-penetration reading of min_k sdf_k); otherwise min_k sdf_k is the
 // square root of the former.  Both equal min_k sdf_k exactly.
+//
+// One block owns an 8x8x8 tile of voxels (one thread per voxel).  Before the
+// per-voxel loop the block drops the boxes that cannot be the minimum anywhere
+// in the tile: sdf_k is convex, so its maximum over the tile is at one of the
+// tile's 8 corner voxel centres (an upper bound U_k), and its minimum over the
+// tile is at least the distance from the tile's box of voxel centres to the
+// cuboid (a lower bound L_k, or -inf when they overlap).  A box with
+// L_k > min_j U_j + 1e-4 is larger than another box's value at every voxel of
+// the tile, so skipping it leaves every min, and every output bit, unchanged;
+// the remaining boxes go through the same per-voxel arithmetic as without the
+// culling.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -14,28 +24,92 @@
 
 namespace dseed {
 
-constexpr int kEsdfThreads = 256;
-constexpr int kEsdfChunk = 256;
+constexpr int kTile = 8;
+constexpr int kEsdfThreads = kTile * kTile * kTile;   // 512
+constexpr int kEsdfChunk = 1024;                      // boxes staged per pass
+
+__device__ __forceinline__ float box_sdf(float px, float py, float pz, const float *bx) {
+    const float dx = fabsf(px - bx[0]) - bx[3];
+    const float dy = fabsf(py - bx[1]) - bx[4];
+    const float dz = fabsf(pz - bx[2]) - bx[5];
+    const float ox = fmaxf(dx, 0.f), oy = fmaxf(dy, 0.f), oz = fmaxf(dz, 0.f);
+    const float in = fmaxf(dx, fmaxf(dy, dz));
+    return sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(in, 0.f);
+}
 
 __global__ void __launch_bounds__(kEsdfThreads)
-    k_esdf_build(const float *__restrict__ cub, int n, DseedGrid g, long long nvox, float *__restrict__ phi) {
+    k_esdf_build(const float *__restrict__ cub, int n, DseedGrid g, float *__restrict__ phi) {
     __shared__ float sb[kEsdfChunk * 6];
-    const long long v = (long long)blockIdx.x * kEsdfThreads + threadIdx.x;
-    const bool live = v < nvox;
-    const long long nxy = (long long)g.nx * g.ny;
-    const int k = live ? (int)(v / nxy) : 0;
-    const long long r = live ? v - (long long)k * nxy : 0;
-    const int j = (int)(r / g.nx), i = (int)(r - (long long)j * g.nx);
+    __shared__ float s_red[kEsdfThreads / 32];
+    __shared__ int s_count;
+    const int tx = blockIdx.x, ty = blockIdx.y, tz = blockIdx.z;
+    const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+    const int i = tx * kTile + lx, j = ty * kTile + ly, k = tz * kTile + lz;
+    const bool live = i < g.nx && j < g.ny && k < g.nz;
     const float px = fmaf((float)i + 0.5f, g.res, g.origin[0]);
     const float py = fmaf((float)j + 0.5f, g.res, g.origin[1]);
     const float pz = fmaf((float)k + 0.5f, g.res, g.origin[2]);
+    // tile extent in voxel centres (the full 8^3 tile, also past the grid edge)
+    float lo[3], hi[3];
+    lo[0] = fmaf((float)(tx * kTile) + 0.5f, g.res, g.origin[0]);
+    lo[1] = fmaf((float)(ty * kTile) + 0.5f, g.res, g.origin[1]);
+    lo[2] = fmaf((float)(tz * kTile) + 0.5f, g.res, g.origin[2]);
+    hi[0] = fmaf((float)(tx * kTile + kTile - 1) + 0.5f, g.res, g.origin[0]);
+    hi[1] = fmaf((float)(ty * kTile + kTile - 1) + 0.5f, g.res, g.origin[1]);
+    hi[2] = fmaf((float)(tz * kTile + kTile - 1) + 0.5f, g.res, g.origin[2]);
+
+    // pass 1: tau = min over boxes of the max of sdf_k over the tile corners
+    float ub = CUDART_INF_F;
+    for (int b = threadIdx.x; b < n; b += kEsdfThreads) {
+        float bx[6];
+#pragma unroll
+        for (int c = 0; c < 6; ++c) bx[c] = cub[(size_t)b * 6 + c];
+        float m = -CUDART_INF_F;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            m = fmaxf(m, box_sdf((c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2], bx));
+        ub = fminf(ub, m);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
+    if ((threadIdx.x & 31) == 0) s_red[threadIdx.x >> 5] = ub;
+    __syncthreads();
+    float tau = s_red[0];
+#pragma unroll
+    for (int w = 1; w < kEsdfThreads / 32; ++w) tau = fminf(tau, s_red[w]);
+    tau += 1e-4f;
+
+    // pass 2: per chunk, keep the boxes whose lower bound over the tile is <= tau
     float out2 = CUDART_INF_F, in = CUDART_INF_F;
     for (int c0 = 0; c0 < n; c0 += kEsdfChunk) {
         const int cnt = min(kEsdfChunk, n - c0);
         __syncthreads();
-        for (int t = threadIdx.x; t < cnt * 6; t += kEsdfThreads) sb[t] = cub[(size_t)c0 * 6 + t];
+        if (threadIdx.x == 0) s_count = 0;
         __syncthreads();
-        for (int q = 0; q < cnt; ++q) {
+        for (int b = threadIdx.x; b < cnt; b += kEsdfThreads) {
+            const float *src = cub + (size_t)(c0 + b) * 6;
+            float bx[6];
+#pragma unroll
+            for (int c = 0; c < 6; ++c) bx[c] = src[c];
+            float gap2 = 0.f;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const float gl = (bx[a] - bx[3 + a]) - hi[a];   // box above the tile
+                const float gh = lo[a] - (bx[a] + bx[3 + a]);   // box below the tile
+                const float gap = fmaxf(fmaxf(gl, gh), 0.f);
+                gap2 = fmaf(gap, gap, gap2);
+            }
+            // gap2 == 0: the boxes overlap, no useful lower bound
+            const float lb = gap2 > 0.f ? sqrtf(gap2) : -CUDART_INF_F;
+            if (lb <= tau) {
+                const int slot = atomicAdd(&s_count, 1);
+#pragma unroll
+                for (int c = 0; c < 6; ++c) sb[slot * 6 + c] = bx[c];
+            }
+        }
+        __syncthreads();
+        const int kept = s_count;
+        for (int q = 0; q < kept; ++q) {
             const float *bx = sb + q * 6;
             const float dx = fabsf(px - bx[0]) - bx[3];
             const float dy = fabsf(py - bx[1]) - bx[4];
@@ -47,14 +121,15 @@ __global__ void __launch_bounds__(kEsdfThreads)
     }
     if (live) {
         const float s = in <= 0.f ? in : sqrtf(out2);
-        phi[v] = fminf(s, DSEED_ESDF_FAR);
+        phi[((size_t)k * g.ny + j) * g.nx + i] = fminf(s, DSEED_ESDF_FAR);
     }
 }
 
 int launch_esdf_build(const float *cuboids, int n, const DseedGrid &g, float *esdf, cudaStream_t st) {
     const long long nvox = (long long)g.nx * g.ny * g.nz;
     if (nvox == 0) return cudaSuccess;
-    k_esdf_build<<<(unsigned)((nvox + kEsdfThreads - 1) / kEsdfThreads), kEsdfThreads, 0, st>>>(cuboids, n, g, nvox, esdf);
+    const dim3 grid((g.nx + kTile - 1) / kTile, (g.ny + kTile - 1) / kTile, (g.nz + kTile - 1) / kTile);
+    k_esdf_build<<<grid, kEsdfThreads, 0, st>>>(cuboids, n, g, esdf);
     return (int)cudaGetLastError();
 }
 

@@ -121,8 +121,8 @@ class CostParams:
     w_v: float = 1e-2       # velocity weight
     w_a: float = 1e-4       # acceleration weight
     w_j: float = 1e-6       # jerk weight
-    w_p: float = 1e3        # goal position weight
-    w_R: float = 1e2        # goal orientation weight
+    w_p: float = 1e4        # goal position weight
+    w_R: float = 1e3        # goal orientation weight
     w_l: float = 1e3        # joint-limit weight
 
     def as_array(self) -> np.ndarray:

@@ -177,7 +177,7 @@ def batched_full():
 
 def test_full_batched_plan_sampled_parity(gpu_lib, batched_full):
     """256 problems x 64 seeds x 32 waypoints, 100 iterations, in one plan call (as
-    timed by the benchmark); the oracle re-plans a 1% seed sample one by one."""
+    timed by the benchmark); the oracle re-plans a 2% seed sample one by one."""
     wl, orc = batched_full
     planner, batch = gpu_side(wl)
     out = planner.plan(batch, wl.seeds)
@@ -185,7 +185,7 @@ def test_full_batched_plan_sampled_parity(gpu_lib, batched_full):
     ok = to_np(out["success"]).astype(bool)
     cost = to_np(out["cost"])
     rng = np.random.default_rng(2)
-    flat = rng.choice(wl.P * wl.S, size=(wl.P * wl.S) // 100, replace=False)
+    flat = rng.choice(wl.P * wl.S, size=(wl.P * wl.S) // 50, replace=False)
     pp, ss = flat // wl.S, flat % wl.S
     agree = []
     rels = []
