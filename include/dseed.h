@@ -264,6 +264,43 @@ int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const D
                      float *traj_dev, float *cost_dev, uint8_t *success_dev, float *metrics_dev,
                      int *best_dev, cudaStream_t stream);
 
+/* ------------------------------------------------ plan without allocation */
+
+/* The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory.  Examples: a control loop that has frozen
+ * its memory after start-up, a plug-in running inside a host process whose
+ * allocator it may not touch, or code that must not trigger the implicit
+ * synchronisation a cudaMalloc/cudaFree can cause.  Such a caller cannot
+ * provide the workspace dseed_plan_batch asks for.
+ *
+ * dseed_plan_batch_static does the same work as dseed_plan_batch (same
+ * kernels, same results) but keeps its scratch (the L-BFGS history and the
+ * per-problem best-seed keys) in one array of DSEED_STATIC_SCRATCH_BYTES
+ * bytes that lives in the library itself, as a file-scope device variable.
+ * The caller still passes every input and output buffer.  The call never
+ * allocates: no cudaMalloc, no cudaFree, no allocating library routine.
+ *
+ * Limits and rules:
+ *   - The scratch needed is what dseed_plan_workspace_bytes reports for
+ *     `desc`; a batch needing more than DSEED_STATIC_SCRATCH_BYTES is refused
+ *     with DSEED_ENOMEM and a message giving both sizes (for T = 32 and m = 5
+ *     that is about 3700 seeds per call).
+ *   - Every GPU on which the library's device code is loaded holds the array
+ *     until the process exits.
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current) and caches it; make that first call before any
+ *     stream capture begins.
+ *   - All calls share the one array, and it keeps what the last call left in
+ *     it.  The call resets the parts that must start at zero itself, but two
+ *     calls whose work overlaps on the GPU (different streams without
+ *     ordering, or different host threads) race on the array: order them. */
+#define DSEED_STATIC_SCRATCH_BYTES (32u << 20)
+
+int dseed_plan_batch_static(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                            const float *seeds_dev, float *traj_dev, float *cost_dev,
+                            uint8_t *success_dev, float *metrics_dev, int *best_dev,
+                            cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

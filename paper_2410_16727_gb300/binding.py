@@ -86,7 +86,11 @@ _SIGS = {
     "dseed_plan_workspace_bytes": ([C.POINTER(PlanDesc), C.POINTER(C.c_size_t)], C.c_int),
     "dseed_plan_batch": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_size_t,
                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_plan_batch_static": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
+
+STATIC_SCRATCH_BYTES = 32 << 20
 
 
 def library_path() -> str:
@@ -349,4 +353,29 @@ def plan_batch(robot: Robot, desc: PlanDesc, pr: Problems, seeds: torch.Tensor, 
                                    _dev(out["success"], torch.uint8, "success", (P, S)),
                                    met.data_ptr() if met is not None else None,
                                    _dev(out["best"], torch.int32, "best", (P,)), _stream()), "dseed_plan_batch")
+    return out
+
+
+def plan_batch_static(robot: Robot, desc: PlanDesc, pr: Problems, seeds: torch.Tensor,
+                      out: Optional[dict] = None) -> dict:
+    """dseed_plan_batch_static: the fused optimiser with the library's own static
+    scratch instead of a caller workspace, for callers that may not allocate
+    device memory (the outputs must then be preallocated and passed in `out`)."""
+    P, S, T = desc.P, desc.S, desc.T
+    dev = seeds.device
+    if out is None:
+        out = dict(traj=torch.empty((P, S, T, 7), dtype=torch.float32, device=dev),
+                   cost=torch.empty((P, S), dtype=torch.float32, device=dev),
+                   success=torch.empty((P, S), dtype=torch.uint8, device=dev),
+                   metrics=torch.empty((P, S, N_METRICS), dtype=torch.float32, device=dev),
+                   best=torch.empty((P,), dtype=torch.int32, device=dev))
+    met = out.get("metrics")
+    _check(load().dseed_plan_batch_static(robot.handle, C.byref(desc), C.byref(pr),
+                                          _dev(seeds, torch.float32, "seeds", (P, S, T, 7)),
+                                          _dev(out["traj"], torch.float32, "traj", (P, S, T, 7)),
+                                          _dev(out["cost"], torch.float32, "cost", (P, S)),
+                                          _dev(out["success"], torch.uint8, "success", (P, S)),
+                                          met.data_ptr() if met is not None else None,
+                                          _dev(out["best"], torch.int32, "best", (P,)), _stream()),
+           "dseed_plan_batch_static")
     return out

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -351,3 +352,58 @@ int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const D
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- plan without allocation
+// Scratch of dseed_plan_batch_static: one file-scope device array.  Host code
+// may not use the symbol as an address (on the host it names a stand-in);
+// its device address is looked up once per device with that device current.
+static __device__ __align__(256) unsigned char g_plan_scratch[DSEED_STATIC_SCRATCH_BYTES];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_scratch_mutex;
+void *g_scratch_ptr[kMaxDevices] = {};
+
+int static_scratch(void **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return fail(DSEED_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+    if (dev < 0 || dev >= kMaxDevices) return fail(DSEED_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mutex);
+    if (!g_scratch_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_plan_scratch);
+        if (e != cudaSuccess)
+            return fail(DSEED_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+        g_scratch_ptr[dev] = p;
+    }
+    *out = g_scratch_ptr[dev];
+    return DSEED_OK;
+}
+}  // namespace
+
+extern "C" int dseed_plan_batch_static(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
+                                       const float *seeds_dev, float *traj_dev, float *cost_dev,
+                                       uint8_t *success_dev, float *metrics_dev, int *best_dev, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    int r = check_desc(desc, true);
+    if (r) return r;
+    if ((r = check_problems(desc, pr))) return r;
+    if (desc->P == 0) return DSEED_OK;
+    if (!seeds_dev || !traj_dev || !cost_dev || !success_dev || !best_dev)
+        return fail(DSEED_EINVAL, "a plan buffer is NULL");
+    const PlanLayout l = plan_layout(desc);
+    if (l.total > (size_t)DSEED_STATIC_SCRATCH_BYTES)
+        return fail(DSEED_ENOMEM, "batch needs %zu bytes of scratch, the static scratch holds %zu", l.total,
+                    (size_t)DSEED_STATIC_SCRATCH_BYTES);
+    void *base = nullptr;
+    if ((r = static_scratch(&base))) return r;
+    char *w = static_cast<char *>(base);
+    // launch_plan resets the best-seed keys; the history is written before it is read
+    return cuda_status(dseed::launch_plan(robot->k, make_cost(desc->cost), make_opt(desc->opt), make_batch(desc, pr),
+                                          seeds_dev, reinterpret_cast<float *>(w + l.s),
+                                          reinterpret_cast<float *>(w + l.y),
+                                          reinterpret_cast<unsigned long long *>(w + l.key), traj_dev, cost_dev,
+                                          success_dev, metrics_dev, best_dev, stream),
+                       "plan (static scratch)");
+}
