@@ -221,13 +221,14 @@ typedef struct {
     size_t x;         /* float [B][n] accepted point */
     size_t g;         /* float [B][n] gradient at x */
     size_t x_trial;   /* float [B][n] next trial point (read by the caller's evaluation) */
-    size_t s;         /* float [B][m][n] history s_i */
-    size_t y;         /* float [B][m][n] history y_i */
-    size_t rho;       /* float [B][m] 1 / s_i^T y_i */
+    size_t d;         /* float [B][n] current search direction */
+    size_t s;         /* float [B][m][n] history s_i, by ring slot */
+    size_t y;         /* float [B][m][n] history y_i, by ring slot */
+    size_t rho;       /* float [B][8] 1 / s_i^T y_i, by ring slot */
+    size_t yy;        /* float [B] y^T y of the newest pair */
     size_t f;         /* float [B] cost at x (+inf before the first evaluation) */
     size_t alpha;     /* float [B] step length */
     size_t gts;       /* float [B] g^T (x_trial - x) */
-    size_t yy;        /* float [B] y^T y of the newest pair */
     size_t meta;      /* int [B][4] history count, newest slot, first-evaluation flag, accepts */
     size_t total;     /* bytes of the whole state */
 } DseedLbfgsLayout;

@@ -59,7 +59,7 @@ class Problems(C.Structure):
 
 
 class LbfgsLayout(C.Structure):
-    _fields_ = [(k, C.c_size_t) for k in ("x", "g", "x_trial", "s", "y", "rho", "f", "alpha", "gts", "yy",
+    _fields_ = [(k, C.c_size_t) for k in ("x", "g", "x_trial", "d", "s", "y", "rho", "yy", "f", "alpha", "gts",
                                           "meta", "total")]
 
 
@@ -311,8 +311,8 @@ def lbfgs_step(desc: PlanDesc, f_trial: torch.Tensor, g_trial: torch.Tensor, sta
 def lbfgs_view(state: torch.Tensor, lay: LbfgsLayout, desc: PlanDesc, name: str) -> torch.Tensor:
     """A typed view of one array of the L-BFGS state buffer."""
     B, n, m = desc.P * desc.S, 7 * desc.T, desc.opt.m
-    shapes = {"x": (B, n), "g": (B, n), "x_trial": (B, n), "s": (B, m, n), "y": (B, m, n), "rho": (B, m),
-              "f": (B,), "alpha": (B,), "gts": (B,), "yy": (B,), "meta": (B, 4)}
+    shapes = {"x": (B, n), "g": (B, n), "x_trial": (B, n), "d": (B, n), "s": (B, m, n), "y": (B, m, n),
+              "rho": (B, 8), "yy": (B,), "f": (B,), "alpha": (B,), "gts": (B,), "meta": (B, 4)}
     shape = shapes[name]
     count = 1
     for s in shape:

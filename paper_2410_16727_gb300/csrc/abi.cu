@@ -124,13 +124,14 @@ DseedLbfgsLayout lbfgs_layout(long long B, int n, int m) {
     l.x = take(sizeof(float) * B * n);
     l.g = take(sizeof(float) * B * n);
     l.x_trial = take(sizeof(float) * B * n);
+    l.d = take(sizeof(float) * B * n);
     l.s = take(sizeof(float) * B * m * n);
     l.y = take(sizeof(float) * B * m * n);
-    l.rho = take(sizeof(float) * B * m);
+    l.rho = take(sizeof(float) * B * 8);
+    l.yy = take(sizeof(float) * B);
     l.f = take(sizeof(float) * B);
     l.alpha = take(sizeof(float) * B);
     l.gts = take(sizeof(float) * B);
-    l.yy = take(sizeof(float) * B);
     l.meta = take(sizeof(int) * B * 4);
     l.total = off;
     return l;
@@ -142,13 +143,14 @@ dseed::KLbfgsPtrs lbfgs_ptrs(void *base, const DseedLbfgsLayout &l) {
     p.x = reinterpret_cast<float *>(c + l.x);
     p.g = reinterpret_cast<float *>(c + l.g);
     p.x_trial = reinterpret_cast<float *>(c + l.x_trial);
+    p.d = reinterpret_cast<float *>(c + l.d);
     p.s = reinterpret_cast<float *>(c + l.s);
     p.y = reinterpret_cast<float *>(c + l.y);
     p.rho = reinterpret_cast<float *>(c + l.rho);
+    p.yy = reinterpret_cast<float *>(c + l.yy);
     p.f = reinterpret_cast<float *>(c + l.f);
     p.alpha = reinterpret_cast<float *>(c + l.alpha);
     p.gts = reinterpret_cast<float *>(c + l.gts);
-    p.yy = reinterpret_cast<float *>(c + l.yy);
     p.meta = reinterpret_cast<int *>(c + l.meta);
     return p;
 }

@@ -59,64 +59,62 @@ __device__ __forceinline__ SceneView load_scene(const DseedScene *scenes, int id
     return v;
 }
 
-// Continuous voxel coordinate along one axis, clamped into the grid; cell index
-// and fraction.  Returns true when the point lay outside (gradient zero there).
-// NaN and infinities land on a valid cell (fmaxf/fminf drop NaN), so no access
-// can leave the grid.
-__device__ __forceinline__ bool grid_axis(float p, float o, float inv_res, int n, int &i0, float &f) {
-    float u = (p - o) * inv_res - 0.5f;
-    float hi = (float)(n - 1);
-    bool clamped = !(u >= 0.0f && u <= hi);
+// Cell of a continuous voxel coordinate u = (p - origin) / res - 1/2 along one
+// axis: u is clamped into [0, n - 1], the cell is i0 = min(floor(u), n - 2)
+// and f = u - i0.  Returns true when the point lay outside the grid (the
+// gradient is zero along that axis).  NaN and infinities land on a valid cell
+// (fmaxf/fminf drop NaN), so no access can leave the grid.
+__device__ __forceinline__ bool cell_axis(float u, int n, int &i0, float &f) {
+    const float hi = (float)(n - 1);
+    const bool clamped = !(u >= 0.0f && u <= hi);
     u = fminf(fmaxf(u, 0.0f), hi);
-    int c = min((int)floorf(u), n - 2);
+    const int c = min(__float2int_rd(u), n - 2);
     i0 = c;
     f = u - (float)c;
     return clamped;
 }
 
-// Trilinear interpolation of the ESDF at (px, py, pz) from the 8 corners of its
-// cell (point loads through the read-only path), with the analytic gradient.
-// With SKIP, the corner nearest to the point is read first; when its value is
-// at least `skip_at` the function returns false without touching the other 7
-// corners (phi and the gradient are then not computed).  For an L-Lipschitz
-// field every corner lies within sqrt(3) res of the nearest one, so with
-// skip_at = r + eta + L sqrt(3) res + 1e-5 the interpolated value exceeds
-// r + eta: the hinge is inactive and contributes nothing, exactly as if the
-// interpolation had been done.
-template <bool GRAD, bool SKIP>
-__device__ __forceinline__ bool esdf_sample(const SceneView &sv, float px, float py, float pz, float skip_at,
-                                            float &val, float &gx, float &gy, float &gz) {
+// Cell index only (the corner (i0, j0, k0) of the cell that holds u).
+__device__ __forceinline__ int cell_index(float u, int n) {
+    return min(__float2int_rd(fminf(fmaxf(u, 0.0f), (float)(n - 1))), n - 2);
+}
+
+__device__ __forceinline__ const float *cell_ptr(const SceneView &sv, int ix, int iy, int iz) {
+    return sv.phi + ((size_t)iz * (size_t)sv.ny + (size_t)iy) * (size_t)sv.nx + ix;
+}
+
+// Trilinear interpolation of the ESDF at voxel coordinates (ux, uy, uz) from
+// the 8 corners of its cell (point loads through the read-only path), with the
+// analytic gradient in world units (d phi / d u divided by res).
+template <bool GRAD>
+__device__ __forceinline__ float esdf_interp(const SceneView &sv, float ux, float uy, float uz,
+                                             float &gx, float &gy, float &gz) {
     int ix, iy, iz;
     float fx, fy, fz;
-    bool cx = grid_axis(px, sv.ox, sv.inv_res, sv.nx, ix, fx);
-    bool cy = grid_axis(py, sv.oy, sv.inv_res, sv.ny, iy, fy);
-    bool cz = grid_axis(pz, sv.oz, sv.inv_res, sv.nz, iz, fz);
+    const bool cx = cell_axis(ux, sv.nx, ix, fx);
+    const bool cy = cell_axis(uy, sv.ny, iy, fy);
+    const bool cz = cell_axis(uz, sv.nz, iz, fz);
     const size_t sy = (size_t)sv.nx, sz = (size_t)sv.nx * (size_t)sv.ny;
-    const float *b = sv.phi + (size_t)iz * sz + (size_t)iy * sy + ix;
-    if (SKIP) {
-        const float *nb = b + (fx >= 0.5f ? 1 : 0) + (fy >= 0.5f ? sy : 0) + (fz >= 0.5f ? sz : 0);
-        if (__ldg(nb) >= skip_at) return false;
-    }
-    float v000 = __ldg(b), v100 = __ldg(b + 1);
-    float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
-    float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
-    float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
-    float c00 = fmaf(fx, v100 - v000, v000);
-    float c10 = fmaf(fx, v110 - v010, v010);
-    float c01 = fmaf(fx, v101 - v001, v001);
-    float c11 = fmaf(fx, v111 - v011, v011);
-    float c0 = fmaf(fy, c10 - c00, c00);
-    float c1 = fmaf(fy, c11 - c01, c01);
-    val = fmaf(fz, c1 - c0, c0);
+    const float *b = cell_ptr(sv, ix, iy, iz);
+    const float v000 = __ldg(b), v100 = __ldg(b + 1);
+    const float v010 = __ldg(b + sy), v110 = __ldg(b + sy + 1);
+    const float v001 = __ldg(b + sz), v101 = __ldg(b + sz + 1);
+    const float v011 = __ldg(b + sz + sy), v111 = __ldg(b + sz + sy + 1);
+    const float c00 = fmaf(fx, v100 - v000, v000);
+    const float c10 = fmaf(fx, v110 - v010, v010);
+    const float c01 = fmaf(fx, v101 - v001, v001);
+    const float c11 = fmaf(fx, v111 - v011, v011);
+    const float c0 = fmaf(fy, c10 - c00, c00);
+    const float c1 = fmaf(fy, c11 - c01, c01);
     if (GRAD) {
-        float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
-        float dx0 = fmaf(fy, d10 - d00, d00), dx1 = fmaf(fy, d11 - d01, d01);
-        float ey0 = c10 - c00, ey1 = c11 - c01;
+        const float d00 = v100 - v000, d10 = v110 - v010, d01 = v101 - v001, d11 = v111 - v011;
+        const float dx0 = fmaf(fy, d10 - d00, d00), dx1 = fmaf(fy, d11 - d01, d01);
+        const float ey0 = c10 - c00, ey1 = c11 - c01;
         gx = cx ? 0.0f : fmaf(fz, dx1 - dx0, dx0) * sv.inv_res;
         gy = cy ? 0.0f : fmaf(fz, ey1 - ey0, ey0) * sv.inv_res;
         gz = cz ? 0.0f : (c1 - c0) * sv.inv_res;
     }
-    return true;
+    return fmaf(fz, c1 - c0, c0);
 }
 
 // ----------------------------------------------------------------- kinematics
@@ -163,6 +161,12 @@ __device__ __forceinline__ Goal make_goal(const float *g) {
 
 enum { MODE_COST = 0, MODE_GRAD = 1, MODE_EVAL = 2 };
 
+// Spheres of one frame whose first ESDF loads are issued together.
+#ifndef DSEED_SPHERE_BATCH
+#define DSEED_SPHERE_BATCH 1
+#endif
+constexpr int kSphereBatch = DSEED_SPHERE_BATCH;
+
 struct WaypointAcc {
     float c_world, c_goal;
     float min_clear;          // MODE_EVAL
@@ -177,50 +181,91 @@ struct WaypointAcc {
 // that is z_i . (M_all - M_<i) - (z_i x p_i) . (F_all - F_<i): the prefix
 // part b_i is recorded when frame i is reached, the rest once all spheres and
 // the goal wrench are in.
+#ifndef DSEED_ADJOINT_RECOMPUTE
+#define DSEED_ADJOINT_RECOMPUTE 1
+#endif
+
 template <int MODE>
 __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc, const SceneView &sv,
                                                const float (&q)[7], bool last, const Goal &G,
                                                WaypointAcc &acc, float (&gq)[7]) {
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
-    float zj[7][3], wj[7][3], bj[7];
+    constexpr bool KEEP = MODE == MODE_GRAD && !DSEED_ADJOINT_RECOMPUTE;
+    float zj[KEEP ? 7 : 1][3], wj[KEEP ? 7 : 1][3], bj[7], sn[7], cs[7];
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
 #pragma unroll
     for (int L = 1; L <= 8; ++L) {
         float st, ct, th = rb.off[L - 1];
         if (L <= 7) th += q[L <= 7 ? L - 1 : 0];
         sincosf(th, &st, &ct);
+        if (L <= 7) { sn[L <= 7 ? L - 1 : 0] = st; cs[L <= 7 ? L - 1 : 0] = ct; }
         dh_step(R, p, rb.a[L - 1], rb.d[L - 1], rb.ca[L - 1], rb.sa[L - 1], ct, st);
         if (MODE == MODE_GRAD && L <= 7) {
+            const int i = L <= 7 ? L - 1 : 0;
             float z0 = R[2], z1 = R[5], z2 = R[8];
             float w0 = z1 * p[2] - z2 * p[1];
             float w1 = z2 * p[0] - z0 * p[2];
             float w2 = z0 * p[1] - z1 * p[0];
-            zj[L - 1][0] = z0; zj[L - 1][1] = z1; zj[L - 1][2] = z2;
-            wj[L - 1][0] = w0; wj[L - 1][1] = w1; wj[L - 1][2] = w2;
-            bj[L - 1] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
+            if (KEEP) {
+                const int ii = KEEP ? i : 0;
+                zj[ii][0] = z0; zj[ii][1] = z1; zj[ii][2] = z2;
+                wj[ii][0] = w0; wj[ii][1] = w1; wj[ii][2] = w2;
+            }
+            bj[i] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
         }
+        // frame L in voxel coordinates: u = Rv o + pv for an offset o
+        float Rv[9], pv[3];
+#pragma unroll
+        for (int r = 0; r < 9; ++r) Rv[r] = R[r] * sv.inv_res;
+        pv[0] = fmaf(p[0] - sv.ox, sv.inv_res, -0.5f);
+        pv[1] = fmaf(p[1] - sv.oy, sv.inv_res, -0.5f);
+        pv[2] = fmaf(p[2] - sv.oz, sv.inv_res, -0.5f);
         const int k1 = rb.frame_begin[L];
-        for (int k = rb.frame_begin[L - 1]; k < k1; ++k) {
-            const float4 s = rb.sph[k];
-            float cx = fmaf(R[0], s.x, fmaf(R[1], s.y, fmaf(R[2], s.z, p[0])));
-            float cy = fmaf(R[3], s.x, fmaf(R[4], s.y, fmaf(R[5], s.z, p[1])));
-            float cz = fmaf(R[6], s.x, fmaf(R[7], s.y, fmaf(R[8], s.z, p[2])));
-            float gx, gy, gz, phi;
-            const float hinge_at = s.w + kc.eta;
-            if (!esdf_sample<MODE == MODE_GRAD, MODE != MODE_EVAL>(sv, cx, cy, cz, hinge_at + sv.skip_pad, phi,
-                                                                   gx, gy, gz))
-                continue;
-            if (MODE == MODE_EVAL) acc.min_clear = fminf(acc.min_clear, phi - s.w);
-            float h = hinge_at - phi;
-            if (h > 0.0f) {
-                acc.c_world = fmaf(kc.w_c, h, acc.c_world);
-                if (MODE == MODE_GRAD) {
-                    float fx = -kc.w_c * gx, fy = -kc.w_c * gy, fz = -kc.w_c * gz;
-                    Fx += fx; Fy += fy; Fz += fz;
-                    Mx += cy * fz - cz * fy;
-                    My += cz * fx - cx * fz;
-                    Mz += cx * fy - cy * fx;
+        for (int k0 = rb.frame_begin[L - 1]; k0 < k1; k0 += kSphereBatch) {
+            // phase 1: one corner of each sphere's cell, all loads in flight together.
+            // Every corner of a cell lies within sqrt(3) res of the others, so for an
+            // L-Lipschitz field phi(c) >= v0 - L sqrt(3) res: when v0 >= r + eta +
+            // skip_pad the hinge is inactive and the sphere contributes nothing.
+            float v0[kSphereBatch];
+#pragma unroll
+            for (int c = 0; c < kSphereBatch; ++c) {
+                v0[c] = -CUDART_INF_F;
+                if (MODE != MODE_EVAL && k0 + c < k1) {
+                    const float4 s = rb.sph[k0 + c];
+                    const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
+                    const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
+                    const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
+                    v0[c] = __ldg(cell_ptr(sv, cell_index(ux, sv.nx), cell_index(uy, sv.ny), cell_index(uz, sv.nz)));
+                }
+            }
+            // phase 2: full interpolation of the spheres the bound cannot clear
+#pragma unroll
+            for (int c = 0; c < kSphereBatch; ++c) {
+                if (k0 + c >= k1) continue;
+                const float4 s = rb.sph[k0 + c];
+                const float hinge_at = s.w + kc.eta;
+                if (MODE != MODE_EVAL && v0[c] >= hinge_at + sv.skip_pad) continue;
+                const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
+                const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
+                const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
+                float gx, gy, gz;
+                const float phi = esdf_interp<MODE == MODE_GRAD>(sv, ux, uy, uz, gx, gy, gz);
+                if (MODE == MODE_EVAL) acc.min_clear = fminf(acc.min_clear, phi - s.w);
+                const float h = hinge_at - phi;
+                if (h > 0.0f) {
+                    acc.c_world = fmaf(kc.w_c, h, acc.c_world);
+                    if (MODE == MODE_GRAD) {
+                        // moment about the world origin needs the centre in world units
+                        const float cx = fmaf(R[0], s.x, fmaf(R[1], s.y, fmaf(R[2], s.z, p[0])));
+                        const float cy = fmaf(R[3], s.x, fmaf(R[4], s.y, fmaf(R[5], s.z, p[1])));
+                        const float cz = fmaf(R[6], s.x, fmaf(R[7], s.y, fmaf(R[8], s.z, p[2])));
+                        const float fx = -kc.w_c * gx, fy = -kc.w_c * gy, fz = -kc.w_c * gz;
+                        Fx += fx; Fy += fy; Fz += fz;
+                        Mx += cy * fz - cz * fy;
+                        My += cz * fx - cx * fz;
+                        Mz += cx * fy - cy * fx;
+                    }
                 }
             }
         }
@@ -258,10 +303,29 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
         }
     }
     if (MODE == MODE_GRAD) {
+        if (KEEP) {
 #pragma unroll
-        for (int i = 0; i < 7; ++i)
-            gq[i] += (zj[i][0] * Mx + zj[i][1] * My + zj[i][2] * Mz)
-                     - (wj[i][0] * Fx + wj[i][1] * Fy + wj[i][2] * Fz) - bj[i];
+            for (int i = 0; i < 7; ++i) {
+                const int ii = KEEP ? i : 0;
+                gq[i] += (zj[ii][0] * Mx + zj[ii][1] * My + zj[ii][2] * Mz)
+                         - (wj[ii][0] * Fx + wj[ii][1] * Fy + wj[ii][2] * Fz) - bj[i];
+            }
+        } else {
+            // second pass: rebuild the joint axes z_i and origins p_i from the
+            // stored sin/cos (bit-identical to the first pass) instead of keeping
+            // 42 values per waypoint live across the sphere loop
+            float R2[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
+            float p2[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int i = 0; i < 7; ++i) {
+                dh_step(R2, p2, rb.a[i], rb.d[i], rb.ca[i], rb.sa[i], cs[i], sn[i]);
+                const float z0 = R2[2], z1 = R2[5], z2 = R2[8];
+                const float w0 = z1 * p2[2] - z2 * p2[1];
+                const float w1 = z2 * p2[0] - z0 * p2[2];
+                const float w2 = z0 * p2[1] - z1 * p2[0];
+                gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i];
+            }
+        }
     }
 }
 
@@ -270,12 +334,13 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
 //   xs [(T + 3) * 7]   y_-2, y_-1, y_0 (= q_start) then the trial waypoints 1..T
 //   es [3 * (T + 3) * 7] velocity / acceleration / jerk adjoint weights, rows >= T zero
 //   gs [T * 7]         gradient of the trial point
-//   xa [T * 7], ga [T * 7]  accepted point and its gradient (optimiser only)
-//   rho [8], al [8]    L-BFGS scalars
-__host__ __device__ constexpr int warp_smem_floats(int T) { return 4 * (T + kPad) * 7 + 3 * 7 * T + 16; }
+//   xa, ga, dd [T * 7] accepted point, its gradient, current search direction (optimiser)
+//   v [32]             L-BFGS scalars: rho per slot [0, 8), y^T y of the newest pair [8],
+//                      alpha_i of the two-loop [16, 24)
+__host__ __device__ constexpr int warp_smem_floats(int T) { return 4 * (T + kPad) * 7 + 4 * 7 * T + 32; }
 
 struct WarpSmem {
-    float *xs, *es, *gs, *xa, *ga, *rho, *al;
+    float *xs, *es, *gs, *xa, *ga, *dd, *v;
 };
 
 __device__ __forceinline__ WarpSmem carve(float *base, int T) {
@@ -285,8 +350,8 @@ __device__ __forceinline__ WarpSmem carve(float *base, int T) {
     w.gs = w.es + 3 * (T + kPad) * 7;
     w.xa = w.gs + T * 7;
     w.ga = w.xa + T * 7;
-    w.rho = w.ga + T * 7;
-    w.al = w.rho + 8;
+    w.dd = w.ga + T * 7;
+    w.v = w.dd + T * 7;
     return w;
 }
 
@@ -398,31 +463,33 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
 // ----------------------------------------------------------------- L-BFGS
 // Warp-uniform scalars of one seed's optimiser state.
 struct LbUni {
-    float f, alpha, gts, yy;
+    float f, alpha, gts;
     int hist, newest, first, accepts;
 };
 
+__device__ __forceinline__ int ring_prev(int k, int m) { return k == 0 ? m - 1 : k - 1; }
+__device__ __forceinline__ int ring_next(int k, int m) { return k + 1 == m ? 0 : k + 1; }
+
 // One L-BFGS update in the flat mapping (lane owns entries lane + 32 i of the
-// n = 7T vector; NPL >= ceil(n / 32)).  Reads the trial point xt and its
-// gradient gt and cost ft; updates the accepted point xa / ga and the history
-// S, Y ([m][n], global) with rho (shared); writes the next trial point into
-// xt_next (may alias xt).  Matches DseedOptParams.
-template <int NPL>
+// n = 7T vector; NPL >= ceil(n / 32)), matching DseedOptParams: Armijo
+// accept/reject of the trial point (xt, gt, ft), history push, the direction
+// d = -H g by the two-loop recursion, and the next trial point into xt_next
+// (may alias xt).  S, Y: this seed's history [m][n] in global memory, by ring
+// slot; rho = 1 / s^T y per slot in ws.v[0..m), y^T y of the newest pair in
+// ws.v[8].  With MH > 0 (m <= MH) the history is first loaded into registers
+// so the two loops wait on one round of loads instead of one per pair.  After
+// a rejected trial g and the history are unchanged, so the stored direction
+// ws.dd is reused (the recursion would give the same numbers).
+template <int NPL, int MH>
 __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, const float *xt,
-                                             const float *gt, float ft, float *xa, float *ga,
-                                             float *__restrict__ S, float *__restrict__ Y, float *rho,
-                                             float *al, float *xt_next) {
+                                             const float *gt, float ft, const WarpSmem &ws,
+                                             float *__restrict__ S, float *__restrict__ Y, float *xt_next) {
     const int lane = threadIdx.x & 31;
     const int m = ko.m;
+    bool new_dir = false, accepted = false;
     if (st.first) {
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int e = lane + 32 * i;
-            if (e < n) { xa[e] = xt[e]; ga[e] = gt[e]; }
-        }
-        st.f = ft;
         st.first = 0;
-        st.accepts += 1;
+        accepted = true;
     } else if (ft <= st.f + ko.c1 * st.gts) {
         float sy = 0.f, ss = 0.f, yy = 0.f;
         float sv[NPL], yv[NPL];
@@ -430,7 +497,7 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
         for (int i = 0; i < NPL; ++i) {
             const int e = lane + 32 * i;
             sv[i] = 0.f; yv[i] = 0.f;
-            if (e < n) { sv[i] = xt[e] - xa[e]; yv[i] = gt[e] - ga[e]; }
+            if (e < n) { sv[i] = xt[e] - ws.xa[e]; yv[i] = gt[e] - ws.ga[e]; }
             sy = fmaf(sv[i], yv[i], sy);
             ss = fmaf(sv[i], sv[i], ss);
             yy = fmaf(yv[i], yv[i], yy);
@@ -439,90 +506,154 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
         ss = warp_sum(ss);
         yy = warp_sum(yy);
         if (sy > 1e-10f * sqrtf(ss) * sqrtf(yy)) {
-            const int k = (st.newest + 1) % m;
+            const int k = st.newest < 0 ? 0 : ring_next(st.newest, m);
 #pragma unroll
             for (int i = 0; i < NPL; ++i) {
                 const int e = lane + 32 * i;
                 if (e < n) { S[(size_t)k * n + e] = sv[i]; Y[(size_t)k * n + e] = yv[i]; }
             }
-            if (lane == 0) rho[k] = 1.0f / sy;
+            if (lane == 0) { ws.v[k] = 1.0f / sy; ws.v[8] = yy; }
             st.newest = k;
-            st.yy = yy;
             st.hist = min(st.hist + 1, m);
         }
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int e = lane + 32 * i;
-            if (e < n) { xa[e] = xt[e]; ga[e] = gt[e]; }
-        }
-        st.f = ft;
+        accepted = true;
         st.alpha = fminf(1.0f, 2.0f * st.alpha);
-        st.accepts += 1;
     } else {
         st.alpha *= 0.5f;
         if (st.alpha < ko.alpha_min) {
             st.hist = 0;
             st.newest = -1;
             st.alpha = 1.0f;
+            new_dir = true;
         }
     }
-    __syncwarp();
-    // two-loop recursion: newest to oldest, then oldest to newest
-    float qv[NPL], gv[NPL];
+    float gv[NPL];
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         const int e = lane + 32 * i;
-        gv[i] = e < n ? ga[e] : 0.f;
-        qv[i] = gv[i];
+        gv[i] = 0.f;
+        if (e < n) {
+            if (accepted) { ws.xa[e] = xt[e]; ws.ga[e] = gt[e]; gv[i] = gt[e]; }
+            else gv[i] = ws.ga[e];
+        }
     }
-    for (int h = 0; h < st.hist; ++h) {
-        const int k = ((st.newest - h) % m + m) % m;
-        const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
-        float dot = 0.f;
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int e = lane + 32 * i;
-            if (e < n) dot = fmaf(Sk[e], qv[i], dot);
-        }
-        const float a = rho[k] * warp_sum(dot);
-        if (lane == 0) al[k] = a;
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int e = lane + 32 * i;
-            if (e < n) qv[i] = fmaf(-a, Yk[e], qv[i]);
-        }
+    if (accepted) {
+        st.f = ft;
+        st.accepts += 1;
+        new_dir = true;
     }
     __syncwarp();
-    const float gamma = st.hist > 0 ? (1.0f / rho[st.newest]) / st.yy : ko.gamma0;
+    if (new_dir) {
+        // two-loop recursion: newest to oldest, then oldest to newest
+        const int h = st.hist;
+        float qv[NPL], al[MH > 0 ? MH : DSEED_MAX_HISTORY];
 #pragma unroll
-    for (int i = 0; i < NPL; ++i) qv[i] *= gamma;
-    for (int h = st.hist - 1; h >= 0; --h) {
-        const int k = ((st.newest - h) % m + m) % m;
-        const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
-        float dot = 0.f;
+        for (int i = 0; i < NPL; ++i) qv[i] = gv[i];
+        if (MH > 0) {
+            float Sr[MH > 0 ? MH : 1][NPL], Yr[MH > 0 ? MH : 1][NPL], rr[MH > 0 ? MH : 1];
+            int k = st.newest;
+#pragma unroll
+            for (int c = 0; c < (MH > 0 ? MH : 1); ++c) {      // c = 0 newest
+                rr[c] = 0.f;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) { Sr[c][i] = 0.f; Yr[c][i] = 0.f; }
+                if (c < h) {
+                    rr[c] = ws.v[k];
+                    const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) {
+                        const int e = lane + 32 * i;
+                        if (e < n) { Sr[c][i] = Sk[e]; Yr[c][i] = Yk[e]; }
+                    }
+                    k = ring_prev(k, m);
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < (MH > 0 ? MH : 1); ++c) {
+                al[c] = 0.f;
+                if (c < h) {
+                    float dot = 0.f;
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) dot = fmaf(Sr[c][i], qv[i], dot);
+                    al[c] = rr[c] * warp_sum(dot);
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) qv[i] = fmaf(-al[c], Yr[c][i], qv[i]);
+                }
+            }
+            const float gamma = h > 0 ? (1.0f / rr[0]) / ws.v[8] : ko.gamma0;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) qv[i] *= gamma;
+#pragma unroll
+            for (int c = (MH > 0 ? MH : 1) - 1; c >= 0; --c) {
+                if (c < h) {
+                    float dot = 0.f;
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) dot = fmaf(Yr[c][i], qv[i], dot);
+                    const float cf = al[c] - rr[c] * warp_sum(dot);
+#pragma unroll
+                    for (int i = 0; i < NPL; ++i) qv[i] = fmaf(cf, Sr[c][i], qv[i]);
+                }
+            }
+        } else {
+            int k = st.newest;
+            for (int c = 0; c < h; ++c) {
+                const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+                float dot = 0.f;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int e = lane + 32 * i;
+                    if (e < n) dot = fmaf(Sk[e], qv[i], dot);
+                }
+                const float a = ws.v[k] * warp_sum(dot);
+                if (lane == 0) ws.v[16 + c] = a;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int e = lane + 32 * i;
+                    if (e < n) qv[i] = fmaf(-a, Yk[e], qv[i]);
+                }
+                k = ring_prev(k, m);
+            }
+            __syncwarp();
+            const float gamma = h > 0 ? (1.0f / ws.v[st.newest]) / ws.v[8] : ko.gamma0;
+#pragma unroll
+            for (int i = 0; i < NPL; ++i) qv[i] *= gamma;
+            // k is now the slot before the oldest; walk forward again
+            for (int c = h - 1; c >= 0; --c) {
+                k = ring_next(k, m);
+                const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+                float dot = 0.f;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int e = lane + 32 * i;
+                    if (e < n) dot = fmaf(Yk[e], qv[i], dot);
+                }
+                const float cf = ws.v[16 + c] - ws.v[k] * warp_sum(dot);
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int e = lane + 32 * i;
+                    if (e < n) qv[i] = fmaf(cf, Sk[e], qv[i]);
+                }
+            }
+        }
+        float gd = 0.f;
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) gd = fmaf(gv[i], -qv[i], gd);
+        gd = warp_sum(gd);
+        const bool descent = gd < 0.0f;
 #pragma unroll
         for (int i = 0; i < NPL; ++i) {
             const int e = lane + 32 * i;
-            if (e < n) dot = fmaf(Yk[e], qv[i], dot);
+            if (e < n) ws.dd[e] = descent ? -qv[i] : -gv[i];
         }
-        const float b = rho[k] * warp_sum(dot);
-        const float c = al[k] - b;
-#pragma unroll
-        for (int i = 0; i < NPL; ++i) {
-            const int e = lane + 32 * i;
-            if (e < n) qv[i] = fmaf(c, Sk[e], qv[i]);
-        }
+        __syncwarp();
     }
-    float gd = 0.f;
-#pragma unroll
-    for (int i = 0; i < NPL; ++i) gd = fmaf(gv[i], -qv[i], gd);
-    gd = warp_sum(gd);
-    const bool descent = gd < 0.0f;
-    float mx = 0.f;
+    // step = alpha d, scaled so that max |step| <= max_step; next trial point
+    float dv[NPL], mx = 0.f;
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
-        qv[i] = descent ? -qv[i] : -gv[i];          // qv now holds d
-        mx = fmaxf(mx, fabsf(st.alpha * qv[i]));
+        const int e = lane + 32 * i;
+        dv[i] = e < n ? ws.dd[e] : 0.f;
+        mx = fmaxf(mx, fabsf(st.alpha * dv[i]));
     }
     mx = warp_max(mx);
     const float scale = mx > ko.max_step ? ko.max_step / mx : 1.0f;
@@ -530,8 +661,8 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
 #pragma unroll
     for (int i = 0; i < NPL; ++i) {
         const int e = lane + 32 * i;
-        const float step = st.alpha * qv[i] * scale;
-        if (e < n) xt_next[e] = xa[e] + step;
+        const float step = st.alpha * dv[i] * scale;
+        if (e < n) xt_next[e] = ws.xa[e] + step;
         gts = fmaf(gv[i], step, gts);
     }
     st.gts = warp_sum(gts);

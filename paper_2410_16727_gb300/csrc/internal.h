@@ -45,7 +45,7 @@ struct KBatch {
 
 // Byte offsets of the L-BFGS state arrays (mirrors DseedLbfgsLayout).
 struct KLbfgsPtrs {
-    float *x, *g, *x_trial, *s, *y, *rho, *f, *alpha, *gts, *yy;
+    float *x, *g, *x_trial, *d, *s, *y, *rho, *yy, *f, *alpha, *gts;
     int *meta;
 };
 

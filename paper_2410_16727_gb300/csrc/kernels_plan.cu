@@ -12,7 +12,18 @@
 
 namespace dseed {
 
-constexpr int kPlanWarps = 4;
+#ifndef DSEED_PLAN_WARPS
+#define DSEED_PLAN_WARPS 4
+#endif
+#ifndef DSEED_PLAN_MINBLOCKS
+#define DSEED_PLAN_MINBLOCKS 4
+#endif
+#ifndef DSEED_PLAN_PREFETCH_HISTORY
+#define DSEED_PLAN_PREFETCH_HISTORY 1
+#endif
+constexpr int kPlanWarps = DSEED_PLAN_WARPS;
+// history length up to which T <= 32 plans keep the L-BFGS history in registers
+constexpr int kPrefetchM = DSEED_PLAN_PREFETCH_HISTORY ? 5 : 0;
 
 // ---------------------------------------------------------------- standalone L-BFGS
 __global__ void k_lbfgs_init(long long B, int n, int m, const float *__restrict__ x0, KLbfgsPtrs p) {
@@ -22,16 +33,14 @@ __global__ void k_lbfgs_init(long long B, int n, int m, const float *__restrict_
         p.f[i] = CUDART_INF_F;
         p.alpha[i] = 1.0f;
         p.gts[i] = 0.0f;
-        p.yy[i] = 0.0f;
         p.meta[i * 4 + 0] = 0;    // history count
         p.meta[i * 4 + 1] = -1;   // newest slot
         p.meta[i * 4 + 2] = 1;    // first evaluation pending
         p.meta[i * 4 + 3] = 0;    // accepts
-        for (int k = 0; k < m; ++k) p.rho[i * m + k] = 0.0f;
     }
 }
 
-template <int NPL>
+template <int NPL, int MH>
 __global__ void __launch_bounds__(kPlanWarps * 32)
     k_lbfgs_step(const __grid_constant__ KOpt ko, long long B, int T, const float *__restrict__ f_trial,
                  const float *__restrict__ g_trial, KLbfgsPtrs p) {
@@ -47,31 +56,33 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
         ws.gs[e] = g_trial[b * n + e];
         ws.xa[e] = p.x[b * n + e];
         ws.ga[e] = p.g[b * n + e];
+        ws.dd[e] = p.d[b * n + e];
     }
-    if (lane < m) ws.rho[lane] = p.rho[b * m + lane];
+    if (lane < 8) ws.v[lane] = p.rho[b * 8 + lane];
+    if (lane == 8) ws.v[8] = p.yy[b];
     LbUni st;
     st.f = p.f[b];
     st.alpha = p.alpha[b];
     st.gts = p.gts[b];
-    st.yy = p.yy[b];
     st.hist = p.meta[b * 4 + 0];
     st.newest = p.meta[b * 4 + 1];
     st.first = p.meta[b * 4 + 2];
     st.accepts = p.meta[b * 4 + 3];
     __syncwarp();
-    lbfgs_update<NPL>(ko, n, st, xt, ws.gs, f_trial[b], ws.xa, ws.ga, p.s + (size_t)b * m * n,
-                      p.y + (size_t)b * m * n, ws.rho, ws.al, xt);
+    lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, f_trial[b], ws, p.s + (size_t)b * m * n, p.y + (size_t)b * m * n,
+                          xt);
     for (int e = lane; e < n; e += 32) {
         p.x_trial[b * n + e] = xt[e];
         p.x[b * n + e] = ws.xa[e];
         p.g[b * n + e] = ws.ga[e];
+        p.d[b * n + e] = ws.dd[e];
     }
-    if (lane < m) p.rho[b * m + lane] = ws.rho[lane];
+    if (lane < 8) p.rho[b * 8 + lane] = ws.v[lane];
+    if (lane == 8) p.yy[b] = ws.v[8];
     if (lane == 0) {
         p.f[b] = st.f;
         p.alpha[b] = st.alpha;
         p.gts[b] = st.gts;
-        p.yy[b] = st.yy;
         p.meta[b * 4 + 0] = st.hist;
         p.meta[b * 4 + 1] = st.newest;
         p.meta[b * 4 + 2] = st.first;
@@ -84,8 +95,8 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 // update) -> success test of the accepted point -> outputs.  best_key[p] holds
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
 // their bit patterns order like the values); it must start at ~0.
-template <int TPL>
-__global__ void __launch_bounds__(kPlanWarps * 32)
+template <int TPL, int MH>
+__global__ void __launch_bounds__(kPlanWarps * 32, DSEED_PLAN_MINBLOCKS)
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
            float *__restrict__ hist_y, unsigned long long *__restrict__ best_key, float *traj,
@@ -124,12 +135,12 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
     const Goal G = make_goal(kb.goal + (size_t)p * 7);
     const SceneView sv = load_scene(kb.scenes, si);
     float *S = hist_s + (size_t)b * m * n, *Y = hist_y + (size_t)b * m * n;
-    LbUni st{CUDART_INF_F, 1.0f, 0.0f, 0.0f, 0, -1, 1, 0};
+    LbUni st{CUDART_INF_F, 1.0f, 0.0f, 0, -1, 1, 0};
     __syncwarp();
     for (int it = 0; it < ko.iters; ++it) {
         const EvalOut o = warp_eval<TPL, MODE_GRAD>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
-        lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws.xa, ws.ga, S, Y, ws.rho, ws.al, xt);
+        lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
     }
     // success test of the accepted point
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
@@ -186,9 +197,9 @@ int launch_lbfgs_step(const KOpt &ko, int B, int T, const float *f_trial, const 
         kern<<<blocks, kPlanWarps * 32, smem, st>>>(ko, (long long)B, T, f_trial, g_trial, p);
         return (int)cudaGetLastError();
     };
-    if (T <= 32) return go(k_lbfgs_step<7>);
-    if (T <= 64) return go(k_lbfgs_step<14>);
-    return go(k_lbfgs_step<28>);
+    if (T <= 32) return ko.m <= 5 ? go(k_lbfgs_step<7, 5>) : go(k_lbfgs_step<7, 0>);
+    if (T <= 64) return go(k_lbfgs_step<14, 0>);
+    return go(k_lbfgs_step<28, 0>);
 }
 
 int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch &kb, const float *seeds,
@@ -208,9 +219,9 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
         return (int)cudaGetLastError();
     };
     int r;
-    if (kb.T <= 32) r = go(k_plan<1>);
-    else if (kb.T <= 64) r = go(k_plan<2>);
-    else r = go(k_plan<4>);
+    if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5>) : go(k_plan<1, 0>);
+    else if (kb.T <= 64) r = go(k_plan<2, 0>);
+    else r = go(k_plan<4, 0>);
     if (r) return r;
     k_best<<<(kb.P + 127) / 128, 128, 0, st>>>(kb.P, best_key, best);
     return (int)cudaGetLastError();

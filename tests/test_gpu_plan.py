@@ -1,7 +1,7 @@
 """GPU parity of the batched L-BFGS and of the fused optimiser (plan) against
 the FP64 oracle, through the C ABI, from the tiny workload up to the full
 batched workload (256 problems x 64 seeds x 32 waypoints, 100 iterations) in the
-benchmark's launch configuration, checked on a 1% seed sample."""
+benchmark's launch configuration, checked seed by seed."""
 import numpy as np
 import pytest
 import torch
@@ -175,31 +175,25 @@ def batched_full():
     return wl, orc
 
 
-def test_full_batched_plan_sampled_parity(gpu_lib, batched_full):
+def test_full_batched_plan_parity(gpu_lib, batched_full):
     """256 problems x 64 seeds x 32 waypoints, 100 iterations, in one plan call (as
-    timed by the benchmark); the oracle re-plans a 2% seed sample one by one."""
+    timed by the benchmark); the oracle re-plans every one of the 16384 seeds.
+    Success flags agree on >= 99% of them (FP32 and FP64 runs of a non-convex
+    optimisation part ways on a few hard seeds after tens of iterations)."""
     wl, orc = batched_full
     planner, batch = gpu_side(wl)
     out = planner.plan(batch, wl.seeds)
     torch.cuda.synchronize()
     ok = to_np(out["success"]).astype(bool)
     cost = to_np(out["cost"])
-    rng = np.random.default_rng(2)
-    flat = rng.choice(wl.P * wl.S, size=(wl.P * wl.S) // 50, replace=False)
-    pp, ss = flat // wl.S, flat % wl.S
-    agree = []
-    rels = []
-    for p in np.unique(pp):
-        sel = ss[pp == p]
-        ref = orc.plan([int(wl.scene_of_problem[p])], wl.q_start[p:p + 1], wl.goal[p:p + 1],
-                       wl.seeds[p:p + 1, sel], wl.opt)
-        agree.extend(list(ok[p, sel] == ref["success"][0]))
-        both = ok[p, sel] & ref["success"][0]
-        rels.extend(list(np.abs(cost[p, sel][both] - ref["cost"][0][both]) / ref["cost"][0][both]))
-    agree = np.mean(agree)
+    ref = orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
+    agree = (ok == ref["success"]).mean()
     assert agree >= AGREE, agree
-    if rels:
-        assert np.median(rels) < 1e-2
+    both = ok & ref["success"]
+    rel = np.abs(cost[both] - ref["cost"][both]) / ref["cost"][both]
+    assert np.median(rel) < 1e-2
+    # problems with at least one successful seed: same on both sides within 1%
+    assert abs((to_np(out["best"]) >= 0).mean() - (ref["best"] >= 0).mean()) <= 0.01
     _check_best(out, cost, ok)
 
 
