@@ -230,6 +230,33 @@ int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
             }
     }
     k.frame_begin[8] = idx;
+    // per-frame bounding sphere of the collision spheres: centre = midpoint of
+    // their bounding box, radius = max over spheres of |o - centre| + r
+    for (int L = 0; L < 8; ++L) {
+        const int b = k.frame_begin[L], e = k.frame_begin[L + 1];
+        float lo[3] = {0.f, 0.f, 0.f}, hi[3] = {0.f, 0.f, 0.f}, rmin = 0.f, rmax = 0.f;
+        for (int q = b; q < e; ++q) {
+            const float o[3] = {k.sph[q].x, k.sph[q].y, k.sph[q].z};
+            for (int c = 0; c < 3; ++c) {
+                lo[c] = q == b ? o[c] : std::min(lo[c], o[c]);
+                hi[c] = q == b ? o[c] : std::max(hi[c], o[c]);
+            }
+            rmin = q == b ? k.sph[q].w : std::min(rmin, k.sph[q].w);
+            rmax = q == b ? k.sph[q].w : std::max(rmax, k.sph[q].w);
+        }
+        double cen[3], rad = 0.0;
+        for (int c = 0; c < 3; ++c) cen[c] = 0.5 * ((double)lo[c] + (double)hi[c]);
+        for (int q = b; q < e; ++q) {
+            const double dx = k.sph[q].x - cen[0], dy = k.sph[q].y - cen[1], dz = k.sph[q].z - cen[2];
+            rad = std::max(rad, std::sqrt(dx * dx + dy * dy + dz * dz) + (double)k.sph[q].w);
+        }
+        // round the radius up so the float value still bounds every sphere
+        k.fbound[L] = make_float4((float)cen[0], (float)cen[1], (float)cen[2], (float)(rad * (1.0 + 1e-6) + 1e-6));
+        k.frmin[L] = rmin;
+        k.frmax[L] = rmax;
+    }
+    k.cf8 = (float)std::cos((double)desc->dh[7][3]);
+    k.sf8 = (float)std::sin((double)desc->dh[7][3]);
     *out = r;
     return DSEED_OK;
 }

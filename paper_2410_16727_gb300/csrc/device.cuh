@@ -36,8 +36,9 @@ __device__ __forceinline__ float warp_min(float v) {
 // ----------------------------------------------------------------- scene / ESDF
 struct SceneView {
     const float *__restrict__ phi;
-    float ox, oy, oz, inv_res;
+    float ox, oy, oz, inv_res, res;
     float skip_pad;           // L sqrt(3) res + 1e-5, or +inf when the early-out is off
+    float lip;                // Lipschitz bound L of phi (0: early-outs off)
     int nx, ny, nz;
     bool ok;                  // descriptor usable: non-null ESDF, every dimension >= 2, res > 0
 };
@@ -52,7 +53,9 @@ __device__ __forceinline__ SceneView load_scene(const DseedScene *scenes, int id
     v.oy = s.grid.origin[1];
     v.oz = s.grid.origin[2];
     v.inv_res = 1.0f / s.grid.res;
+    v.res = s.grid.res;
     v.skip_pad = s.lipschitz > 0.0f ? s.lipschitz * 1.7320508f * s.grid.res + 1e-5f : CUDART_INF_F;
+    v.lip = s.lipschitz > 0.0f ? s.lipschitz : 0.0f;
     v.nx = s.grid.nx;
     v.ny = s.grid.ny;
     v.nz = s.grid.nz;
@@ -74,9 +77,17 @@ __device__ __forceinline__ bool cell_axis(float u, int n, int &i0, float &f) {
     return clamped;
 }
 
-// Cell index only (the corner (i0, j0, k0) of the cell that holds u).
+// Cell index only (the corner (i0, j0, k0) of the cell that holds u): the same
+// cell as cell_axis, from floor(u) clamped to [0, n - 2] (NaN converts to 0,
+// out-of-range values saturate).
 __device__ __forceinline__ int cell_index(float u, int n) {
-    return min(__float2int_rd(fminf(fmaxf(u, 0.0f), (float)(n - 1))), n - 2);
+    return min(max(__float2int_rd(u), 0), n - 2);
+}
+
+// ESDF value at that corner; grids are limited to 2^31 voxels so the index is 32-bit.
+__device__ __forceinline__ float corner_value(const SceneView &sv, float ux, float uy, float uz) {
+    const int idx = (cell_index(uz, sv.nz) * sv.ny + cell_index(uy, sv.ny)) * sv.nx + cell_index(ux, sv.nx);
+    return __ldg(sv.phi + idx);
 }
 
 __device__ __forceinline__ const float *cell_ptr(const SceneView &sv, int ix, int iy, int iz) {
@@ -166,6 +177,10 @@ enum { MODE_COST = 0, MODE_GRAD = 1, MODE_EVAL = 2 };
 #define DSEED_SPHERE_BATCH 1
 #endif
 constexpr int kSphereBatch = DSEED_SPHERE_BATCH;
+// Skip a whole frame when the ESDF at its bounding sphere clears all its spheres.
+#ifndef DSEED_FRAME_EARLY_OUT
+#define DSEED_FRAME_EARLY_OUT 1
+#endif
 
 struct WaypointAcc {
     float c_world, c_goal;
@@ -196,10 +211,15 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
 #pragma unroll
     for (int L = 1; L <= 8; ++L) {
-        float st, ct, th = rb.off[L - 1];
-        if (L <= 7) th += q[L <= 7 ? L - 1 : 0];
-        sincosf(th, &st, &ct);
-        if (L <= 7) { sn[L <= 7 ? L - 1 : 0] = st; cs[L <= 7 ? L - 1 : 0] = ct; }
+        float st, ct;
+        if (L <= 7) {
+            sincosf(q[L <= 7 ? L - 1 : 0] + rb.off[L - 1], &st, &ct);
+            sn[L <= 7 ? L - 1 : 0] = st;
+            cs[L <= 7 ? L - 1 : 0] = ct;
+        } else {
+            st = rb.sf8;
+            ct = rb.cf8;
+        }
         dh_step(R, p, rb.a[L - 1], rb.d[L - 1], rb.ca[L - 1], rb.sa[L - 1], ct, st);
         if (MODE == MODE_GRAD && L <= 7) {
             const int i = L <= 7 ? L - 1 : 0;
@@ -222,6 +242,21 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
         pv[1] = fmaf(p[1] - sv.oy, sv.inv_res, -0.5f);
         pv[2] = fmaf(p[2] - sv.oz, sv.inv_res, -0.5f);
         const int k1 = rb.frame_begin[L];
+        if (DSEED_FRAME_EARLY_OUT && MODE != MODE_EVAL && sv.lip > 0.0f && k1 > rb.frame_begin[L - 1]) {
+            // all spheres of the frame lie inside its bounding sphere (centre b,
+            // radius R): for sphere k, phi(c_k) >= v_b - L (2 sqrt(3) res + R - r_k)
+            // (corner of b's cell to corner of c_k's cell, through the clamped
+            // points), so one read clears the whole frame when it exceeds
+            // r_k + eta for every k
+            const float4 fb = rb.fbound[L - 1];
+            const float ux = fmaf(Rv[0], fb.x, fmaf(Rv[1], fb.y, fmaf(Rv[2], fb.z, pv[0])));
+            const float uy = fmaf(Rv[3], fb.x, fmaf(Rv[4], fb.y, fmaf(Rv[5], fb.z, pv[1])));
+            const float uz = fmaf(Rv[6], fb.x, fmaf(Rv[7], fb.y, fmaf(Rv[8], fb.z, pv[2])));
+            const float one_m_l = 1.0f - sv.lip;
+            const float thr = kc.eta + sv.lip * (2.0f * 1.7320508f * sv.res + fb.w) +
+                              fmaxf(one_m_l * rb.frmin[L - 1], one_m_l * rb.frmax[L - 1]) + 1e-5f;
+            if (corner_value(sv, ux, uy, uz) >= thr) continue;
+        }
         for (int k0 = rb.frame_begin[L - 1]; k0 < k1; k0 += kSphereBatch) {
             // phase 1: one corner of each sphere's cell, all loads in flight together.
             // Every corner of a cell lies within sqrt(3) res of the others, so for an
@@ -236,7 +271,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                     const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
                     const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
                     const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
-                    v0[c] = __ldg(cell_ptr(sv, cell_index(ux, sv.nx), cell_index(uy, sv.ny), cell_index(uz, sv.nz)));
+                    v0[c] = corner_value(sv, ux, uy, uz);
                 }
             }
             // phase 2: full interpolation of the spheres the bound cannot clear

@@ -20,6 +20,9 @@ struct KRobot {
     float lo[7], hi[7];                      // joint limits
     int n_spheres;
     int frame_begin[9];                      // spheres of frame L (1..8): [frame_begin[L-1], frame_begin[L])
+    float4 fbound[8];                        // per frame: bounding-sphere centre (frame coordinates), radius
+    float frmin[8], frmax[8];                // per frame: smallest / largest sphere radius
+    float cf8, sf8;                          // cos / sin of the flange frame's fixed theta offset
     float4 sph[DSEED_MAX_SPHERES];           // offset xyz, radius (sorted by frame)
     int sph_orig[DSEED_MAX_SPHERES];         // index in the caller's description
 };
