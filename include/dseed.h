@@ -181,6 +181,21 @@ void dseed_robot_destroy(DseedRobot *robot);
 int dseed_scene_build_esdf(const float *cuboids_dev, int n, const DseedGrid *grid,
                            float *esdf_dev, cudaStream_t stream);
 
+/* One ESDF to build: cuboids_dev [n][6] (may be NULL when n == 0), its grid,
+ * and the output esdf_dev [nz][ny][nx]. */
+typedef struct {
+    const float *cuboids_dev;
+    int          n;
+    DseedGrid    grid;
+    float       *esdf_dev;
+} DseedEsdfJob;
+
+/* The same per-voxel ESDF as dseed_scene_build_esdf for n_jobs scenes at once
+ * (grids may differ), in as few launches as possible.  jobs_host is a host
+ * array, read during the call.  EINVAL as for the single-scene call, for the
+ * first offending job. */
+int dseed_scene_build_esdf_batch(const DseedEsdfJob *jobs_host, int n_jobs, cudaStream_t stream);
+
 /* ------------------------------------------------------------ kinematics */
 
 /* Forward kinematics of N configurations q_dev [N][7]: flange poses

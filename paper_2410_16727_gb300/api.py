@@ -78,10 +78,8 @@ class Planner:
     # -- scenes ---------------------------------------------------------------
     def set_scenes(self, cuboids: Sequence, grids: Sequence, out: Optional[List[torch.Tensor]] = None):
         """Build (or rebuild in place, when `out` is given) one ESDF per scene on the device."""
-        esdfs = []
-        for i, (c, g) in enumerate(zip(cuboids, grids)):
-            ct = _to(c, torch.float32, self.device).reshape(-1, 6)
-            esdfs.append(B.scene_build_esdf(ct, g, out[i] if out is not None else None))
+        cts = [_to(c, torch.float32, self.device).reshape(-1, 6) for c in cuboids]
+        esdfs = B.scene_build_esdf_batch(cts, grids, out)
         self.esdfs, self.grids = esdfs, list(grids)
         self.table = B.SceneTable(esdfs, grids, self.device)
         return esdfs

@@ -35,6 +35,10 @@ class Grid(C.Structure):
     _fields_ = [("origin", C.c_float * 3), ("res", C.c_float), ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int)]
 
 
+class EsdfJob(C.Structure):
+    _fields_ = [("cuboids_dev", C.c_void_p), ("n", C.c_int), ("grid", Grid), ("esdf_dev", C.c_void_p)]
+
+
 class Scene(C.Structure):
     _fields_ = [("esdf_dev", C.c_void_p), ("grid", Grid), ("lipschitz", C.c_float)]
 
@@ -73,6 +77,7 @@ _SIGS = {
     "dseed_robot_create": ([C.POINTER(RobotDesc), C.POINTER(C.c_void_p)], C.c_int),
     "dseed_robot_destroy": ([C.c_void_p], None),
     "dseed_scene_build_esdf": ([C.c_void_p, C.c_int, C.POINTER(Grid), C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_scene_build_esdf_batch": ([C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "dseed_fk": ([C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "dseed_cost": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_void_p,
                     C.c_void_p], C.c_int),
@@ -248,6 +253,26 @@ def scene_build_esdf(cuboids: torch.Tensor, grid, out: Optional[torch.Tensor] = 
     _check(load().dseed_scene_build_esdf(cp, n, C.byref(g), _dev(out, torch.float32, "esdf"), _stream()),
            "dseed_scene_build_esdf")
     return out
+
+
+def scene_build_esdf_batch(cuboids: Sequence[torch.Tensor], grids: Sequence,
+                           outs: Optional[Sequence[torch.Tensor]] = None) -> list:
+    """ESDFs of several scenes in one call (device cuboid tensors [n_i][6])."""
+    jobs = (EsdfJob * len(cuboids))()
+    res = []
+    for q, (c, g) in enumerate(zip(cuboids, grids)):
+        gg = make_grid(g)
+        out = outs[q] if outs is not None else torch.empty((gg.nz, gg.ny, gg.nx), dtype=torch.float32,
+                                                             device=c.device)
+        n = int(c.shape[0])
+        jobs[q].cuboids_dev = _dev(c, torch.float32, f"cuboids[{q}]", (n, 6)) if n > 0 else None
+        jobs[q].n = n
+        jobs[q].grid = gg
+        jobs[q].esdf_dev = _dev(out, torch.float32, f"esdf[{q}]", (gg.nz, gg.ny, gg.nx))
+        res.append(out)
+    _check(load().dseed_scene_build_esdf_batch(C.cast(jobs, C.c_void_p), len(cuboids), _stream()),
+           "dseed_scene_build_esdf_batch")
+    return res
 
 
 def fk(robot: Robot, q: torch.Tensor, spheres: bool = False):

@@ -263,15 +263,37 @@ int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
 
 void dseed_robot_destroy(DseedRobot *robot) { delete robot; }
 
-int dseed_scene_build_esdf(const float *cuboids_dev, int n, const DseedGrid *grid, float *esdf_dev,
-                           cudaStream_t stream) {
+static int check_esdf_job(const float *cuboids_dev, int n, const DseedGrid *grid, const float *esdf_dev) {
     if (!grid || !esdf_dev) return fail(DSEED_EINVAL, "grid or esdf is NULL");
     if (n < 0 || (n > 0 && !cuboids_dev)) return fail(DSEED_EINVAL, "bad cuboid count or NULL cuboids");
     if (grid->nx < 2 || grid->ny < 2 || grid->nz < 2) return fail(DSEED_EINVAL, "grid dimensions must be >= 2");
+    if ((long long)grid->nx * grid->ny * grid->nz > (1LL << 31) - 1)
+        return fail(DSEED_EINVAL, "grid of more than 2^31 voxels");
     if (!(grid->res > 0.f) || !finite(grid->res) || !finite(grid->origin[0]) || !finite(grid->origin[1]) ||
         !finite(grid->origin[2]))
         return fail(DSEED_EINVAL, "bad grid origin or resolution");
-    return cuda_status(dseed::launch_esdf_build(cuboids_dev, n, *grid, esdf_dev, stream), "esdf build");
+    return DSEED_OK;
+}
+
+int dseed_scene_build_esdf(const float *cuboids_dev, int n, const DseedGrid *grid, float *esdf_dev,
+                           cudaStream_t stream) {
+    int r = check_esdf_job(cuboids_dev, n, grid, esdf_dev);
+    if (r) return r;
+    DseedEsdfJob job;
+    job.cuboids_dev = cuboids_dev;
+    job.n = n;
+    job.grid = *grid;
+    job.esdf_dev = esdf_dev;
+    return cuda_status(dseed::launch_esdf_build(&job, 1, stream), "esdf build");
+}
+
+int dseed_scene_build_esdf_batch(const DseedEsdfJob *jobs_host, int n_jobs, cudaStream_t stream) {
+    if (n_jobs < 0 || (n_jobs > 0 && !jobs_host)) return fail(DSEED_EINVAL, "bad job count or NULL jobs");
+    for (int q = 0; q < n_jobs; ++q) {
+        int r = check_esdf_job(jobs_host[q].cuboids_dev, jobs_host[q].n, &jobs_host[q].grid, jobs_host[q].esdf_dev);
+        if (r) return fail(r, "job %d: %s", q, g_last_error.c_str());
+    }
+    return cuda_status(dseed::launch_esdf_build(jobs_host, n_jobs, stream), "esdf build (batch)");
 }
 
 int dseed_fk(const DseedRobot *robot, const float *q_dev, int N, float *pose_dev, float *spheres_dev,

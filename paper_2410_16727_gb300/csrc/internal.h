@@ -53,7 +53,8 @@ struct KLbfgsPtrs {
 };
 
 // Launchers (return a cudaError_t as int); defined in the kernels_*.cu files.
-int launch_esdf_build(const float *cuboids, int n, const DseedGrid &g, float *esdf, cudaStream_t st);
+constexpr int kMaxEsdfJobs = 256;                // ESDF jobs per launch (carried in the kernel parameters)
+int launch_esdf_build(const DseedEsdfJob *jobs, int n_jobs, cudaStream_t st);
 int launch_fk(const KRobot &rb, const float *q, int N, float *pose, float *spheres, cudaStream_t st);
 int launch_cost(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x, float *cost,
                 float *terms, cudaStream_t st);

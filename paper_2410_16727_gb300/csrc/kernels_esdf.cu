@@ -7,16 +7,19 @@
 // deepest-penetration reading of min_k sdf_k); otherwise min_k sdf_k is the
 // square root of the former.  Both equal min_k sdf_k exactly.
 //
-// One block owns an 8x8x8 tile of voxels (one thread per voxel).  Before the
-// per-voxel loop the block drops the boxes that cannot be the minimum anywhere
-// in the tile: sdf_k is convex, so its maximum over the tile is at one of the
-// tile's 8 corner voxel centres (an upper bound U_k), and its minimum over the
-// tile is at least the distance from the tile's box of voxel centres to the
-// cuboid (a lower bound L_k, or -inf when they overlap).  A box with
-// L_k > min_j U_j + 1e-4 is larger than another box's value at every voxel of
-// the tile, so skipping it leaves every min, and every output bit, unchanged;
-// the remaining boxes go through the same per-voxel arithmetic as without the
-// culling.
+// One block owns an 8x8x8 tile of voxels (one thread per voxel) of one scene;
+// a launch covers up to kMaxJobs scenes (job descriptors travel in the kernel
+// parameters, so no device-side table is needed).  Before the per-voxel loop
+// the block drops the boxes that cannot be the minimum anywhere in the tile:
+// sdf_k is convex, so its maximum over the tile is at one of the tile's 8
+// corner voxel centres (an upper bound U_k; the 8 corners of a box are
+// evaluated by 8 neighbouring lanes), and its minimum over the tile is at least
+// the distance from the tile's box of voxel centres to the cuboid (a lower
+// bound L_k, or -inf when they overlap).  A box with L_k > min_j U_j + 1e-4 is
+// larger than another box's value at every voxel of the tile, so skipping it
+// leaves every min, and every output bit, unchanged; the remaining boxes go
+// through the same per-voxel arithmetic as without the culling (checked
+// bitwise against a build without culling on the benchmark workloads).
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -28,6 +31,12 @@ constexpr int kTile = 8;
 constexpr int kEsdfThreads = kTile * kTile * kTile;   // 512
 constexpr int kEsdfChunk = 1024;                      // boxes staged per pass
 
+struct EsdfBatch {
+    int n_jobs;
+    int tiles_z;                                      // max over the jobs
+    DseedEsdfJob job[kMaxEsdfJobs];
+};
+
 __device__ __forceinline__ float box_sdf(float px, float py, float pz, const float *bx) {
     const float dx = fabsf(px - bx[0]) - bx[3];
     const float dy = fabsf(py - bx[1]) - bx[4];
@@ -37,12 +46,18 @@ __device__ __forceinline__ float box_sdf(float px, float py, float pz, const flo
     return sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(in, 0.f);
 }
 
-__global__ void __launch_bounds__(kEsdfThreads)
-    k_esdf_build(const float *__restrict__ cub, int n, DseedGrid g, float *__restrict__ phi) {
-    __shared__ float sb[kEsdfChunk * 6];
+__global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_constant__ EsdfBatch batch) {
+    __shared__ float sb[kEsdfChunk * 6];                 // kept boxes
     __shared__ float s_red[kEsdfThreads / 32];
     __shared__ int s_count;
-    const int tx = blockIdx.x, ty = blockIdx.y, tz = blockIdx.z;
+    const int jid = blockIdx.z / batch.tiles_z;
+    const int tz = blockIdx.z - jid * batch.tiles_z;
+    const int tx = blockIdx.x, ty = blockIdx.y;
+    const DseedEsdfJob &job = batch.job[jid];
+    const DseedGrid &g = job.grid;
+    if (tx * kTile >= g.nx || ty * kTile >= g.ny || tz * kTile >= g.nz) return;   // whole block: tile outside this grid
+    const float *__restrict__ cub = job.cuboids_dev;
+    const int n = job.n;
     const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
     const int i = tx * kTile + lx, j = ty * kTile + ly, k = tz * kTile + lz;
     const bool live = i < g.nx && j < g.ny && k < g.nz;
@@ -58,17 +73,28 @@ __global__ void __launch_bounds__(kEsdfThreads)
     hi[1] = fmaf((float)(ty * kTile + kTile - 1) + 0.5f, g.res, g.origin[1]);
     hi[2] = fmaf((float)(tz * kTile + kTile - 1) + 0.5f, g.res, g.origin[2]);
 
-    // pass 1: tau = min over boxes of the max of sdf_k over the tile corners
+    // pass 1: tau = min over boxes of the max of sdf_k over the 8 tile corners;
+    // lane group (8 lanes) = one box, lane & 7 = corner
     float ub = CUDART_INF_F;
-    for (int b = threadIdx.x; b < n; b += kEsdfThreads) {
-        float bx[6];
+    const int corner = threadIdx.x & 7;
+    const float cxp = (corner & 1) ? hi[0] : lo[0];
+    const float cyp = (corner & 2) ? hi[1] : lo[1];
+    const float czp = (corner & 4) ? hi[2] : lo[2];
+    for (int base = 0; base < n * 8; base += kEsdfThreads) {
+        const int w = base + threadIdx.x;
+        const bool valid = w < n * 8;
+        float v = -CUDART_INF_F;
+        if (valid) {
+            float bx[6];
+            const float *src = cub + (size_t)(w >> 3) * 6;
 #pragma unroll
-        for (int c = 0; c < 6; ++c) bx[c] = cub[(size_t)b * 6 + c];
-        float m = -CUDART_INF_F;
-#pragma unroll
-        for (int c = 0; c < 8; ++c)
-            m = fmaxf(m, box_sdf((c & 1) ? hi[0] : lo[0], (c & 2) ? hi[1] : lo[1], (c & 4) ? hi[2] : lo[2], bx));
-        ub = fminf(ub, m);
+            for (int c = 0; c < 6; ++c) bx[c] = src[c];
+            v = box_sdf(cxp, cyp, czp, bx);
+        }
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
+        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+        if (valid) ub = fminf(ub, v);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
@@ -99,7 +125,7 @@ __global__ void __launch_bounds__(kEsdfThreads)
                 const float gap = fmaxf(fmaxf(gl, gh), 0.f);
                 gap2 = fmaf(gap, gap, gap2);
             }
-            // gap2 == 0: the boxes overlap, no useful lower bound
+            // gap2 == 0: the boxes touch or overlap, no useful lower bound
             const float lb = gap2 > 0.f ? sqrtf(gap2) : -CUDART_INF_F;
             if (lb <= tau) {
                 const int slot = atomicAdd(&s_count, 1);
@@ -121,16 +147,31 @@ __global__ void __launch_bounds__(kEsdfThreads)
     }
     if (live) {
         const float s = in <= 0.f ? in : sqrtf(out2);
-        phi[((size_t)k * g.ny + j) * g.nx + i] = fminf(s, DSEED_ESDF_FAR);
+        job.esdf_dev[((size_t)k * g.ny + j) * g.nx + i] = fminf(s, DSEED_ESDF_FAR);
     }
 }
 
-int launch_esdf_build(const float *cuboids, int n, const DseedGrid &g, float *esdf, cudaStream_t st) {
-    const long long nvox = (long long)g.nx * g.ny * g.nz;
-    if (nvox == 0) return cudaSuccess;
-    const dim3 grid((g.nx + kTile - 1) / kTile, (g.ny + kTile - 1) / kTile, (g.nz + kTile - 1) / kTile);
-    k_esdf_build<<<grid, kEsdfThreads, 0, st>>>(cuboids, n, g, esdf);
-    return (int)cudaGetLastError();
+int launch_esdf_build(const DseedEsdfJob *jobs, int n_jobs, cudaStream_t st) {
+    for (int j0 = 0; j0 < n_jobs; j0 += kMaxEsdfJobs) {
+        EsdfBatch batch;
+        batch.n_jobs = n_jobs - j0 < kMaxEsdfJobs ? n_jobs - j0 : kMaxEsdfJobs;
+        int tx = 0, ty = 0, tz = 0;
+        for (int q = 0; q < batch.n_jobs; ++q) {
+            batch.job[q] = jobs[j0 + q];
+            const DseedGrid &g = jobs[j0 + q].grid;
+            tx = max(tx, (g.nx + kTile - 1) / kTile);
+            ty = max(ty, (g.ny + kTile - 1) / kTile);
+            tz = max(tz, (g.nz + kTile - 1) / kTile);
+        }
+        batch.tiles_z = tz;
+        const long long gz = (long long)tz * batch.n_jobs;
+        if (tx == 0 || ty == 0 || tz == 0) continue;
+        if (ty > 65535 || gz > 65535) return (int)cudaErrorInvalidConfiguration;
+        k_esdf_build<<<dim3(tx, ty, (unsigned)gz), kEsdfThreads, 0, st>>>(batch);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return (int)e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace dseed

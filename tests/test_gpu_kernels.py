@@ -53,6 +53,22 @@ def test_esdf_tiny_workload_full_grid(gpu_lib):
     assert np.abs(got - want).max() <= TOL_M
 
 
+def test_esdf_batch_matches_single_builds(gpu_lib):
+    """One batched call over scenes of different grids and cuboid counts (incl. an
+    empty scene) writes exactly what the single-scene call writes."""
+    rng = np.random.default_rng(21)
+    grids = [I.Grid((-0.2, -0.3, 0.0), 0.03, (20, 17, 9)), I.Grid((0.0, 0.0, 0.0), 0.05, (8, 8, 8)),
+             I.Grid((-0.64, -0.64, -0.14), 0.02, (64, 64, 64)), I.Grid((-0.1, 0.1, 0.2), 0.01, (33, 40, 25))]
+    cubs = [I.scene_tiny(rng, n_boxes=3), np.zeros((0, 6), np.float32), I.scene_tiny(rng, n_boxes=40),
+            I.scene_clutter(rng, n_boxes=120)]
+    dc = [_cuda(c).reshape(-1, 6) for c in cubs]
+    batch = B.scene_build_esdf_batch(dc, grids)
+    for c, g, got in zip(dc, grids, batch):
+        assert torch.equal(got, B.scene_build_esdf(c, g))
+    for c, g, got in zip(cubs, grids, batch):
+        assert np.abs(to_np(got) - oracle.esdf_build(c, g)).max() <= TOL_M
+
+
 @pytest.mark.parametrize("name", ["batched", "stress"])
 def test_esdf_full_size_windows(gpu_lib, name):
     """Full 128^3 / 256^3 grids on the GPU; the oracle recomputes random 12^3
