@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--problems", type=int, default=None,
                     help="smaller case for profiling: this many problems (and scenes) of the workload")
     return ap.parse_args()
@@ -261,6 +263,53 @@ def run_gpu(args, rank: int, world: int):
     return res, wl
 
 
+# ---------------------------------------------------------------------------- serving
+
+def run_serving(args, rank: int) -> dict:
+    """Serving workload: Poisson arrivals of planning requests with seed counts
+    in {4, 16, 64, 256} and horizons in {32, 48, 64} over a pool of 64 scenes
+    (64^3..192^3 ESDFs at 1-2 cm, 10-100 cuboids), 100 iterations each, under a
+    120 GB HBM budget.  First the saturation throughput (all requests at once),
+    then p50/p99 latency at 0.25, 0.5 and 0.8 of it."""
+    import torch
+    from paper_2410_16727_gb300 import api, serving as SV
+
+    n = args.serve_requests
+    robot = I.make_robot()
+    cub, grids = SV.serving_scene_pool(64, seed=rank)
+    planner = api.Planner(robot)
+    planner.set_scenes(cub, grids)
+    cf, pf = api.device_workload_fns(planner)
+    sw = SV.build_serving_workload(n, cf, pf, n_scenes=64, seed=rank)
+    budget = 120 * 10 ** 9
+    out = {"workload": f"{n} requests, S in {{4,16,64,256}}, T in {{32,48,64}}, 64 scenes 64^3-192^3 at 1-2 cm, "
+                       f"100 iterations, 120 GB budget, rounds of 10 iterations"}
+
+    def fresh():
+        sv = SV.Server(sw.robot, budget, max_requests=4096, round_iters=10)
+        for s, (c, g) in enumerate(zip(sw.cuboids, sw.grids)):
+            sv.add_scene(s, c, g)
+        torch.cuda.synchronize()
+        return sv
+
+    sv = fresh()
+    warm = SV.ServingWorkload(sw.robot, sw.cuboids, sw.grids, sw.problems, sw.requests[:64])
+    SV.run_trace(sv, warm, None)
+    sat = SV.summarize(SV.run_trace(sv, sw, None))
+    out["saturation"] = sat
+    st_per_req = float(np.mean([S * T for (_, S, T) in sw.requests])) * 100
+    out["saturation_st_evals_per_s"] = sat["plans_per_s"] * st_per_req
+    sv.close()
+    for frac in (0.25, 0.5, 0.8):
+        sv = fresh()
+        rate = frac * sat["plans_per_s"]
+        res = SV.summarize(SV.run_trace(sv, sw, SV.poisson_arrivals(n, rate, seed=int(frac * 100))))
+        res["offered_plans_per_s"] = rate
+        out[f"load_{frac}"] = res
+        sv.close()
+    return out
+
+
 # ---------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(spec, budget_s: float, seed_offset: int = 0):
@@ -325,6 +374,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     res, wl = run_gpu(args, rank, world)
+    if not args.no_serving:
+        res["serving"] = run_serving(args, rank)
     if rank == 0 and not args.no_cpu_baseline:
         v, k, t, cores = oracle_sample(I.WORKLOADS[args.workload], args.cpu_seconds)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

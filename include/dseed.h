@@ -280,6 +280,101 @@ int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const D
                      float *traj_dev, float *cost_dev, uint8_t *success_dev, float *metrics_dev,
                      int *best_dev, cudaStream_t stream);
 
+/* --------------------------------------------------------------- serving */
+
+/* Device-memory arena manager (host bookkeeping only): first-fit over
+ * [0, bytes) in 256-byte units, neighbouring free blocks merged on free.  The
+ * server below uses it to place scenes and request state inside the caller's
+ * arena; it is exposed so that its policy can be used and tested on its own. */
+typedef struct DseedArena DseedArena;
+int  dseed_arena_create(size_t bytes, DseedArena **out);
+void dseed_arena_destroy(DseedArena *arena);
+/* Reserve `bytes` (rounded up to 256): *offset receives the start, or the call
+ * returns DSEED_ENOMEM (nothing reserved) when no free block is large enough. */
+int  dseed_arena_alloc(DseedArena *arena, size_t bytes, size_t *offset);
+/* Release a block returned by dseed_arena_alloc; EINVAL for an unknown offset. */
+int  dseed_arena_free(DseedArena *arena, size_t offset);
+/* Bytes reserved now, the most ever reserved, and the largest free block. */
+int  dseed_arena_usage(const DseedArena *arena, size_t *used, size_t *peak, size_t *largest_free);
+
+/* Serving loop with continuous batching (the paper measures plan time per
+ * problem, Sec. 5.1, Table 1; requests of uneven seed counts, horizons and
+ * grids arrive while others are being planned).
+ *
+ * The server owns no device memory of its own: the caller hands it one device
+ * arena of arena_bytes, which is the HBM budget for resident scenes (ESDF +
+ * cuboids) and for the optimiser state of admitted requests.  Requests queue on
+ * the host in arrival order; dseed_server_step admits queued requests while
+ * their state fits in the arena (first come, first served: the head of the
+ * queue waits for memory rather than being overtaken), then runs one round:
+ * up to round_iters L-BFGS iterations of every admitted request, all requests
+ * together, in one launch per waypoint class (T <= 32, <= 64, <= 128).  A
+ * request finishes after desc->opt.iters iterations; its outputs are copied to
+ * its host buffers and its memory returns to the arena.  Each seed computes
+ * exactly what dseed_plan_batch computes for it, whatever shares its rounds.
+ * At most two rounds are in flight on the server's stream, so a new request
+ * starts within about two rounds. */
+typedef struct DseedServer DseedServer;
+
+typedef struct {
+    size_t arena_bytes;      /* size of arena_dev (the HBM budget) */
+    int    max_requests;     /* requests admitted at the same time, >= 1 */
+    int    round_iters;      /* iterations per round, >= 1 */
+    DseedCostParams cost;
+    DseedOptParams  opt;     /* opt.iters: iterations of every request */
+    float  delta_t, delta_r; /* success thresholds */
+} DseedServerDesc;
+
+/* One planning request.  Host buffers (pinned memory recommended; they must
+ * stay valid until the request is done): q_start [7], goal [7], seeds
+ * [S][T][7]; outputs traj [S][T][7], cost [S], success [S], best (index of the
+ * lowest-cost successful seed or -1). */
+typedef struct {
+    int scene_id;
+    int S, T;                /* S >= 1, 1 <= T <= DSEED_MAX_T */
+    const float *q_start_host, *goal_host, *seeds_host;
+    float *traj_host, *cost_host;
+    uint8_t *success_host;
+    int *best_host;
+} DseedRequest;
+
+typedef struct {
+    long long submitted, admitted, completed, failed, rounds;
+    int queued, active;                  /* now */
+    size_t arena_used, arena_peak;       /* bytes */
+} DseedServerStats;
+
+/* Create a server on the current device.  arena_dev: caller's device buffer of
+ * desc->arena_bytes (256-byte aligned), used by the server until destroy.
+ * The server creates its own CUDA stream and events and a small pinned host
+ * staging area; it allocates no device memory. */
+int  dseed_server_create(const DseedRobot *robot, const DseedServerDesc *desc, void *arena_dev,
+                         DseedServer **out);
+/* Waits for the server's stream, then frees its host resources. */
+void dseed_server_destroy(DseedServer *server);
+/* Make a scene resident: copy cuboids_host [n][6] into the arena and build its
+ * ESDF there (Lipschitz bound 1).  ENOMEM when it does not fit; EINVAL for a
+ * used id or a bad grid.  Asynchronous on the server's stream. */
+int  dseed_server_add_scene(DseedServer *server, int scene_id, const float *cuboids_host, int n,
+                            const DseedGrid *grid);
+/* Release a scene; EINVAL while queued or admitted requests use it. */
+int  dseed_server_remove_scene(DseedServer *server, int scene_id);
+/* Queue a request (host-side only, returns at once); *ticket identifies it. */
+int  dseed_server_submit(DseedServer *server, const DseedRequest *req, long long *ticket);
+/* One scheduling step: retire finished rounds (outputs are in the host buffers
+ * of requests reported done), admit queued requests, and launch one round if
+ * any request is admitted and fewer than two rounds are in flight.  Never
+ * blocks on the GPU unless `wait` is non-zero, in which case it first waits for
+ * the oldest round in flight.  *n_done (optional) receives the number of
+ * requests that finished in this call. */
+int  dseed_server_step(DseedServer *server, int wait, int *n_done);
+/* State of a ticket: 0 queued, 1 admitted, 2 done, -1 failed (scene missing
+ * or request larger than the whole arena).  t_submit/t_done (optional)
+ * receive the host steady-clock times in seconds of submission and of the step
+ * that saw it finish. */
+int  dseed_server_poll(DseedServer *server, long long ticket, int *state, double *t_submit, double *t_done);
+int  dseed_server_stats(const DseedServer *server, DseedServerStats *out);
+
 /* ------------------------------------------------ plan without allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that

@@ -67,6 +67,23 @@ class LbfgsLayout(C.Structure):
                                           "meta", "total")]
 
 
+class ServerDesc(C.Structure):
+    _fields_ = [("arena_bytes", C.c_size_t), ("max_requests", C.c_int), ("round_iters", C.c_int),
+                ("cost", CostParams), ("opt", OptParams), ("delta_t", C.c_float), ("delta_r", C.c_float)]
+
+
+class Request(C.Structure):
+    _fields_ = [("scene_id", C.c_int), ("S", C.c_int), ("T", C.c_int), ("q_start_host", C.c_void_p),
+                ("goal_host", C.c_void_p), ("seeds_host", C.c_void_p), ("traj_host", C.c_void_p),
+                ("cost_host", C.c_void_p), ("success_host", C.c_void_p), ("best_host", C.c_void_p)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
+                ("failed", C.c_longlong), ("rounds", C.c_longlong), ("queued", C.c_int), ("active", C.c_int),
+                ("arena_used", C.c_size_t), ("arena_peak", C.c_size_t)]
+
+
 class DseedError(RuntimeError):
     pass
 
@@ -91,6 +108,20 @@ _SIGS = {
     "dseed_plan_workspace_bytes": ([C.POINTER(PlanDesc), C.POINTER(C.c_size_t)], C.c_int),
     "dseed_plan_batch": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p, C.c_size_t,
                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_arena_create": ([C.c_size_t, C.POINTER(C.c_void_p)], C.c_int),
+    "dseed_arena_destroy": ([C.c_void_p], None),
+    "dseed_arena_alloc": ([C.c_void_p, C.c_size_t, C.POINTER(C.c_size_t)], C.c_int),
+    "dseed_arena_free": ([C.c_void_p, C.c_size_t], C.c_int),
+    "dseed_arena_usage": ([C.c_void_p, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
+    "dseed_server_create": ([C.c_void_p, C.POINTER(ServerDesc), C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "dseed_server_destroy": ([C.c_void_p], None),
+    "dseed_server_add_scene": ([C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.POINTER(Grid)], C.c_int),
+    "dseed_server_remove_scene": ([C.c_void_p, C.c_int], C.c_int),
+    "dseed_server_submit": ([C.c_void_p, C.POINTER(Request), C.POINTER(C.c_longlong)], C.c_int),
+    "dseed_server_step": ([C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "dseed_server_poll": ([C.c_void_p, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                           C.POINTER(C.c_double)], C.c_int),
+    "dseed_server_stats": ([C.c_void_p, C.POINTER(ServerStats)], C.c_int),
     "dseed_plan_batch_static": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -404,3 +435,92 @@ def plan_batch_static(robot: Robot, desc: PlanDesc, pr: Problems, seeds: torch.T
                                           _dev(out["best"], torch.int32, "best", (P,)), _stream()),
            "dseed_plan_batch_static")
     return out
+
+
+# ---------------------------------------------------------------------------- arena / server
+
+class Arena:
+    """Host-side arena manager (dseed_arena_*): offsets only, no device memory."""
+
+    def __init__(self, nbytes: int):
+        h = C.c_void_p()
+        _check(load().dseed_arena_create(nbytes, C.byref(h)), "dseed_arena_create")
+        self.handle = h
+
+    def alloc(self, nbytes: int) -> Optional[int]:
+        off = C.c_size_t()
+        rc = load().dseed_arena_alloc(self.handle, nbytes, C.byref(off))
+        if rc == -2:
+            return None
+        _check(rc, "dseed_arena_alloc")
+        return int(off.value)
+
+    def free(self, offset: int):
+        _check(load().dseed_arena_free(self.handle, offset), "dseed_arena_free")
+
+    def usage(self):
+        u, p, l = C.c_size_t(), C.c_size_t(), C.c_size_t()
+        _check(load().dseed_arena_usage(self.handle, C.byref(u), C.byref(p), C.byref(l)), "dseed_arena_usage")
+        return int(u.value), int(p.value), int(l.value)
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.dseed_arena_destroy(self.handle)
+            self.handle = None
+
+
+def server_desc(arena_bytes: int, max_requests: int, round_iters: int, cost, opt,
+                delta_t: float = 0.005, delta_r: float = 2.86 * math.pi / 180.0) -> ServerDesc:
+    d = ServerDesc()
+    d.arena_bytes, d.max_requests, d.round_iters = int(arena_bytes), int(max_requests), int(round_iters)
+    pd = plan_desc(0, 1, 1, cost, opt, delta_t, delta_r)
+    d.cost, d.opt = pd.cost, pd.opt
+    d.delta_t, d.delta_r = pd.delta_t, pd.delta_r
+    return d
+
+
+def server_create(robot: Robot, desc: ServerDesc, arena: torch.Tensor) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().dseed_server_create(robot.handle, C.byref(desc), _dev(arena, torch.uint8, "arena"), C.byref(h)),
+           "dseed_server_create")
+    return h
+
+
+def server_destroy(h):
+    load().dseed_server_destroy(h)
+
+
+def server_add_scene(h, scene_id: int, cuboids, grid):
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(cuboids, dtype=np.float32).reshape(-1, 6))
+    g = make_grid(grid)
+    _check(load().dseed_server_add_scene(h, int(scene_id), c.ctypes.data if c.size else None, int(c.shape[0]),
+                                         C.byref(g)), "dseed_server_add_scene")
+
+
+def server_remove_scene(h, scene_id: int):
+    _check(load().dseed_server_remove_scene(h, int(scene_id)), "dseed_server_remove_scene")
+
+
+def server_submit(h, req: Request) -> int:
+    t = C.c_longlong()
+    _check(load().dseed_server_submit(h, C.byref(req), C.byref(t)), "dseed_server_submit")
+    return int(t.value)
+
+
+def server_step(h, wait: bool = False) -> int:
+    n = C.c_int()
+    _check(load().dseed_server_step(h, 1 if wait else 0, C.byref(n)), "dseed_server_step")
+    return int(n.value)
+
+
+def server_poll(h, ticket: int):
+    st, t0, t1 = C.c_int(), C.c_double(), C.c_double()
+    _check(load().dseed_server_poll(h, int(ticket), C.byref(st), C.byref(t0), C.byref(t1)), "dseed_server_poll")
+    return int(st.value), float(t0.value), float(t1.value)
+
+
+def server_stats(h) -> ServerStats:
+    s = ServerStats()
+    _check(load().dseed_server_stats(h, C.byref(s)), "dseed_server_stats")
+    return s

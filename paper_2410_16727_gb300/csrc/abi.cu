@@ -173,6 +173,34 @@ PlanLayout plan_layout(const DseedPlanDesc *d) {
 
 }  // namespace
 
+namespace dseed {
+// Shared with the serving runtime (server.cu).
+int set_error(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+KRobot robot_params(const DseedRobot *robot) { return robot->k; }
+KCost cost_params(const DseedCostParams &c) { return make_cost(c); }
+KOpt opt_params(const DseedOptParams &o) { return make_opt(o); }
+int check_cost_opt(const DseedCostParams &c, const DseedOptParams &o, float delta_t, float delta_r) {
+    DseedPlanDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.P = 0;
+    d.S = 1;
+    d.T = 1;
+    d.cost = c;
+    d.opt = o;
+    d.delta_t = delta_t;
+    d.delta_r = delta_r;
+    return check_desc(&d, true);
+}
+}  // namespace dseed
+
 extern "C" {
 
 int dseed_abi_version(void) { return DSEED_ABI_VERSION; }

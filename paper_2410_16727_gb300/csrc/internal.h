@@ -70,3 +70,52 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
                 float *traj, float *cost, uint8_t *success, float *metrics, int *best, cudaStream_t st);
 
 }  // namespace dseed
+
+namespace dseed {
+
+// ---------------------------------------------------------------- serving
+// Device memory of one served request (offsets in floats from its region base;
+// every array 64-float (256-byte) aligned).  S seeds of n = 7T unknowns,
+// history m.  The trial point starts as the request's seeds.
+struct ServeLayout {
+    size_t qs, goal, xt, xa, ga, dd, hs, hy, sc, cost, succ, key, total;
+};
+
+__host__ __device__ inline size_t serve_align(size_t v) { return (v + 63) & ~(size_t)63; }
+
+__host__ __device__ inline ServeLayout serve_layout(int S, int T, int m) {
+    const size_t n = 7 * (size_t)T, Sn = (size_t)S * n;
+    ServeLayout l;
+    size_t off = 0;
+    l.qs = off;   off = serve_align(off + 7);
+    l.goal = off; off = serve_align(off + 7);
+    l.xt = off;   off = serve_align(off + Sn);
+    l.xa = off;   off = serve_align(off + Sn);
+    l.ga = off;   off = serve_align(off + Sn);
+    l.dd = off;   off = serve_align(off + Sn);
+    l.hs = off;   off = serve_align(off + (size_t)m * Sn);
+    l.hy = off;   off = serve_align(off + (size_t)m * Sn);
+    l.sc = off;   off = serve_align(off + 16 * (size_t)S);   // per seed: f, alpha, gts, yy, rho[8], hist, newest, first, accepts
+    l.cost = off; off = serve_align(off + (size_t)S);
+    l.succ = off; off = serve_align(off + ((size_t)S + 3) / 4);   // uint8 per seed
+    l.key = off;  off = serve_align(off + 2);                     // one uint64
+    l.total = off;
+    return l;
+}
+
+// One request in a serving round (built on the host, read by every warp of it).
+struct ServeEntry {
+    long long warp_begin;     // first warp of this request in the launch
+    float *region;            // request region base
+    DseedScene scene;
+    int S, T;
+    int iters_done;           // iterations done before this round (0: start from the seeds)
+    int iters_round;          // iterations to run in this round
+    int final_round;          // 1: test success and write the outputs after this round
+    int pad;
+};
+
+int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_t, float delta_r, int tpl,
+                 const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st);
+
+}  // namespace dseed

@@ -1,0 +1,143 @@
+// kernels_serve.cu -- resumable fused optimiser for the serving loop.
+//
+// A serving round runs every active request for up to K iterations in one
+// launch per waypoint class (T <= 32, <= 64, <= 128).  Warp w finds its
+// request by binary search over the round's table and its seed as the offset
+// inside it.  The optimiser state of each seed (trial point, accepted point,
+// gradient, direction, scalars, history) lives in the request's region of the
+// serving arena between rounds, so a seed computes exactly what the one-shot
+// plan computes for it, whichever requests share its rounds.
+#include <cuda_runtime.h>
+
+#include "device.cuh"
+
+namespace dseed {
+
+#ifndef DSEED_SERVE_MINBLOCKS
+#define DSEED_SERVE_MINBLOCKS 4
+#endif
+constexpr int kServeWarps = 4;
+
+template <int TPL, int MH>
+__global__ void __launch_bounds__(kServeWarps * 32, DSEED_SERVE_MINBLOCKS)
+    k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
+            float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
+    constexpr int NPL = 7 * TPL;
+    extern __shared__ float smem[];
+    const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long w = (long long)blockIdx.x * kServeWarps + wid;
+    if (w >= total_warps) return;
+    int lo = 0, hi = n_entries - 1;                 // last entry with warp_begin <= w
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (table[mid].warp_begin <= w) lo = mid; else hi = mid - 1;
+    }
+    const ServeEntry &E = table[lo];
+    const int s = (int)(w - E.warp_begin);
+    const int T = E.T, n = 7 * T, m = ko.m;
+    if (s < 0 || s >= E.S || T > 32 * TPL) return;
+    const ServeLayout L = serve_layout(E.S, T, m);
+    float *R = E.region;
+    float *g_xt = R + L.xt + (size_t)s * n, *g_xa = R + L.xa + (size_t)s * n;
+    float *g_ga = R + L.ga + (size_t)s * n, *g_dd = R + L.dd + (size_t)s * n;
+    float *S_ = R + L.hs + (size_t)s * m * n, *Y_ = R + L.hy + (size_t)s * m * n;
+    float *sc = R + L.sc + (size_t)s * 16;
+    WarpSmem ws = carve(smem + wid * warp_smem_floats(32 * TPL), T);
+    float *xt = ws.xs + kPad * 7;
+    SceneView sv;
+    {
+        DseedScene one = E.scene;
+        sv = load_scene(&one, 0);
+    }
+    if (!sv.ok) {
+        if (E.final_round && lane == 0) {
+            R[L.cost + s] = CUDART_NAN_F;
+            reinterpret_cast<uint8_t *>(R + L.succ)[s] = 0;
+        }
+        return;
+    }
+    const int R3 = (T + kPad) * 7;
+    for (int e = lane; e < kPad * 7; e += 32) {
+        ws.xs[e] = R[L.qs + e % 7];
+        ws.es[T * 7 + e] = 0.f;
+        ws.es[R3 + T * 7 + e] = 0.f;
+        ws.es[2 * R3 + T * 7 + e] = 0.f;
+    }
+    LbUni st{CUDART_INF_F, 1.0f, 0.0f, 0, -1, 1, 0};
+    for (int e = lane; e < n; e += 32) xt[e] = g_xt[e];
+    if (E.iters_done > 0) {
+        for (int e = lane; e < n; e += 32) {
+            ws.xa[e] = g_xa[e];
+            ws.ga[e] = g_ga[e];
+            ws.dd[e] = g_dd[e];
+        }
+        if (lane < 9) ws.v[lane] = sc[3 + lane];     // rho[0..8) at v[0..8), y^T y at v[8]
+        st.f = sc[0];
+        st.alpha = sc[1];
+        st.gts = sc[2];
+        st.hist = __float_as_int(sc[12]);
+        st.newest = __float_as_int(sc[13]);
+        st.first = __float_as_int(sc[14]);
+        st.accepts = __float_as_int(sc[15]);
+    }
+    const Goal G = make_goal(R + L.goal);
+    __syncwarp();
+    for (int it = 0; it < E.iters_round; ++it) {
+        const EvalOut o = warp_eval<TPL, MODE_GRAD>(rb, kc, sv, T, G, ws, false);
+        __syncwarp();
+        lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, o.cost, ws, S_, Y_, xt);
+    }
+    if (!E.final_round) {
+        for (int e = lane; e < n; e += 32) {
+            g_xt[e] = xt[e];
+            g_xa[e] = ws.xa[e];
+            g_ga[e] = ws.ga[e];
+            g_dd[e] = ws.dd[e];
+        }
+        if (lane < 9) sc[3 + lane] = ws.v[lane];
+        if (lane == 0) {
+            sc[0] = st.f;
+            sc[1] = st.alpha;
+            sc[2] = st.gts;
+            sc[12] = __int_as_float(st.hist);
+            sc[13] = __int_as_float(st.newest);
+            sc[14] = __int_as_float(st.first);
+            sc[15] = __int_as_float(st.accepts);
+        }
+        return;
+    }
+    // last round: success test of the accepted point, outputs
+    for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
+    __syncwarp();
+    const EvalOut o = warp_eval<TPL, MODE_EVAL>(rb, kc, sv, T, G, ws, false);
+    for (int e = lane; e < n; e += 32) g_xa[e] = ws.xa[e];
+    const bool ok = o.min_clear >= 0.0f && o.pos_err < delta_t && o.rot_err < delta_r && o.lim_viol == 0.0f;
+    if (lane == 0) {
+        R[L.cost + s] = st.f;
+        reinterpret_cast<uint8_t *>(R + L.succ)[s] = ok ? 1 : 0;
+        if (ok && st.f >= 0.0f) {
+            const unsigned long long key = ((unsigned long long)__float_as_uint(st.f) << 32) | (unsigned)s;
+            atomicMin(reinterpret_cast<unsigned long long *>(R + L.key), key);
+        }
+    }
+}
+
+int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_t, float delta_r, int tpl,
+                 const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st) {
+    if (n_entries == 0 || total_warps == 0) return cudaSuccess;
+    const unsigned blocks = (unsigned)((total_warps + kServeWarps - 1) / kServeWarps);
+    const size_t smem = (size_t)kServeWarps * warp_smem_floats(32 * tpl) * sizeof(float);
+    auto go = [&](auto kern) {
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return (int)e;
+        }
+        kern<<<blocks, kServeWarps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
+        return (int)cudaGetLastError();
+    };
+    if (tpl == 1) return ko.m <= 5 ? go(k_serve<1, 5>) : go(k_serve<1, 0>);
+    if (tpl == 2) return go(k_serve<2, 0>);
+    return go(k_serve<4, 0>);
+}
+
+}  // namespace dseed
