@@ -375,6 +375,95 @@ int  dseed_server_step(DseedServer *server, int wait, int *n_done);
 int  dseed_server_poll(DseedServer *server, long long ticket, int *state, double *t_submit, double *t_done);
 int  dseed_server_stats(const DseedServer *server, DseedServerStats *out);
 
+/* ------------------------------------------------- learned seed proposal */
+
+/* Layers of the conditional denoiser that proposes seed trajectories (Sec.
+ * 4.2 "Model Architecture": a 1-D temporal-convolution U-Net of conditional
+ * residual blocks conditioned on a time-step embedding and an observation +
+ * problem encoding; Sec. 4.3 "Model Training and Inference": the noise
+ * prediction objective of Eq. 1 and DDIM sampling, App. A.3 / A.5).  The
+ * caller strings the layers together; every arithmetic step runs here.
+ *
+ * Tensors are FP32, channels-last [N][L][C] (C fastest) unless stated; all
+ * pointers are device pointers; calls are asynchronous on `stream`; no call
+ * allocates.  EINVAL on negative sizes or NULL required pointers. */
+
+/* C[M][N] = alpha op(A) op(B) + beta C (+ bias[N] if bias_dev != NULL), FP32.
+ * op(A) = A ([M][K], lda) or, with trans_a, A^T (A stored [K][M]); likewise B. */
+int dseed_nn_gemm_f32(int trans_a, int trans_b, int M, int N, int K, float alpha, const float *A_dev, int lda,
+                      const float *B_dev, int ldb, float beta, float *C_dev, int ldc, const float *bias_dev,
+                      cudaStream_t stream);
+/* C[M][N] (FP32) = A[M][K] W[N][K]^T (+ bias[N]) on the tensor cores: A and W
+ * BF16 row-major, K a multiple of 16, FP32 accumulation. */
+int dseed_nn_gemm_bf16(int M, int N, int K, const void *A_dev, const void *W_dev, float *C_dev,
+                       const float *bias_dev, cudaStream_t stream);
+/* im2col for a 1-D convolution of x [N][L][C] with kernel k, stride s, padding
+ * p: cols[N * Lo][kc_pad], entry (j, c) of row (n, lo) = x[n][lo s - p + j][c]
+ * (0 outside [0, L) and for columns >= k C).  cols is BF16 when bf16 != 0. */
+int dseed_nn_im2col1d(const float *x_dev, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad,
+                      void *cols_dev, int bf16, cudaStream_t stream);
+/* Adjoint of im2col: dx[N][L][C] += the column entries that came from it. */
+int dseed_nn_col2im1d(const float *cols_dev, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad,
+                      float *dx_dev, cudaStream_t stream);
+/* out[c] = (out[c] if accumulate) + sum_r y[r][c] over y [R][C]. */
+int dseed_nn_colsum(const float *y_dev, int R, int C, float *out_dev, int accumulate, cudaStream_t stream);
+/* Group normalisation over (L, C / G) per sample and group, affine gamma/beta
+ * [C]; mean / rstd [N][G] are saved for the backward pass. */
+int dseed_nn_groupnorm_fwd(const float *x_dev, int N, int L, int C, int G, const float *gamma_dev,
+                           const float *beta_dev, float eps, float *y_dev, float *mean_dev, float *rstd_dev,
+                           cudaStream_t stream);
+/* Backward of the above: dx [N][L][C]; per-sample partials dgamma_n, dbeta_n
+ * [N][C] (sum them over N with dseed_nn_colsum). */
+int dseed_nn_groupnorm_bwd(const float *dy_dev, const float *x_dev, int N, int L, int C, int G,
+                           const float *gamma_dev, const float *mean_dev, const float *rstd_dev, float *dx_dev,
+                           float *dgamma_n_dev, float *dbeta_n_dev, cudaStream_t stream);
+/* Mish(x) = x tanh(softplus(x)) elementwise (backward: out = dy * Mish'(x)). */
+int dseed_nn_mish(const float *x_dev, const float *dy_dev, float *out_dev, long long n, int backward,
+                  cudaStream_t stream);
+/* FiLM conditioning of a residual block: y = h * film[:, :C] + film[:, C:]
+ * with film [N][2C] broadcast over L; backward gives dh and dfilm [N][2C]. */
+int dseed_nn_film(const float *h_dev, const float *film_dev, int N, int L, int C, float *y_dev,
+                  const float *dy_dev, float *dh_dev, float *dfilm_dev, int backward, cudaStream_t stream);
+/* out = a x + b y elementwise (y may be NULL). */
+int dseed_nn_axpby(float a, const float *x_dev, float b, const float *y_dev, float *out_dev, long long n,
+                   cudaStream_t stream);
+/* Channel-slice copy for concatenation and its adjoint: for R rows,
+ * out[r][out_off + c] (+)= in[r][in_off + c], c < C_in. */
+int dseed_nn_copy_cols(const float *in_dev, long long R, int C_in, int in_stride, int in_off, float *out_dev,
+                       int out_stride, int out_off, int accumulate, cudaStream_t stream);
+/* Nearest-neighbour upsampling by 2 along L ([N][L][C] -> [N][2L][C]); the
+ * backward (backward != 0) maps [N][2L][C] gradients to [N][L][C]. */
+int dseed_nn_upsample2(const float *x_dev, int N, int L, int C, float *y_dev, int backward, cudaStream_t stream);
+/* Per-row gather out[r][e] = in[r][idx[e]] over n rows of `per` entries, or the
+ * adjoint scatter-add (scatter != 0): out[r][idx[e]] += in[r][e]. */
+int dseed_nn_gather(const float *in_dev, const int *idx_dev, float *out_dev, long long n, long long per,
+                    int scatter, cudaStream_t stream);
+/* Sinusoidal embedding of integer diffusion steps k [N] into [N][dim]. */
+int dseed_nn_sinusoid(const int *k_dev, int N, int dim, float *out_dev, cudaStream_t stream);
+/* One Adam step with decoupled weight decay on n parameters (step >= 1). */
+int dseed_nn_adam(float *p_dev, const float *g_dev, float *m_dev, float *v_dev, long long n, float lr, float beta1,
+                  float beta2, float eps, float weight_decay, int step, cudaStream_t stream);
+/* Forward noising of Eq. 1: x_k = sqrt(abar[k_n]) x0 + sqrt(1 - abar[k_n]) eps
+ * for N samples of `per` values; abar_dev [K] the cumulative noise schedule. */
+int dseed_nn_ddpm_noise(const float *x0_dev, const float *eps_dev, const int *k_dev, const float *abar_dev, int N,
+                        int per, float *xk_dev, cudaStream_t stream);
+/* The loss of Eq. 1 with optional per-sample weights w [N] (Eq. 2's
+ * (1 + alpha 1(tau)) factor): loss = sum w_n (pred - target)^2 / (N per),
+ * written as `blocks` partial sums into loss_partial_dev; dpred = dloss/dpred. */
+int dseed_nn_mse(const float *pred_dev, const float *target_dev, const float *w_dev, int N, int per,
+                 float *dpred_dev, float *loss_partial_dev, int blocks, cudaStream_t stream);
+/* One deterministic DDIM step (App. A.5) from step k to an earlier step:
+ * x0 = clamp((x_k - sqrt(1 - ab_k) eps) / sqrt(ab_k), -clip, clip),
+ * out = sqrt(ab_prev) x0 + sqrt(1 - ab_prev) eps. */
+int dseed_nn_ddim_step(const float *xk_dev, const float *eps_dev, float ab_k, float ab_prev, long long n, float clip,
+                       float *out_dev, cudaStream_t stream);
+/* out = min(max(a x + b, lo), hi) elementwise (e.g. occupancy from an ESDF:
+ * a = -1e6, b = 0, lo = 0, hi = 1). */
+int dseed_nn_clamp_affine(const float *x_dev, float a, float b, float lo, float hi, float *out_dev, long long n,
+                          cudaStream_t stream);
+/* FP32 -> BF16 (round to nearest even). */
+int dseed_nn_to_bf16(const float *x_dev, void *y_dev, long long n, cudaStream_t stream);
+
 /* ------------------------------------------------ plan without allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that

@@ -122,6 +122,40 @@ _SIGS = {
     "dseed_server_poll": ([C.c_void_p, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
                            C.POINTER(C.c_double)], C.c_int),
     "dseed_server_stats": ([C.c_void_p, C.POINTER(ServerStats)], C.c_int),
+    "dseed_nn_gemm_f32": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p,
+                           C.c_int, C.c_float, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_gemm_bf16": ([C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+                           C.c_int),
+    "dseed_nn_im2col1d": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                           C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_col2im1d": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                           C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_colsum": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_groupnorm_fwd": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_float,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_groupnorm_bwd": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_mish": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_film": ([C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                       C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_axpby": ([C.c_float, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p], C.c_int),
+    "dseed_nn_copy_cols": ([C.c_void_p, C.c_longlong, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                            C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_upsample2": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_gather": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p],
+                        C.c_int),
+    "dseed_nn_sinusoid": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_float, C.c_float, C.c_float,
+                       C.c_float, C.c_float, C.c_int, C.c_void_p], C.c_int),
+    "dseed_nn_ddpm_noise": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p,
+                             C.c_void_p], C.c_int),
+    "dseed_nn_mse": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
+                      C.c_void_p], C.c_int),
+    "dseed_nn_ddim_step": ([C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_longlong, C.c_float, C.c_void_p,
+                           C.c_void_p], C.c_int),
+    "dseed_nn_to_bf16": ([C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p], C.c_int),
+    "dseed_nn_clamp_affine": ([C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_longlong,
+                               C.c_void_p], C.c_int),
     "dseed_plan_batch_static": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -524,3 +558,20 @@ def server_stats(h) -> ServerStats:
     s = ServerStats()
     _check(load().dseed_server_stats(h, C.byref(s)), "dseed_server_stats")
     return s
+
+
+# ---------------------------------------------------------------------------- denoiser layers
+
+def nn(name: str, *args):
+    """Call dseed_nn_<name>(*args, stream) and raise on failure.  Tensors are
+    passed by data pointer (None -> NULL)."""
+    conv = []
+    for a in args:
+        if isinstance(a, torch.Tensor):
+            if not a.is_cuda or not a.is_contiguous():
+                raise DseedError(f"nn_{name}: tensors must be contiguous CUDA tensors")
+            conv.append(a.data_ptr())
+        else:
+            conv.append(a)
+    fn = getattr(load(), "dseed_nn_" + name)
+    _check(fn(*conv, _stream()), "dseed_nn_" + name)

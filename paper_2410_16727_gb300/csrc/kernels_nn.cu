@@ -1,0 +1,611 @@
+// kernels_nn.cu -- layers of the conditional denoiser (learned seed proposal).
+//
+// Activations are channels-last: a tensor [N][L][C] holds N samples of length
+// L with C channels, C fastest.  A 1-D convolution is an im2col gather into
+// cols [N * Lo][k * C] followed by a GEMM with the weights [Cout][k * C]; its
+// backward is the transposed GEMMs and a col2im scatter-add.  Training runs in
+// FP32 (SIMT GEMM); inference runs the GEMMs on the tensor cores in BF16 with
+// FP32 accumulation.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+#include "internal.h"
+
+namespace dseed {
+
+// ---------------------------------------------------------------- FP32 GEMM
+// C[M][N] = alpha * op(A)[M][K] * op(B)[K][N] + beta * C (+ bias[N] when given).
+// op(A) = A (row-major [M][K], lda) or A^T (A stored [K][M]); same for B.
+constexpr int GB = 64, GK = 16;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alpha, const float *__restrict__ A,
+                                                 int lda, const float *__restrict__ B, int ldb, float beta,
+                                                 float *__restrict__ C, int ldc, const float *__restrict__ bias) {
+    __shared__ float As[GK][GB + 4];
+    __shared__ float Bs[GK][GB + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
+    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += GK) {
+        for (int t = threadIdx.x; t < GB * GK; t += 256) {
+            const int kk = t % GK, mm = t / GK;                    // A tile: [mm][kk]
+            const int gm = m0 + mm, gk = k0 + kk;
+            float a = 0.f;
+            if (gm < M && gk < K) a = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            As[kk][mm] = a;
+            const int nn = t % GB, kb = t / GB;                    // B tile: [kb][nn]
+            const int gn = n0 + nn, gk2 = k0 + kb;
+            float b = 0.f;
+            if (gn < N && gk2 < K) b = TB ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn];
+            Bs[kb][nn] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int gm = m0 + ty * 4 + i;
+        if (gm >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gn = n0 + tx * 4 + j;
+            if (gn >= N) continue;
+            float v = alpha * acc[i][j];
+            if (beta != 0.f) v += beta * C[(size_t)gm * ldc + gn];
+            if (bias) v += bias[gn];
+            C[(size_t)gm * ldc + gn] = v;
+        }
+    }
+}
+
+// ---------------------------------------------------------------- BF16 tensor-core GEMM
+// C[M][N] (fp32) = A[M][K] (bf16, row-major) * W[N][K]^T (bf16, row-major) + bias.
+// Block 128 x 64, 8 warps (4 x 2), warp tile 32 x 32 of m16n8k16 MMAs; K
+// padded by the caller to a multiple of 16 (zero tail).
+constexpr int TM = 128, TN = 64, TK = 32;
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, const __nv_bfloat16 *__restrict__ A,
+                                                  const __nv_bfloat16 *__restrict__ W, float *__restrict__ C,
+                                                  const float *__restrict__ bias) {
+    __shared__ __nv_bfloat16 As[TM][TK + 8];
+    __shared__ __nv_bfloat16 Ws[TN][TK + 8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int wm = warp >> 1, wn = warp & 1;            // 4 x 2 warps
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    float acc[2][4][4] = {};
+    for (int k0 = 0; k0 < K; k0 += TK) {
+        // 16-byte chunks (8 bf16); K % 8 == 0 (caller pads K to 16)
+        for (int t = threadIdx.x; t < TM * TK / 8; t += 256) {
+            const int r = t / (TK / 8), c8 = (t % (TK / 8)) * 8;
+            const int gm = m0 + r, gk = k0 + c8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gm < M && gk < K) v = *reinterpret_cast<const uint4 *>(A + (size_t)gm * K + gk);
+            *reinterpret_cast<uint4 *>(&As[r][c8]) = v;
+        }
+        for (int t = threadIdx.x; t < TN * TK / 8; t += 256) {
+            const int r = t / (TK / 8), c8 = (t % (TK / 8)) * 8;
+            const int gn = n0 + r, gk = k0 + c8;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (gn < N && gk < K) v = *reinterpret_cast<const uint4 *>(W + (size_t)gn * K + gk);
+            *reinterpret_cast<uint4 *>(&Ws[r][c8]) = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ks = 0; ks < TK; ks += 16) {
+            unsigned af[2][4], bfm[4][2];
+            const int g = lane >> 2, tq = (lane & 3) * 2;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                const int r = wm * 32 + i * 16 + g;
+                af[i][0] = *reinterpret_cast<const unsigned *>(&As[r][ks + tq]);
+                af[i][1] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + tq]);
+                af[i][2] = *reinterpret_cast<const unsigned *>(&As[r][ks + tq + 8]);
+                af[i][3] = *reinterpret_cast<const unsigned *>(&As[r + 8][ks + tq + 8]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int cn = wn * 32 + j * 8 + g;
+                bfm[j][0] = *reinterpret_cast<const unsigned *>(&Ws[cn][ks + tq]);
+                bfm[j][1] = *reinterpret_cast<const unsigned *>(&Ws[cn][ks + tq + 8]);
+            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfm[j]);
+        }
+        __syncthreads();
+    }
+    const int g = lane >> 2, tq = (lane & 3) * 2;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int gm = m0 + wm * 32 + i * 16 + g + h * 8;
+                if (gm >= M) continue;
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int gn = n0 + wn * 32 + j * 8 + tq + e;
+                    if (gn >= N) continue;
+                    C[(size_t)gm * N + gn] = acc[i][j][h * 2 + e] + (bias ? bias[gn] : 0.f);
+                }
+            }
+}
+
+// ---------------------------------------------------------------- layout ops
+// im2col: cols[(n, lo)][(j, c)] = x[n][lo * s - p + j][c] (0 outside), row width
+// kc_pad >= k * C (zero tail).  T = float or bf16 output.
+template <typename TO>
+__global__ void k_im2col1d(const float *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad,
+                           TO *__restrict__ cols) {
+    const long long total = (long long)N * Lo * kc_pad;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(i % kc_pad);
+        const long long row = i / kc_pad;
+        const int lo = (int)(row % Lo), n = (int)(row / Lo);
+        float v = 0.f;
+        if (col < k * C) {
+            const int j = col / C, c = col - j * C;
+            const int li = lo * s - p + j;
+            if (li >= 0 && li < L) v = x[((size_t)n * L + li) * C + c];
+        }
+        cols[i] = (TO)v;
+    }
+}
+
+// col2im (backward of im2col): dx[n][li][c] += sum over (lo, j) with lo*s - p + j = li.
+__global__ void k_col2im1d(const float *__restrict__ cols, int N, int L, int C, int k, int s, int p, int Lo,
+                           int kc_pad, float *__restrict__ dx) {
+    const long long total = (long long)N * L * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long r = i / C;
+        const int li = (int)(r % L), n = (int)(r / L);
+        float acc = 0.f;
+        for (int j = 0; j < k; ++j) {
+            const int t = li + p - j;
+            if (t < 0 || t % s) continue;
+            const int lo = t / s;
+            if (lo >= Lo) continue;
+            acc += cols[((size_t)n * Lo + lo) * kc_pad + j * C + c];
+        }
+        dx[i] += acc;
+    }
+}
+
+// column sums: out[c] (+)= sum_r y[r][c]
+__global__ void k_colsum(const float *__restrict__ y, int R, int C, float *__restrict__ out, int accumulate) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float acc = 0.f;
+    for (int r = 0; r < R; ++r) acc += y[(size_t)r * C + c];
+    out[c] = accumulate ? out[c] + acc : acc;
+}
+
+// ---------------------------------------------------------------- group norm
+// per (n, group): mean and 1/sqrt(var + eps) over L x (C / G) values
+__global__ void k_gn_fwd(const float *__restrict__ x, int N, int L, int C, int G, const float *__restrict__ gamma,
+                         const float *__restrict__ beta, float eps, float *__restrict__ y, float *__restrict__ mean,
+                         float *__restrict__ rstd) {
+    const int ng = blockIdx.x;          // n * G + g
+    const int n = ng / G, g = ng % G, cg = C / G;
+    __shared__ float s1[256], s2[256];
+    float a = 0.f, b = 0.f;
+    for (int t = threadIdx.x; t < L * cg; t += blockDim.x) {
+        const int l = t / cg, c = g * cg + t % cg;
+        const float v = x[((size_t)n * L + l) * C + c];
+        a += v;
+        b += v * v;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const float cnt = (float)(L * cg);
+    const float mu = s1[0] / cnt;
+    const float var = fmaxf(s2[0] / cnt - mu * mu, 0.f);
+    const float rs = rsqrtf(var + eps);
+    if (threadIdx.x == 0) {
+        mean[ng] = mu;
+        rstd[ng] = rs;
+    }
+    for (int t = threadIdx.x; t < L * cg; t += blockDim.x) {
+        const int l = t / cg, c = g * cg + t % cg;
+        const size_t i = ((size_t)n * L + l) * C + c;
+        y[i] = (x[i] - mu) * rs * gamma[c] + beta[c];
+    }
+}
+
+// dx, and per-(n, channel) partials of dgamma / dbeta (summed over n by the caller's colsum)
+__global__ void k_gn_bwd(const float *__restrict__ dy, const float *__restrict__ x, int N, int L, int C, int G,
+                         const float *__restrict__ gamma, const float *__restrict__ mean,
+                         const float *__restrict__ rstd, float *__restrict__ dx, float *__restrict__ dgamma_n,
+                         float *__restrict__ dbeta_n) {
+    const int ng = blockIdx.x;
+    const int n = ng / G, g = ng % G, cg = C / G;
+    const float mu = mean[ng], rs = rstd[ng];
+    __shared__ float s1[256], s2[256];
+    float a = 0.f, b = 0.f;   // sum dy*gamma, sum dy*gamma*xhat
+    for (int t = threadIdx.x; t < L * cg; t += blockDim.x) {
+        const int l = t / cg, c = g * cg + t % cg;
+        const size_t i = ((size_t)n * L + l) * C + c;
+        const float xh = (x[i] - mu) * rs;
+        const float d = dy[i] * gamma[c];
+        a += d;
+        b += d * xh;
+    }
+    s1[threadIdx.x] = a;
+    s2[threadIdx.x] = b;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            s1[threadIdx.x] += s1[threadIdx.x + o];
+            s2[threadIdx.x] += s2[threadIdx.x + o];
+        }
+        __syncthreads();
+    }
+    const float cnt = (float)(L * cg);
+    const float m1 = s1[0] / cnt, m2 = s2[0] / cnt;
+    for (int t = threadIdx.x; t < L * cg; t += blockDim.x) {
+        const int l = t / cg, c = g * cg + t % cg;
+        const size_t i = ((size_t)n * L + l) * C + c;
+        const float xh = (x[i] - mu) * rs;
+        dx[i] = rs * (dy[i] * gamma[c] - m1 - xh * m2);
+    }
+    // per-channel partials for this sample (one thread per channel of the group)
+    for (int c = g * cg + threadIdx.x; c < (g + 1) * cg; c += blockDim.x) {
+        float dg = 0.f, db = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const size_t i = ((size_t)n * L + l) * C + c;
+            dg += dy[i] * (x[i] - mu) * rs;
+            db += dy[i];
+        }
+        dgamma_n[(size_t)n * C + c] = dg;
+        dbeta_n[(size_t)n * C + c] = db;
+    }
+}
+
+// ---------------------------------------------------------------- elementwise
+// Mish(x) = x tanh(softplus(x))
+__device__ __forceinline__ float softplus(float x) { return x > 20.f ? x : log1pf(expf(x)); }
+
+__global__ void k_mish_fwd(const float *__restrict__ x, float *__restrict__ y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = x[i] * tanhf(softplus(x[i]));
+}
+
+__global__ void k_mish_bwd(const float *__restrict__ dy, const float *__restrict__ x, float *__restrict__ dx,
+                           long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float v = x[i];
+        const float t = tanhf(softplus(v));
+        const float sg = 1.f / (1.f + expf(-v));
+        dx[i] = dy[i] * (t + v * (1.f - t * t) * sg);
+    }
+}
+
+// FiLM: y[n][l][c] = h[n][l][c] * film[n][c] + film[n][C + c]
+__global__ void k_film_fwd(const float *__restrict__ h, const float *__restrict__ film, int N, int L, int C,
+                           float *__restrict__ y) {
+    const long long total = (long long)N * L * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const int n = (int)(i / ((long long)L * C));
+        y[i] = h[i] * film[(size_t)n * 2 * C + c] + film[(size_t)n * 2 * C + C + c];
+    }
+}
+
+// dh = dy * scale; dfilm[n][c] = sum_l dy h, dfilm[n][C + c] = sum_l dy
+__global__ void k_film_bwd(const float *__restrict__ dy, const float *__restrict__ h, const float *__restrict__ film,
+                           int N, int L, int C, float *__restrict__ dh, float *__restrict__ dfilm) {
+    const long long total = (long long)N * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C), n = (int)(i / C);
+        const float sc = film[(size_t)n * 2 * C + c];
+        float a = 0.f, b = 0.f;
+        for (int l = 0; l < L; ++l) {
+            const size_t k = ((size_t)n * L + l) * C + c;
+            dh[k] = dy[k] * sc;
+            a += dy[k] * h[k];
+            b += dy[k];
+        }
+        dfilm[(size_t)n * 2 * C + c] = a;
+        dfilm[(size_t)n * 2 * C + C + c] = b;
+    }
+}
+
+// out = a * x + b * y  (elementwise; y may be null)
+__global__ void k_axpby(float a, const float *__restrict__ x, float b, const float *__restrict__ y,
+                        float *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = a * x[i] + (y ? b * y[i] : 0.f);
+}
+
+// strided row copy: out[r][off + c] (+)= in[r][c], c < Cin (concat / split along channels)
+__global__ void k_copy_cols(const float *__restrict__ in, long long R, int Cin, int in_stride, int in_off,
+                            float *__restrict__ out, int out_stride, int out_off, int accumulate) {
+    const long long total = R * Cin;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % Cin);
+        const long long r = i / Cin;
+        const float v = in[r * in_stride + in_off + c];
+        float *o = out + r * out_stride + out_off + c;
+        *o = accumulate ? *o + v : v;
+    }
+}
+
+// nearest-neighbour x2 along L: up[n][2l + e][c] = x[n][l][c]; backward sums pairs
+__global__ void k_upsample2(const float *__restrict__ x, int N, int L, int C, float *__restrict__ y, int backward) {
+    const long long total = backward ? (long long)N * L * C : (long long)N * 2 * L * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long r = i / C;
+        if (!backward) {
+            const int l2 = (int)(r % (2 * L)), n = (int)(r / (2 * L));
+            y[i] = x[((size_t)n * L + l2 / 2) * C + c];
+        } else {
+            const int l = (int)(r % L), n = (int)(r / L);
+            const size_t b = ((size_t)n * 2 * L + 2 * l) * C + c;
+            y[i] = x[b] + x[b + C];
+        }
+    }
+}
+
+// gather out[i] = in[idx[i]]; scatter out[idx[i]] += in[i] (idx a permutation-free map)
+__global__ void k_gather(const float *__restrict__ in, const int *__restrict__ idx, float *__restrict__ out,
+                         long long n, long long per, int scatter) {
+    // n rows of `per` entries; idx maps an entry of a row to an entry of the source row
+    const long long total = n * per;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / per;
+        const int e = (int)(i % per);
+        if (!scatter) out[i] = in[r * per + idx[e]];
+        else atomicAdd(out + r * per + idx[e], in[i]);
+    }
+}
+
+// sinusoidal embedding of integer steps: out[n][2i] = sin(k w_i), out[n][2i+1] = cos(k w_i),
+// w_i = 10000^(-i / (dim/2))
+__global__ void k_sinusoid(const int *__restrict__ k, int N, int dim, float *__restrict__ out) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int h = dim / 2;
+    for (int i = 0; i < h; ++i) {
+        const float w = expf(-logf(10000.f) * (float)i / (float)h);
+        float s, c;
+        sincosf((float)k[n] * w, &s, &c);
+        out[(size_t)n * dim + 2 * i] = s;
+        out[(size_t)n * dim + 2 * i + 1] = c;
+    }
+}
+
+// Adam (decoupled weight decay): m = b1 m + (1-b1) g; v = b2 v + (1-b2) g^2;
+// p -= lr (mhat / (sqrt(vhat) + eps) + wd p)
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, long long n, float lr, float b1, float b2, float eps, float wd,
+                       float bc1, float bc2) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * ((mi / bc1) / (sqrtf(vi / bc2) + eps) + wd * p[i]);
+    }
+}
+
+// DDPM forward noising (Eq. 1 set-up): xk = sqrt(abar_k) x0 + sqrt(1 - abar_k) eps, per sample k[n]
+__global__ void k_ddpm_noise(const float *__restrict__ x0, const float *__restrict__ eps, const int *__restrict__ k,
+                             const float *__restrict__ abar, int N, int per, float *__restrict__ xk) {
+    const long long total = (long long)N * per;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const float ab = abar[k[i / per]];
+        xk[i] = sqrtf(ab) * x0[i] + sqrtf(1.f - ab) * eps[i];
+    }
+}
+
+// mean squared error between pred and target (Eq. 1) with weights per sample:
+// loss = sum_n w_n sum_j (pred - target)^2 / (N * per); dpred = 2 w_n (pred - target) / (N * per)
+__global__ void k_mse(const float *__restrict__ pred, const float *__restrict__ target, const float *__restrict__ w,
+                      int N, int per, float *__restrict__ dpred, float *__restrict__ loss_partial) {
+    __shared__ float s[256];
+    const long long total = (long long)N * per;
+    const float inv = 1.f / (float)total;
+    float acc = 0.f;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const float wn = w ? w[i / per] : 1.f;
+        const float d = pred[i] - target[i];
+        acc += wn * d * d;
+        dpred[i] = 2.f * wn * d * inv;
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_partial[blockIdx.x] = s[0] * inv;
+}
+
+// DDIM step (eta = 0): x0hat = (xk - sqrt(1 - ab_k) eps) / sqrt(ab_k);
+// x_prev = sqrt(ab_prev) x0hat + sqrt(1 - ab_prev) eps (ab_prev = 1 at the end)
+__global__ void k_ddim_step(const float *__restrict__ xk, const float *__restrict__ eps, float ab_k, float ab_prev,
+                            long long n, float clip, float *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float x0 = (xk[i] - sqrtf(1.f - ab_k) * eps[i]) / sqrtf(ab_k);
+        x0 = fminf(fmaxf(x0, -clip), clip);
+        out[i] = sqrtf(ab_prev) * x0 + sqrtf(1.f - ab_prev) * eps[i];
+    }
+}
+
+__global__ void k_clamp_affine(const float *__restrict__ x, float a, float b, float lo, float hi,
+                               float *__restrict__ out, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = fminf(fmaxf(fmaf(a, x[i], b), lo), hi);
+}
+
+__global__ void k_to_bf16(const float *__restrict__ x, __nv_bfloat16 *__restrict__ y, long long n) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// ---------------------------------------------------------------- launchers
+static unsigned grid_for(long long n, int block = 256) {
+    long long g = (n + block - 1) / block;
+    if (g > 152LL * 64) g = 152LL * 64;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
+                float beta, float *C, int ldc, const float *bias, cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
+    if (!ta && !tb) k_gemm_f32<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
+    else if (!ta && tb) k_gemm_f32<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
+    else if (ta && !tb) k_gemm_f32<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
+    else k_gemm_f32<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
+    return (int)cudaGetLastError();
+}
+
+int nn_gemm_bf16(int M, int N, int K, const void *A, const void *W, float *C, const float *bias, cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+    k_gemm_bf16<<<grid, 256, 0, st>>>(M, N, K, (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)W, C, bias);
+    return (int)cudaGetLastError();
+}
+
+int nn_im2col1d(const float *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols, int bf16,
+                cudaStream_t st) {
+    const long long total = (long long)N * Lo * kc_pad;
+    if (bf16) k_im2col1d<__nv_bfloat16><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
+    else k_im2col1d<float><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (float *)cols);
+    return (int)cudaGetLastError();
+}
+
+int nn_col2im1d(const float *cols, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, float *dx,
+                cudaStream_t st) {
+    k_col2im1d<<<grid_for((long long)N * L * C), 256, 0, st>>>(cols, N, L, C, k, s, p, Lo, kc_pad, dx);
+    return (int)cudaGetLastError();
+}
+
+int nn_colsum(const float *y, int R, int C, float *out, int accumulate, cudaStream_t st) {
+    k_colsum<<<(C + 127) / 128, 128, 0, st>>>(y, R, C, out, accumulate);
+    return (int)cudaGetLastError();
+}
+
+int nn_gn_fwd(const float *x, int N, int L, int C, int G, const float *gamma, const float *beta, float eps, float *y,
+              float *mean, float *rstd, cudaStream_t st) {
+    k_gn_fwd<<<N * G, 256, 0, st>>>(x, N, L, C, G, gamma, beta, eps, y, mean, rstd);
+    return (int)cudaGetLastError();
+}
+
+int nn_gn_bwd(const float *dy, const float *x, int N, int L, int C, int G, const float *gamma, const float *mean,
+              const float *rstd, float *dx, float *dgamma_n, float *dbeta_n, cudaStream_t st) {
+    k_gn_bwd<<<N * G, 256, 0, st>>>(dy, x, N, L, C, G, gamma, mean, rstd, dx, dgamma_n, dbeta_n);
+    return (int)cudaGetLastError();
+}
+
+int nn_mish(const float *x, const float *dy, float *out, long long n, int backward, cudaStream_t st) {
+    if (backward) k_mish_bwd<<<grid_for(n), 256, 0, st>>>(dy, x, out, n);
+    else k_mish_fwd<<<grid_for(n), 256, 0, st>>>(x, out, n);
+    return (int)cudaGetLastError();
+}
+
+int nn_film(const float *h, const float *film, int N, int L, int C, float *y, const float *dy, float *dh,
+            float *dfilm, int backward, cudaStream_t st) {
+    if (backward) k_film_bwd<<<grid_for((long long)N * C), 256, 0, st>>>(dy, h, film, N, L, C, dh, dfilm);
+    else k_film_fwd<<<grid_for((long long)N * L * C), 256, 0, st>>>(h, film, N, L, C, y);
+    return (int)cudaGetLastError();
+}
+
+int nn_axpby(float a, const float *x, float b, const float *y, float *out, long long n, cudaStream_t st) {
+    k_axpby<<<grid_for(n), 256, 0, st>>>(a, x, b, y, out, n);
+    return (int)cudaGetLastError();
+}
+
+int nn_copy_cols(const float *in, long long R, int Cin, int in_stride, int in_off, float *out, int out_stride,
+                 int out_off, int accumulate, cudaStream_t st) {
+    k_copy_cols<<<grid_for(R * Cin), 256, 0, st>>>(in, R, Cin, in_stride, in_off, out, out_stride, out_off, accumulate);
+    return (int)cudaGetLastError();
+}
+
+int nn_upsample2(const float *x, int N, int L, int C, float *y, int backward, cudaStream_t st) {
+    k_upsample2<<<grid_for((long long)N * 2 * L * C), 256, 0, st>>>(x, N, L, C, y, backward);
+    return (int)cudaGetLastError();
+}
+
+int nn_gather(const float *in, const int *idx, float *out, long long n, long long per, int scatter, cudaStream_t st) {
+    k_gather<<<grid_for(n * per), 256, 0, st>>>(in, idx, out, n, per, scatter);
+    return (int)cudaGetLastError();
+}
+
+int nn_sinusoid(const int *k, int N, int dim, float *out, cudaStream_t st) {
+    k_sinusoid<<<(N + 127) / 128, 128, 0, st>>>(k, N, dim, out);
+    return (int)cudaGetLastError();
+}
+
+int nn_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps,
+            float wd, int step, cudaStream_t st) {
+    const float bc1 = 1.f - powf(b1, (float)step), bc2 = 1.f - powf(b2, (float)step);
+    k_adam<<<grid_for(n), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, wd, bc1, bc2);
+    return (int)cudaGetLastError();
+}
+
+int nn_ddpm_noise(const float *x0, const float *eps, const int *k, const float *abar, int N, int per, float *xk,
+                  cudaStream_t st) {
+    k_ddpm_noise<<<grid_for((long long)N * per), 256, 0, st>>>(x0, eps, k, abar, N, per, xk);
+    return (int)cudaGetLastError();
+}
+
+int nn_mse(const float *pred, const float *target, const float *w, int N, int per, float *dpred, float *loss_partial,
+           int blocks, cudaStream_t st) {
+    k_mse<<<blocks, 256, 0, st>>>(pred, target, w, N, per, dpred, loss_partial);
+    return (int)cudaGetLastError();
+}
+
+int nn_ddim_step(const float *xk, const float *eps, float ab_k, float ab_prev, long long n, float clip, float *out,
+                 cudaStream_t st) {
+    k_ddim_step<<<grid_for(n), 256, 0, st>>>(xk, eps, ab_k, ab_prev, n, clip, out);
+    return (int)cudaGetLastError();
+}
+
+int nn_clamp_affine(const float *x, float a, float b, float lo, float hi, float *out, long long n, cudaStream_t st) {
+    k_clamp_affine<<<grid_for(n), 256, 0, st>>>(x, a, b, lo, hi, out, n);
+    return (int)cudaGetLastError();
+}
+
+int nn_to_bf16(const float *x, void *y, long long n, cudaStream_t st) {
+    k_to_bf16<<<grid_for(n), 256, 0, st>>>(x, (__nv_bfloat16 *)y, n);
+    return (int)cudaGetLastError();
+}
+
+}  // namespace dseed

@@ -1,0 +1,438 @@
+"""Conditional denoiser that proposes seed trajectories (the learned part of the
+method, paper Sec. 4.2-4.3), built from libdseed's layer kernels.
+
+Orchestration only: each layer call below is one C-ABI kernel launch
+(binding.nn); this module decides their order, keeps the activations the
+backward pass needs (a tape of closures, replayed in reverse), and owns the
+parameter, gradient and Adam buffers (device tensors).  Training runs in FP32;
+`infer` runs every GEMM on the tensor cores in BF16 (FP32 accumulation).
+
+Inputs of one sample: the noisy normalised trajectory x_k [T][D], the
+diffusion step k, the normalised start configuration [D], the goal pose [7]
+and the scene's 32^3 occupancy grid.  Output: the predicted noise [T][D]
+(Eq. 1).  Joint values are normalised to [-1, 1] by the mechanical limits
+(App. A.4).
+"""
+from __future__ import annotations
+
+import math
+from typing import Callable, Dict, List, Optional
+
+import numpy as np
+import torch
+
+from . import binding as B
+from . import netspec as NS
+
+
+def _nn(name, *a):
+    B.nn(name, *a)
+
+
+class Tape:
+    def __init__(self):
+        self.ops: List[Callable] = []
+        self.grads: Dict[int, torch.Tensor] = {}
+        self.keep: List[torch.Tensor] = []
+
+    def record(self, fn):
+        self.ops.append(fn)
+
+    def grad(self, t: torch.Tensor) -> Optional[torch.Tensor]:
+        return self.grads.get(id(t))
+
+    def add_grad(self, t: torch.Tensor, g: torch.Tensor):
+        cur = self.grads.get(id(t))
+        if cur is None:
+            self.grads[id(t)] = g
+            self.keep.append(t)
+        else:
+            _nn("axpby", 1.0, cur, 1.0, g, cur, cur.numel())
+
+
+def cosine_abar(K: int, s: float = 0.008) -> np.ndarray:
+    """Cumulative noise schedule abar_k, k = 0..K-1 (squared-cosine schedule)."""
+    f = lambda t: math.cos((t / K + s) / (1 + s) * math.pi / 2) ** 2
+    betas = np.array([min(1 - f(k + 1) / f(k), 0.999) for k in range(K)])
+    return np.cumprod(1.0 - betas)
+
+
+class Denoiser:
+    def __init__(self, spec: NS.NetSpec = NS.NetSpec(), device="cuda", seed: int = 0):
+        self.spec = spec
+        self.dev = torch.device(device)
+        self.offsets = NS.param_offsets(spec)
+        self.n_params = NS.param_count(spec)
+        self.params = torch.zeros(self.n_params, dtype=torch.float32, device=self.dev)
+        self.grads = torch.zeros_like(self.params)
+        self.m = torch.zeros_like(self.params)
+        self.v = torch.zeros_like(self.params)
+        self.step_count = 0
+        m1, m2 = NS.occ_patch_maps(spec)
+        self.map1 = torch.tensor(m1, dtype=torch.int32, device=self.dev)
+        self.map2 = torch.tensor(m2, dtype=torch.int32, device=self.dev)
+        self.abar = torch.tensor(cosine_abar(spec.K), dtype=torch.float32, device=self.dev)
+        self.abar_host = cosine_abar(spec.K)
+        self._bf16: Dict[str, torch.Tensor] = {}
+        self.init_params(seed)
+
+    # ------------------------------------------------------------------ parameters
+    def P(self, name: str) -> torch.Tensor:
+        off, shape = self.offsets[name]
+        n = int(np.prod(shape))
+        return self.params[off:off + n]
+
+    def G(self, name: str) -> torch.Tensor:
+        off, shape = self.offsets[name]
+        n = int(np.prod(shape))
+        return self.grads[off:off + n]
+
+    def init_params(self, seed: int):
+        """Uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) weights and biases; group-norm
+        gains 1, offsets 0; the output convolution starts at zero."""
+        rng = np.random.default_rng(seed)
+        host = np.zeros(self.n_params, np.float32)
+        for name, (off, shape) in self.offsets.items():
+            n = int(np.prod(shape))
+            if ".g" in name and name.endswith(".w") and len(shape) == 1:
+                host[off:off + n] = 1.0
+                continue
+            if ".g" in name and name.endswith(".b") and len(shape) == 1:
+                continue
+            wname = name[:-2] + ".w"
+            wshape = self.offsets[wname][1]
+            fan_in = int(np.prod(wshape[1:]))
+            bound = 1.0 / math.sqrt(fan_in)
+            host[off:off + n] = rng.uniform(-bound, bound, size=n)
+        for name in ("fin.o.w", "fin.o.b"):
+            off, shape = self.offsets[name]
+            host[off:off + int(np.prod(shape))] = 0.0
+        self.params.copy_(torch.from_numpy(host))
+        self.m.zero_()
+        self.v.zero_()
+        self.step_count = 0
+        self._bf16.clear()
+
+    # ------------------------------------------------------------------ layers (FP32, with tape)
+    def linear(self, x, name, tape, R=None):
+        """x [R][in] -> [R][out] with weight name.w [out][in], bias name.b."""
+        W, b = self.P(name + ".w"), self.P(name + ".b")
+        out_f, in_f = self.offsets[name + ".w"][1][0], int(np.prod(self.offsets[name + ".w"][1][1:]))
+        R = x.numel() // in_f if R is None else R
+        y = torch.empty((R, out_f), dtype=torch.float32, device=self.dev)
+        if self.bf16_mode:
+            xb = torch.empty((R, _pad16(in_f)), dtype=torch.bfloat16, device=self.dev)
+            _nn("im2col1d", x, R, 1, in_f, 1, 1, 0, 1, _pad16(in_f), xb, 1)
+            _nn("gemm_bf16", R, out_f, _pad16(in_f), xb, self.w_bf16(name + ".w", out_f, in_f), y, b)
+            return y
+        _nn("gemm_f32", 0, 1, R, out_f, in_f, 1.0, x, in_f, W, in_f, 0.0, y, out_f, b)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                _nn("gemm_f32", 1, 0, out_f, in_f, R, 1.0, dy, out_f, x, in_f, 1.0, self.G(name + ".w"), in_f, None)
+                _nn("colsum", dy, R, out_f, self.G(name + ".b"), 1)
+                dx = torch.empty_like(x)
+                _nn("gemm_f32", 0, 0, R, in_f, out_f, 1.0, dy, out_f, W, in_f, 0.0, dx, in_f, None)
+                tape.add_grad(x, dx)
+            tape.record(bwd)
+        return y
+
+    def conv(self, x, N, L, name, k, s, p, tape):
+        """x [N][L][Cin] -> [N][Lo][Cout], weight [Cout][k][Cin]."""
+        W, b = self.P(name + ".w"), self.P(name + ".b")
+        cout, kk, cin = self.offsets[name + ".w"][1]
+        assert kk == k
+        Lo = (L + 2 * p - k) // s + 1
+        kc = k * cin
+        y = torch.empty((N, Lo, cout), dtype=torch.float32, device=self.dev)
+        if self.bf16_mode:
+            cols = torch.empty((N * Lo, _pad16(kc)), dtype=torch.bfloat16, device=self.dev)
+            _nn("im2col1d", x, N, L, cin, k, s, p, Lo, _pad16(kc), cols, 1)
+            _nn("gemm_bf16", N * Lo, cout, _pad16(kc), cols, self.w_bf16(name + ".w", cout, kc), y, b)
+            return y, Lo
+        cols = torch.empty((N * Lo, kc), dtype=torch.float32, device=self.dev)
+        _nn("im2col1d", x, N, L, cin, k, s, p, Lo, kc, cols, 0)
+        _nn("gemm_f32", 0, 1, N * Lo, cout, kc, 1.0, cols, kc, W, kc, 0.0, y, cout, b)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                _nn("gemm_f32", 1, 0, cout, kc, N * Lo, 1.0, dy, cout, cols, kc, 1.0, self.G(name + ".w"), kc, None)
+                _nn("colsum", dy, N * Lo, cout, self.G(name + ".b"), 1)
+                dcols = torch.empty_like(cols)
+                _nn("gemm_f32", 0, 0, N * Lo, kc, cout, 1.0, dy, cout, W, kc, 0.0, dcols, kc, None)
+                dx = torch.zeros_like(x)
+                _nn("col2im1d", dcols, N, L, cin, k, s, p, Lo, kc, dx)
+                tape.add_grad(x, dx)
+            tape.record(bwd)
+        return y, Lo
+
+    def groupnorm(self, x, N, L, C, name, tape):
+        gamma, beta = self.P(name + ".w"), self.P(name + ".b")
+        G = self.spec.groups
+        y = torch.empty_like(x)
+        mean = torch.empty((N, G), dtype=torch.float32, device=self.dev)
+        rstd = torch.empty_like(mean)
+        _nn("groupnorm_fwd", x, N, L, C, G, gamma, beta, self.spec.gn_eps, y, mean, rstd)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                dx = torch.empty_like(x)
+                dg = torch.empty((N, C), dtype=torch.float32, device=self.dev)
+                db = torch.empty_like(dg)
+                _nn("groupnorm_bwd", dy, x, N, L, C, G, gamma, mean, rstd, dx, dg, db)
+                _nn("colsum", dg, N, C, self.G(name + ".w"), 1)
+                _nn("colsum", db, N, C, self.G(name + ".b"), 1)
+                tape.add_grad(x, dx)
+            tape.record(bwd)
+        return y
+
+    def mish(self, x, tape):
+        y = torch.empty_like(x)
+        _nn("mish", x, None, y, x.numel(), 0)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                dx = torch.empty_like(x)
+                _nn("mish", x, dy, dx, x.numel(), 1)
+                tape.add_grad(x, dx)
+            tape.record(bwd)
+        return y
+
+    def film(self, h, f, N, L, C, tape):
+        y = torch.empty_like(h)
+        _nn("film", h, f, N, L, C, y, None, None, None, 0)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                dh = torch.empty_like(h)
+                df = torch.empty_like(f)
+                _nn("film", h, f, N, L, C, None, dy, dh, df, 1)
+                tape.add_grad(h, dh)
+                tape.add_grad(f, df)
+            tape.record(bwd)
+        return y
+
+    def add(self, a, b, tape):
+        y = torch.empty_like(a)
+        _nn("axpby", 1.0, a, 1.0, b, y, a.numel())
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                tape.add_grad(a, dy)
+                tape.add_grad(b, dy.clone())
+            tape.record(bwd)
+        return y
+
+    def concat(self, tensors, R, tape, shape=None):
+        widths = [t.numel() // R for t in tensors]
+        Ct = sum(widths)
+        y = torch.empty(shape if shape is not None else (R, Ct), dtype=torch.float32, device=self.dev)
+        off = 0
+        for t, w in zip(tensors, widths):
+            _nn("copy_cols", t, R, w, w, 0, y, Ct, off, 0)
+            off += w
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                o = 0
+                for t, w in zip(tensors, widths):
+                    g = torch.empty((R, w), dtype=torch.float32, device=self.dev)
+                    _nn("copy_cols", dy, R, w, Ct, o, g, w, 0, 0)
+                    tape.add_grad(t, g.view(t.shape))
+                    o += w
+            tape.record(bwd)
+        return y
+
+    def upsample(self, x, N, L, C, tape):
+        y = torch.empty((N, 2 * L, C), dtype=torch.float32, device=self.dev)
+        _nn("upsample2", x, N, L, C, y, 0)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                dx = torch.empty_like(x)
+                _nn("upsample2", dy, N, L, C, dx, 1)
+                tape.add_grad(x, dx)
+            tape.record(bwd)
+        return y
+
+    def gather(self, x, idx, N, per, tape):
+        y = torch.empty((N, per), dtype=torch.float32, device=self.dev)
+        _nn("gather", x, idx, y, N, per, 0)
+        if tape is not None:
+            def bwd():
+                dy = tape.grad(y)
+                if dy is None:
+                    return
+                dx = torch.zeros((N, per), dtype=torch.float32, device=self.dev)
+                _nn("gather", dy, idx, dx, N, per, 1)
+                tape.add_grad(x, dx.view(x.shape))
+            tape.record(bwd)
+        return y
+
+    # ------------------------------------------------------------------ BF16 weights
+    bf16_mode = False
+
+    def w_bf16(self, name, out_f, kc):
+        w = self._bf16.get(name)
+        if w is None:
+            # [out][kc] FP32 -> [out][pad16(kc)] BF16 (zero tail) via im2col with L = 1
+            w = torch.empty((out_f, _pad16(kc)), dtype=torch.bfloat16, device=self.dev)
+            _nn("im2col1d", self.P(name), out_f, 1, kc, 1, 1, 0, 1, _pad16(kc), w, 1)
+            self._bf16[name] = w
+        return w
+
+    # ------------------------------------------------------------------ network
+    def res_block(self, x, N, L, name, cin, cout, mc, tape):
+        k = self.spec.kernel
+        a, _ = self.conv(x, N, L, name + ".c1", k, 1, k // 2, tape)
+        b = self.groupnorm(a, N, L, cout, name + ".g1", tape)
+        c = self.mish(b, tape)
+        f = self.linear(mc, name + ".f", tape)
+        d = self.film(c, f, N, L, cout, tape)
+        e, _ = self.conv(d, N, L, name + ".c2", k, 1, k // 2, tape)
+        g = self.groupnorm(e, N, L, cout, name + ".g2", tape)
+        h = self.mish(g, tape)
+        if cin != cout:
+            r, _ = self.conv(x, N, L, name + ".r", 1, 1, 0, tape)
+        else:
+            r = x
+        return self.add(h, r, tape)
+
+    def condition(self, k, qs, goal, occ, tape):
+        """cond = [time MLP (sinusoid(k)), problem MLP (q_start, goal), occupancy
+        encoder]; returns Mish(cond) [N][cond_dim], the input of every FiLM layer."""
+        s = self.spec
+        N = qs.shape[0]
+        te = torch.empty((N, s.t_sin), dtype=torch.float32, device=self.dev)
+        _nn("sinusoid", k, N, s.t_sin, te)
+        t1 = self.mish(self.linear(te, "t.l1", tape), tape)
+        t2 = self.linear(t1, "t.l2", tape)
+        pin = self.concat([qs, goal], N, tape)
+        p1 = self.mish(self.linear(pin, "p.l1", tape), tape)
+        p2 = self.linear(p1, "p.l2", tape)
+        o0 = self.gather(occ, self.map1, N, s.occ_n ** 3, tape)                      # [N][8^3][4^3]
+        o1 = self.mish(self.linear(o0, "o.c1", tape, R=N * s.occ_g1 ** 3), tape)     # [N*8^3][c1]
+        o2 = self.gather(o1, self.map2, N, s.occ_g1 ** 3 * s.occ_c1, tape)           # [N][4^3][2^3 c1]
+        o3 = self.mish(self.linear(o2, "o.c2", tape, R=N * s.occ_g2 ** 3), tape)     # [N*4^3][c2]
+        o4 = self.linear(o3, "o.l", tape, R=N)                                       # flattened per sample
+        cond = self.concat([t2, p2, o4], N, tape)
+        return self.mish(cond, tape)
+
+    def unet(self, x, N, mc, tape):
+        s = self.spec
+        c1, c2, c3 = s.chans
+        T = s.T
+        h = self.res_block(x, N, T, "d1a", s.D, c1, mc, tape)
+        h = self.res_block(h, N, T, "d1b", c1, c1, mc, tape)
+        h, L2 = self.conv(h, N, T, "down1", 3, 2, 1, tape)
+        h = self.res_block(h, N, L2, "d2a", c1, c2, mc, tape)
+        s2 = self.res_block(h, N, L2, "d2b", c2, c2, mc, tape)
+        h, L3 = self.conv(s2, N, L2, "down2", 3, 2, 1, tape)
+        h = self.res_block(h, N, L3, "d3a", c2, c3, mc, tape)
+        s3 = self.res_block(h, N, L3, "d3b", c3, c3, mc, tape)
+        h = self.res_block(s3, N, L3, "mid", c3, c3, mc, tape)
+        h = self.concat([h, s3], N * L3, tape, shape=(N, L3, 2 * c3))
+        h = self.res_block(h, N, L3, "u2a", 2 * c3, c2, mc, tape)
+        h = self.res_block(h, N, L3, "u2b", c2, c2, mc, tape)
+        h = self.upsample(h, N, L3, c2, tape)
+        h, _ = self.conv(h, N, L2, "up2", 3, 1, 1, tape)
+        h = self.concat([h, s2], N * L2, tape, shape=(N, L2, 2 * c2))
+        h = self.res_block(h, N, L2, "u1a", 2 * c2, c1, mc, tape)
+        h = self.res_block(h, N, L2, "u1b", c1, c1, mc, tape)
+        h = self.upsample(h, N, L2, c1, tape)
+        h, _ = self.conv(h, N, T, "up1", 3, 1, 1, tape)
+        h, _ = self.conv(h, N, T, "fin.c", s.kernel, 1, s.kernel // 2, tape)
+        h = self.mish(self.groupnorm(h, N, T, c1, "fin.g", tape), tape)
+        out, _ = self.conv(h, N, T, "fin.o", 1, 1, 0, tape)
+        return out
+
+    def forward(self, xk, k, qs, goal, occ, tape: Optional[Tape] = None):
+        """Predicted noise [N][T][D] (FP32)."""
+        N = xk.shape[0]
+        mc = self.condition(k, qs, goal, occ, tape)
+        return self.unet(xk, N, mc, tape)
+
+    @staticmethod
+    def backward(tape: Tape, out: torch.Tensor, dout: torch.Tensor):
+        tape.grads[id(out)] = dout
+        for fn in reversed(tape.ops):
+            fn()
+
+    # ------------------------------------------------------------------ training
+    def loss_and_grad(self, x0, qs, goal, occ, k, eps, weights=None):
+        """Eq. 1 (optionally weighted per sample as in Eq. 2): noise the clean
+        normalised trajectories x0 to step k with eps, predict the noise,
+        accumulate parameter gradients of the mean squared error into self.grads.
+        Returns the loss (device scalar)."""
+        N = x0.shape[0]
+        per = x0.numel() // N
+        xk = torch.empty_like(x0)
+        _nn("ddpm_noise", x0, eps, k, self.abar, N, per, xk)
+        tape = Tape()
+        pred = self.forward(xk, k, qs, goal, occ, tape)
+        dpred = torch.empty_like(pred)
+        blocks = 64
+        part = torch.empty(blocks, dtype=torch.float32, device=self.dev)
+        _nn("mse", pred, eps, weights, N, per, dpred, part, blocks)
+        self.backward(tape, pred, dpred)
+        return part.sum()
+
+    def adam_step(self, lr=3e-4, b1=0.9, b2=0.999, eps=1e-8, wd=0.0):
+        self.step_count += 1
+        _nn("adam", self.params, self.grads, self.m, self.v, self.n_params, lr, b1, b2, eps, wd, self.step_count)
+        self.grads.zero_()
+        self._bf16.clear()
+
+    # ------------------------------------------------------------------ inference
+    def infer(self, xk, k, qs, goal, occ):
+        """Predicted noise with every GEMM on the BF16 tensor cores."""
+        self.bf16_mode = True
+        try:
+            return self.forward(xk, k, qs, goal, occ, None)
+        finally:
+            self.bf16_mode = False
+
+    def ddim_sample(self, qs, goal, occ, noise, steps: int = 10, bf16: bool = True, clip: float = 1.0):
+        """DDIM (deterministic) from x_K = noise over `steps` evenly spaced steps
+        of the K-step schedule; returns normalised trajectories [N][T][D]."""
+        K = self.spec.K
+        ks = np.linspace(K - 1, 0, steps).round().astype(int)
+        x = noise.clone()
+        N = x.shape[0]
+        for i, kk in enumerate(ks):
+            kt = torch.full((N,), int(kk), dtype=torch.int32, device=self.dev)
+            eps = self.infer(x, kt, qs, goal, occ) if bf16 else self.forward(x, kt, qs, goal, occ, None)
+            ab_k = float(self.abar_host[kk])
+            ab_prev = float(self.abar_host[ks[i + 1]]) if i + 1 < len(ks) else 1.0
+            out = torch.empty_like(x)
+            _nn("ddim_step", x, eps, ab_k, ab_prev, x.numel(), clip, out)
+            x = out
+        return x
+
+    # ------------------------------------------------------------------ checkpoints
+    def state(self) -> dict:
+        return {"spec": self.spec.__dict__, "params": self.params.detach().cpu().numpy()}
+
+    def load_state(self, st: dict):
+        self.params.copy_(torch.from_numpy(np.asarray(st["params"], np.float32)))
+        self._bf16.clear()
+
+
+def _pad16(n: int) -> int:
+    return (n + 15) // 16 * 16
