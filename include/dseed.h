@@ -438,6 +438,10 @@ int dseed_nn_upsample2(const float *x_dev, int N, int L, int C, float *y_dev, in
  * adjoint scatter-add (scatter != 0): out[r][idx[e]] += in[r][e]. */
 int dseed_nn_gather(const float *in_dev, const int *idx_dev, float *out_dev, long long n, long long per,
                     int scatter, cudaStream_t stream);
+/* Row gather: out[r] = in[rows[r]] for rows [R_out] (int32), rows of C floats
+ * (one condition vector per problem broadcast to its samples). */
+int dseed_nn_gather_rows(const float *in_dev, const int *rows_dev, long long R_out, int C, float *out_dev,
+                         cudaStream_t stream);
 /* Sinusoidal embedding of integer diffusion steps k [N] into [N][dim]. */
 int dseed_nn_sinusoid(const int *k_dev, int N, int dim, float *out_dev, cudaStream_t stream);
 /* One Adam step with decoupled weight decay on n parameters (step >= 1). */

@@ -71,9 +71,9 @@ def _res_block(x, P, name, cin, cout, mc, spec):
     return h + r
 
 
-def condition(spec, P, k, qs, goal, occ):
+def condition(spec, P, k, qs, qg, goal, occ):
     t = _lin(F.mish(_lin(sinusoid(k, spec.t_sin), P, "t.l1")), P, "t.l2")
-    p = _lin(F.mish(_lin(torch.cat([qs, goal], 1), P, "p.l1")), P, "p.l2")
+    p = _lin(F.mish(_lin(torch.cat([qs, qg, goal], 1), P, "p.l1")), P, "p.l2")
     N = qs.shape[0]
     n, p1, p2 = spec.occ_n, spec.occ_p1, spec.occ_p2
     vol = occ.view(N, 1, n, n, n)                          # (z, y, x)
@@ -86,9 +86,9 @@ def condition(spec, P, k, qs, goal, occ):
     return F.mish(torch.cat([t, p, o], 1))
 
 
-def forward(spec: NS.NetSpec, P: dict, xk, k, qs, goal, occ):
+def forward(spec: NS.NetSpec, P: dict, xk, k, qs, qg, goal, occ):
     """xk [N][T][D] (channels-last like the CUDA path) -> predicted noise [N][T][D]."""
-    mc = condition(spec, P, k, qs, goal, occ)
+    mc = condition(spec, P, k, qs, qg, goal, occ)
     c1, c2, c3 = spec.chans
     x = xk.permute(0, 2, 1)                                # [N][D][T]
     h = _res_block(x, P, "d1a", spec.D, c1, mc, spec)
@@ -118,27 +118,27 @@ def ddpm_noise(x0, eps, k, abar):
     return torch.sqrt(ab) * x0 + torch.sqrt(1 - ab) * eps
 
 
-def loss_and_grads(spec, flat_params, x0, qs, goal, occ, k, eps, abar, weights=None):
+def loss_and_grads(spec, flat_params, x0, qs, qg, goal, occ, k, eps, abar, weights=None):
     """Eq. 1 (weighted per sample as in Eq. 2): mean over all entries of
     w_n (Theta(x_k, k, cond) - eps)^2.  Returns (loss, dL/dparams flat)."""
     flat = torch.as_tensor(np.asarray(flat_params), dtype=DT).clone().requires_grad_(True)
     P = unpack(spec, flat)
     t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
-    x0, qs, goal, occ, eps = t(x0), t(qs), t(goal), t(occ), t(eps)
+    x0, qs, qg, goal, occ, eps = t(x0), t(qs), t(qg), t(goal), t(occ), t(eps)
     k = torch.as_tensor(np.asarray(k), dtype=torch.long)
     xk = ddpm_noise(x0, eps, k, abar)
-    pred = forward(spec, P, xk, k, qs, goal, occ)
+    pred = forward(spec, P, xk, k, qs, qg, goal, occ)
     w = torch.ones(x0.shape[0], dtype=DT) if weights is None else t(weights)
     loss = (w.view(-1, 1, 1) * (pred - eps) ** 2).sum() / pred.numel()
     loss.backward()
     return float(loss.detach()), flat.grad.detach().numpy()
 
 
-def predict(spec, flat_params, xk, k, qs, goal, occ):
+def predict(spec, flat_params, xk, k, qs, qg, goal, occ):
     P = unpack(spec, torch.as_tensor(np.asarray(flat_params), dtype=DT))
     t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
     with torch.no_grad():
-        return forward(spec, P, t(xk), torch.as_tensor(np.asarray(k), dtype=torch.long), t(qs), t(goal),
+        return forward(spec, P, t(xk), torch.as_tensor(np.asarray(k), dtype=torch.long), t(qs), t(qg), t(goal),
                        t(occ)).numpy()
 
 

@@ -144,6 +144,7 @@ _SIGS = {
     "dseed_nn_upsample2": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "dseed_nn_gather": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_longlong, C.c_int, C.c_void_p],
                         C.c_int),
+    "dseed_nn_gather_rows": ([C.c_void_p, C.c_void_p, C.c_longlong, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "dseed_nn_sinusoid": ([C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "dseed_nn_adam": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong, C.c_float, C.c_float, C.c_float,
                        C.c_float, C.c_float, C.c_int, C.c_void_p], C.c_int),

@@ -26,6 +26,7 @@ int nn_copy_cols(const float *in, long long R, int Cin, int in_stride, int in_of
 int nn_upsample2(const float *x, int N, int L, int C, float *y, int backward, cudaStream_t st);
 int nn_gather(const float *in, const int *idx, float *out, long long n, long long per, int scatter, cudaStream_t st);
 int nn_sinusoid(const int *k, int N, int dim, float *out, cudaStream_t st);
+int nn_gather_rows(const float *in, const int *rows, long long R, int C, float *out, cudaStream_t st);
 int nn_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps,
             float wd, int step, cudaStream_t st);
 int nn_ddpm_noise(const float *x0, const float *eps, const int *k, const float *abar, int N, int per, float *xk,
@@ -140,6 +141,12 @@ int dseed_nn_gather(const float *in_dev, const int *idx_dev, float *out_dev, lon
                     cudaStream_t stream) {
     NEED(n >= 0 && per >= 1 && in_dev && idx_dev && out_dev, "gather: bad arguments");
     return cu(dseed::nn_gather(in_dev, idx_dev, out_dev, n, per, scatter, stream), "gather");
+}
+
+int dseed_nn_gather_rows(const float *in_dev, const int *rows_dev, long long R_out, int C, float *out_dev,
+                         cudaStream_t stream) {
+    NEED(R_out >= 0 && C >= 1 && in_dev && rows_dev && out_dev, "gather_rows: bad arguments");
+    return cu(dseed::nn_gather_rows(in_dev, rows_dev, R_out, C, out_dev, stream), "gather_rows");
 }
 
 int dseed_nn_sinusoid(const int *k_dev, int N, int dim, float *out_dev, cudaStream_t stream) {

@@ -19,27 +19,33 @@ namespace dseed {
 // op(A) = A (row-major [M][K], lda) or A^T (A stored [K][M]); same for B.
 constexpr int GB = 64, GK = 16;
 
-template <bool TA, bool TB>
+// SPLIT: blockIdx.z takes K-range [z * kchunk, (z + 1) * kchunk) and adds
+// alpha * partial into C atomically (used for accumulating weight gradients,
+// where M x N is small and K = batch x length is large).
+template <bool TA, bool TB, bool SPLIT>
 __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alpha, const float *__restrict__ A,
                                                  int lda, const float *__restrict__ B, int ldb, float beta,
-                                                 float *__restrict__ C, int ldc, const float *__restrict__ bias) {
+                                                 float *__restrict__ C, int ldc, const float *__restrict__ bias,
+                                                 int kchunk) {
     __shared__ float As[GK][GB + 4];
     __shared__ float Bs[GK][GB + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
     const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    const int kb = SPLIT ? blockIdx.z * kchunk : 0;
+    const int ke = SPLIT ? min(K, kb + kchunk) : K;
     float acc[4][4] = {};
-    for (int k0 = 0; k0 < K; k0 += GK) {
+    for (int k0 = kb; k0 < ke; k0 += GK) {
         for (int t = threadIdx.x; t < GB * GK; t += 256) {
             const int kk = t % GK, mm = t / GK;                    // A tile: [mm][kk]
             const int gm = m0 + mm, gk = k0 + kk;
             float a = 0.f;
-            if (gm < M && gk < K) a = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
+            if (gm < M && gk < ke) a = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
             As[kk][mm] = a;
-            const int nn = t % GB, kb = t / GB;                    // B tile: [kb][nn]
-            const int gn = n0 + nn, gk2 = k0 + kb;
+            const int nn = t % GB, kr = t / GB;                    // B tile: [kr][nn]
+            const int gn = n0 + nn, gk2 = k0 + kr;
             float b = 0.f;
-            if (gn < N && gk2 < K) b = TB ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn];
-            Bs[kb][nn] = b;
+            if (gn < N && gk2 < ke) b = TB ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn];
+            Bs[kr][nn] = b;
         }
         __syncthreads();
 #pragma unroll
@@ -64,6 +70,10 @@ __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alp
         for (int j = 0; j < 4; ++j) {
             const int gn = n0 + tx * 4 + j;
             if (gn >= N) continue;
+            if (SPLIT) {
+                atomicAdd(C + (size_t)gm * ldc + gn, alpha * acc[i][j]);
+                continue;
+            }
             float v = alpha * acc[i][j];
             if (beta != 0.f) v += beta * C[(size_t)gm * ldc + gn];
             if (bias) v += bias[gn];
@@ -196,13 +206,22 @@ __global__ void k_col2im1d(const float *__restrict__ cols, int N, int L, int C, 
     }
 }
 
-// column sums: out[c] (+)= sum_r y[r][c]
-__global__ void k_colsum(const float *__restrict__ y, int R, int C, float *__restrict__ out, int accumulate) {
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
+// column sums: out[c] += sum over a chunk of rows of y[r][c]; block = 32
+// columns x 8 row lanes, grid.y = row chunks, partial sums added atomically
+__global__ void k_colsum(const float *__restrict__ y, int R, int C, int rows_per, float *__restrict__ out) {
+    __shared__ float s[8][33];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
+    const int r0 = blockIdx.y * rows_per, r1 = min(R, r0 + rows_per);
     float acc = 0.f;
-    for (int r = 0; r < R; ++r) acc += y[(size_t)r * C + c];
-    out[c] = accumulate ? out[c] + acc : acc;
+    if (c < C)
+        for (int r = r0 + ty; r < r1; r += 8) acc += y[(size_t)r * C + c];
+    s[ty][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (ty == 0 && c < C) {
+        float t = 0.f;
+        for (int i = 0; i < 8; ++i) t += s[i][threadIdx.x];
+        atomicAdd(out + c, t);
+    }
 }
 
 // ---------------------------------------------------------------- group norm
@@ -393,6 +412,15 @@ __global__ void k_gather(const float *__restrict__ in, const int *__restrict__ i
     }
 }
 
+__global__ void k_gather_rows(const float *__restrict__ in, const int *__restrict__ rows, long long R, int C,
+                              float *__restrict__ out) {
+    const long long total = R * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / C;
+        out[i] = in[(long long)rows[r] * C + (i - r * C)];
+    }
+}
+
 // sinusoidal embedding of integer steps: out[n][2i] = sin(k w_i), out[n][2i+1] = cos(k w_i),
 // w_i = 10000^(-i / (dim/2))
 __global__ void k_sinusoid(const int *__restrict__ k, int N, int dim, float *__restrict__ out) {
@@ -485,14 +513,32 @@ static unsigned grid_for(long long n, int block = 256) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
+template <bool SPLIT>
+static void gemm_go(int ta, int tb, dim3 grid, int M, int N, int K, float alpha, const float *A, int lda,
+                    const float *B, int ldb, float beta, float *C, int ldc, const float *bias, int kchunk,
+                    cudaStream_t st) {
+    if (!ta && !tb) k_gemm_f32<false, false, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else if (!ta && tb) k_gemm_f32<false, true, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else if (ta && !tb) k_gemm_f32<true, false, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else k_gemm_f32<true, true, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+}
+
 int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
                 float beta, float *C, int ldc, const float *bias, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
-    dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
-    if (!ta && !tb) k_gemm_f32<false, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
-    else if (!ta && tb) k_gemm_f32<false, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
-    else if (ta && !tb) k_gemm_f32<true, false><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
-    else k_gemm_f32<true, true><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias);
+    const int tiles = ((N + GB - 1) / GB) * ((M + GB - 1) / GB);
+    // few output tiles and a long K: split K over blocks when the result is accumulated
+    if (beta == 1.0f && !bias && tiles < 2 * 152 && K >= 1024) {
+        int splits = (2 * 152 * 2 + tiles - 1) / tiles;
+        splits = min(splits, K / 256);
+        const int kchunk = ((K + splits - 1) / splits + GK - 1) / GK * GK;
+        splits = (K + kchunk - 1) / kchunk;
+        dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB, splits);
+        gemm_go<true>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk, st);
+    } else {
+        dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
+        gemm_go<false>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, K, st);
+    }
     return (int)cudaGetLastError();
 }
 
@@ -518,7 +564,14 @@ int nn_col2im1d(const float *cols, int N, int L, int C, int k, int s, int p, int
 }
 
 int nn_colsum(const float *y, int R, int C, float *out, int accumulate, cudaStream_t st) {
-    k_colsum<<<(C + 127) / 128, 128, 0, st>>>(y, R, C, out, accumulate);
+    if (!accumulate) {
+        cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float) * C, st);
+        if (e != cudaSuccess) return (int)e;
+    }
+    if (R == 0) return cudaSuccess;
+    const int rows_per = 256;
+    dim3 grid((C + 31) / 32, (R + rows_per - 1) / rows_per);
+    k_colsum<<<grid, 256, 0, st>>>(y, R, C, rows_per, out);
     return (int)cudaGetLastError();
 }
 
@@ -565,6 +618,11 @@ int nn_upsample2(const float *x, int N, int L, int C, float *y, int backward, cu
 
 int nn_gather(const float *in, const int *idx, float *out, long long n, long long per, int scatter, cudaStream_t st) {
     k_gather<<<grid_for(n * per), 256, 0, st>>>(in, idx, out, n, per, scatter);
+    return (int)cudaGetLastError();
+}
+
+int nn_gather_rows(const float *in, const int *rows, long long R, int C, float *out, cudaStream_t st) {
+    k_gather_rows<<<grid_for(R * C), 256, 0, st>>>(in, rows, R, C, out);
     return (int)cudaGetLastError();
 }
 

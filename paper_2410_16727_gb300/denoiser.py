@@ -7,11 +7,12 @@ backward pass needs (a tape of closures, replayed in reverse), and owns the
 parameter, gradient and Adam buffers (device tensors).  Training runs in FP32;
 `infer` runs every GEMM on the tensor cores in BF16 (FP32 accumulation).
 
-Inputs of one sample: the noisy normalised trajectory x_k [T][D], the
-diffusion step k, the normalised start configuration [D], the goal pose [7]
-and the scene's 32^3 occupancy grid.  Output: the predicted noise [T][D]
-(Eq. 1).  Joint values are normalised to [-1, 1] by the mechanical limits
-(App. A.4).
+Inputs of one sample: the noisy trajectory x_k [T][D], the diffusion step k,
+the normalised start and goal configurations [D], the goal pose [7] and the
+scene's 32^3 occupancy grid.  Output: the predicted noise [T][D] (Eq. 1).
+Joint values are normalised to [-1, 1] by the mechanical limits (App. A.4);
+the diffused quantity is the deviation of the normalised trajectory from the
+straight start-goal joint path (see learned.py).
 """
 from __future__ import annotations
 
@@ -314,16 +315,17 @@ class Denoiser:
             r = x
         return self.add(h, r, tape)
 
-    def condition(self, k, qs, goal, occ, tape):
-        """cond = [time MLP (sinusoid(k)), problem MLP (q_start, goal), occupancy
-        encoder]; returns Mish(cond) [N][cond_dim], the input of every FiLM layer."""
+    def condition(self, k, qs, qg, goal, occ, tape):
+        """cond = [time MLP (sinusoid(k)), problem MLP (q_start, q_goal, goal pose),
+        occupancy encoder]; returns Mish(cond) [N][cond_dim], the input of every
+        FiLM layer."""
         s = self.spec
         N = qs.shape[0]
         te = torch.empty((N, s.t_sin), dtype=torch.float32, device=self.dev)
         _nn("sinusoid", k, N, s.t_sin, te)
         t1 = self.mish(self.linear(te, "t.l1", tape), tape)
         t2 = self.linear(t1, "t.l2", tape)
-        pin = self.concat([qs, goal], N, tape)
+        pin = self.concat([qs, qg, goal], N, tape)
         p1 = self.mish(self.linear(pin, "p.l1", tape), tape)
         p2 = self.linear(p1, "p.l2", tape)
         o0 = self.gather(occ, self.map1, N, s.occ_n ** 3, tape)                      # [N][8^3][4^3]
@@ -362,10 +364,10 @@ class Denoiser:
         out, _ = self.conv(h, N, T, "fin.o", 1, 1, 0, tape)
         return out
 
-    def forward(self, xk, k, qs, goal, occ, tape: Optional[Tape] = None):
+    def forward(self, xk, k, qs, qg, goal, occ, tape: Optional[Tape] = None):
         """Predicted noise [N][T][D] (FP32)."""
         N = xk.shape[0]
-        mc = self.condition(k, qs, goal, occ, tape)
+        mc = self.condition(k, qs, qg, goal, occ, tape)
         return self.unet(xk, N, mc, tape)
 
     @staticmethod
@@ -375,7 +377,7 @@ class Denoiser:
             fn()
 
     # ------------------------------------------------------------------ training
-    def loss_and_grad(self, x0, qs, goal, occ, k, eps, weights=None):
+    def loss_and_grad(self, x0, qs, qg, goal, occ, k, eps, weights=None):
         """Eq. 1 (optionally weighted per sample as in Eq. 2): noise the clean
         normalised trajectories x0 to step k with eps, predict the noise,
         accumulate parameter gradients of the mean squared error into self.grads.
@@ -385,7 +387,7 @@ class Denoiser:
         xk = torch.empty_like(x0)
         _nn("ddpm_noise", x0, eps, k, self.abar, N, per, xk)
         tape = Tape()
-        pred = self.forward(xk, k, qs, goal, occ, tape)
+        pred = self.forward(xk, k, qs, qg, goal, occ, tape)
         dpred = torch.empty_like(pred)
         blocks = 64
         part = torch.empty(blocks, dtype=torch.float32, device=self.dev)
@@ -400,24 +402,37 @@ class Denoiser:
         self._bf16.clear()
 
     # ------------------------------------------------------------------ inference
-    def infer(self, xk, k, qs, goal, occ):
+    def infer(self, xk, k, qs, qg, goal, occ):
         """Predicted noise with every GEMM on the BF16 tensor cores."""
         self.bf16_mode = True
         try:
-            return self.forward(xk, k, qs, goal, occ, None)
+            return self.forward(xk, k, qs, qg, goal, occ, None)
         finally:
             self.bf16_mode = False
 
-    def ddim_sample(self, qs, goal, occ, noise, steps: int = 10, bf16: bool = True, clip: float = 1.0):
+    def ddim_sample(self, qs, qg, goal, occ, noise, steps: int = 10, bf16: bool = True, clip: float = 2.0,
+                    sample_problem: Optional[torch.Tensor] = None):
         """DDIM (deterministic) from x_K = noise over `steps` evenly spaced steps
-        of the K-step schedule; returns normalised trajectories [N][T][D]."""
+        of the K-step schedule; returns normalised trajectories [N][T][D].
+        qs, qg, goal, occ are per problem; sample_problem [N] (int32) maps each
+        sample to its problem (default: sample n -> problem n).  The condition is
+        computed once per problem and step and broadcast to the samples."""
         K = self.spec.K
         ks = np.linspace(K - 1, 0, steps).round().astype(int)
         x = noise.clone()
         N = x.shape[0]
+        P = qs.shape[0]
+        rows = sample_problem if sample_problem is not None else torch.arange(N, dtype=torch.int32, device=self.dev)
         for i, kk in enumerate(ks):
-            kt = torch.full((N,), int(kk), dtype=torch.int32, device=self.dev)
-            eps = self.infer(x, kt, qs, goal, occ) if bf16 else self.forward(x, kt, qs, goal, occ, None)
+            kp = torch.full((P,), int(kk), dtype=torch.int32, device=self.dev)
+            self.bf16_mode = bf16
+            try:
+                mc_p = self.condition(kp, qs, qg, goal, occ, None)
+                mc = torch.empty((N, mc_p.shape[1]), dtype=torch.float32, device=self.dev)
+                _nn("gather_rows", mc_p, rows, N, mc_p.shape[1], mc)
+                eps = self.unet(x, N, mc, None)
+            finally:
+                self.bf16_mode = False
             ab_k = float(self.abar_host[kk])
             ab_prev = float(self.abar_host[ks[i + 1]]) if i + 1 < len(ks) else 1.0
             out = torch.empty_like(x)

@@ -1,0 +1,296 @@
+"""Learned seed proposal (the paper's DiffusionSeeder idea on top of the
+plain optimiser): generate problems on shelf scenes, solve them with the plain
+random-seed optimiser, train the conditional denoiser on the solutions
+(Eq. 1, optionally weighted as in Eq. 2), then propose seeds by DDIM and
+refine them with a few optimiser iterations.  The plain optimiser stays both
+the fallback and the judge (success is tested by the same kernels).
+
+Data handling (batch assembly, repetition of per-problem inputs) uses PyTorch
+indexing on the device; every numeric step of the method -- the optimiser,
+the ESDF and occupancy, normalisation, the network, DDIM -- runs in libdseed.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+import time
+from typing import Optional
+
+import numpy as np
+import torch
+
+from . import api
+from . import binding as B
+from . import denoiser as DN
+from . import inputs as I
+from . import netspec as NS
+
+OCC_GRID = I.Grid((-0.30, -0.64, -0.14), 0.04, (32, 32, 32))    # same box as the shelf ESDF grid
+RES_SCALE = 4.0    # diffused quantity: RES_SCALE * (normalised trajectory - straight joint path)
+
+
+def _nn(name, *a):
+    B.nn(name, *a)
+
+
+@dataclasses.dataclass
+class ProblemSet:
+    """Problems on shelf scenes (device tensors)."""
+    cuboids: list
+    grids: list
+    scene_of_problem: torch.Tensor    # [P] int32
+    q_start: torch.Tensor             # [P][7]
+    q_goal: torch.Tensor              # [P][7]
+    goal: torch.Tensor                # [P][7]
+    occ: torch.Tensor                 # [n_scenes][32^3]
+    table: B.SceneTable = None        # the scenes' ESDFs on the device
+
+
+def make_problems(planner: api.Planner, n_scenes: int, per_scene: int, seed: int) -> ProblemSet:
+    spec = I.WORKLOADS["batched"]
+    spec = I.WorkloadSpec("learned", 40 + seed, n_scenes, n_scenes * per_scene, 1, 32, 100, "shelf", spec.grid)
+    cub, grids = I.make_scenes(spec)
+    planner.set_scenes(cub, grids)
+    cf, pf = api.device_workload_fns(planner)
+    wl = I.build_workload(spec, cub, grids, cf, pf, S=1)
+    occ = occupancy(planner, cub)
+    dev = planner.device
+    return ProblemSet(cub, grids, torch.as_tensor(wl.scene_of_problem).to(dev), torch.as_tensor(wl.q_start).to(dev),
+                      torch.as_tensor(wl.q_goal).to(dev), torch.as_tensor(wl.goal).to(dev), occ, planner.table)
+
+
+def occupancy(planner: api.Planner, cuboids) -> torch.Tensor:
+    """32^3 occupancy of each scene over the shelf workspace: the ESDF at 4 cm
+    voxels thresholded at 0 (1 inside a cuboid)."""
+    dev = planner.device
+    cts = [torch.as_tensor(c).to(dev).reshape(-1, 6) for c in cuboids]
+    esdf = B.scene_build_esdf_batch(cts, [OCC_GRID] * len(cts))
+    phi = torch.stack(esdf).reshape(len(cts), -1).contiguous()
+    occ = torch.empty_like(phi)
+    _nn("clamp_affine", phi, -1e6, 0.0, 0.0, 1.0, occ, phi.numel())
+    return occ
+
+
+def _limits_affine(robot: I.Robot, dev, inverse: bool) -> torch.Tensor:
+    """FiLM vector [1][14] (scale, shift) mapping joints to [-1, 1] by the
+    mechanical limits (App. A.4), or back."""
+    lo = robot.limits[:, 0].astype(np.float64)
+    hi = robot.limits[:, 1].astype(np.float64)
+    if not inverse:
+        sc, sh = 2.0 / (hi - lo), -2.0 * lo / (hi - lo) - 1.0
+    else:
+        sc, sh = (hi - lo) / 2.0, lo + (hi - lo) / 2.0
+    return torch.tensor(np.concatenate([sc, sh])[None], dtype=torch.float32, device=dev)
+
+
+def normalise(robot, q: torch.Tensor, inverse: bool = False) -> torch.Tensor:
+    rows = q.numel() // 7
+    out = torch.empty_like(q)
+    _nn("film", q.contiguous(), _limits_affine(robot, q.device, inverse), 1, rows, 7, out, None, None, None, 0)
+    return out
+
+
+def linear_path(qs_n: torch.Tensor, qg_n: torch.Tensor, T: int) -> torch.Tensor:
+    """Straight start-goal joint path [N][T][7] (waypoint t at fraction t/T,
+    t = 1..T, the start itself excluded like the optimiser's waypoints), from
+    normalised start and goal configurations: one GEMM of [q_s, q_g] against
+    the constant interpolation matrix [14][T*7]."""
+    N, D = qs_n.shape
+    tau = np.arange(1, T + 1, dtype=np.float64) / T
+    W = np.zeros((2 * D, T * D), np.float32)
+    for t in range(T):
+        for d in range(D):
+            W[d, t * D + d] = 1.0 - tau[t]
+            W[D + d, t * D + d] = tau[t]
+    W = torch.from_numpy(W).to(qs_n.device)
+    A = torch.cat([qs_n, qg_n], 1).contiguous()
+    out = torch.empty((N, T, D), dtype=torch.float32, device=qs_n.device)
+    _nn("gemm_f32", 0, 0, N, T * D, 2 * D, 1.0, A, 2 * D, W, T * D, 0.0, out, T * D, None)
+    return out
+
+
+def to_residual(x_n: torch.Tensor, lin: torch.Tensor) -> torch.Tensor:
+    out = torch.empty_like(x_n)
+    _nn("axpby", RES_SCALE, x_n.contiguous(), -RES_SCALE, lin.contiguous(), out, x_n.numel())
+    return out
+
+
+def from_residual(r: torch.Tensor, lin: torch.Tensor) -> torch.Tensor:
+    out = torch.empty_like(r)
+    _nn("axpby", 1.0, lin.contiguous(), 1.0 / RES_SCALE, r.contiguous(), out, r.numel())
+    return out
+
+
+def random_seeds(ps: ProblemSet, robot: I.Robot, S: int, T: int, seed: int, p0: int = 0,
+                 p1: Optional[int] = None) -> np.ndarray:
+    """The plain method's seeds (linear start-goal interpolation plus noise,
+    clipped to the limits) of problems p0..p1-1: [P][S][T][7]."""
+    p1 = ps.q_start.shape[0] if p1 is None else p1
+    qs, qg = ps.q_start[p0:p1].cpu().numpy(), ps.q_goal[p0:p1].cpu().numpy()
+    return np.stack([I.make_seeds(I._rng(77 + seed, p0 + i, 3), qs[i], qg[i], S, T, robot.limits)
+                     for i in range(p1 - p0)])
+
+
+def solve(planner: api.Planner, ps: ProblemSet, seeds, iters: int, chunk: int = 256):
+    """Plan every problem with the given seeds [P][S][T][7] for `iters`
+    iterations; returns the output dict (device tensors, concatenated)."""
+    P, S, T = seeds.shape[0], seeds.shape[1], seeds.shape[2]
+    opt = I.OptParams(iters=iters)
+    outs = []
+    seeds_t = torch.as_tensor(seeds).to(planner.device) if not isinstance(seeds, torch.Tensor) else seeds
+    for p0 in range(0, P, chunk):
+        p1 = min(P, p0 + chunk)
+        batch = api.Batch(ps.q_start[p0:p1], ps.goal[p0:p1], ps.scene_of_problem[p0:p1], ps.table, S, T,
+                          planner.cost, opt, planner.device)
+        outs.append({k: v.clone() for k, v in planner.plan(batch, seeds_t[p0:p1].contiguous()).items()})
+    return {k: torch.cat([o[k] for o in outs]) for k in outs[0]}
+
+
+@dataclasses.dataclass
+class Dataset:
+    x0: torch.Tensor       # [M][T][7] scaled residuals of the normalised solutions from the straight path
+    qs: torch.Tensor       # [M][7] normalised starts
+    qg: torch.Tensor       # [M][7] normalised goal configurations
+    goal: torch.Tensor     # [M][7]
+    scene: torch.Tensor    # [M] int64 index into occ
+    occ: torch.Tensor      # [n_scenes][32^3]
+    weight: torch.Tensor   # [M] 1 + alpha * 1(non-linear solution)
+
+
+def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int = 64, iters: int = 100,
+                  alpha: float = 4.0, nonlinear_rad: float = 0.3, seed: int = 0, chunk: int = 256) -> Dataset:
+    """Solve every problem with S random seeds; keep the best successful
+    trajectory of each solved problem.  A solution that leaves the straight
+    start-goal joint line by more than `nonlinear_rad` counts as non-linear
+    and gets weight 1 + alpha (the paper up-weights solutions a linear seed
+    does not reach, Eq. 2)."""
+    T = 32
+    P = ps.q_start.shape[0]
+    opt = I.OptParams(iters=iters)
+    keeps, trajs = [], []
+    for p0 in range(0, P, chunk):
+        p1 = min(P, p0 + chunk)
+        seeds = torch.as_tensor(random_seeds(ps, robot, S, T, seed, p0, p1)).to(planner.device)
+        batch = api.Batch(ps.q_start[p0:p1], ps.goal[p0:p1], ps.scene_of_problem[p0:p1], ps.table, S, T,
+                          planner.cost, opt, planner.device)
+        out = planner.plan(batch, seeds)
+        best = out["best"].long()
+        keep = torch.nonzero(best >= 0).squeeze(1)
+        keeps.append(keep + p0)
+        trajs.append(out["traj"][keep, best[keep]].clone())
+    keep = torch.cat(keeps)
+    traj = torch.cat(trajs)                                        # [M][T][7]
+    qs, qg = ps.q_start[keep], ps.q_goal[keep]
+    tt = torch.arange(1, T + 1, device=planner.device, dtype=torch.float32)[None, :, None] / T
+    lin = qs[:, None, :] + tt * (qg - qs)[:, None, :]
+    dev = (traj - lin).abs().amax(dim=(1, 2))
+    weight = 1.0 + alpha * (dev > nonlinear_rad).float()
+    qs_n, qg_n = normalise(robot, qs.contiguous()), normalise(robot, qg.contiguous())
+    x0 = to_residual(normalise(robot, traj.contiguous()), linear_path(qs_n, qg_n, T))
+    return Dataset(x0, qs_n, qg_n, ps.goal[keep].contiguous(), ps.scene_of_problem[keep].long(), ps.occ,
+                   weight.contiguous())
+
+
+class GraphStep:
+    """One training step's kernels (noising, forward, loss, backward) captured
+    once in a CUDA graph over static input buffers, then replayed: the launch
+    sequence of a fixed batch size never changes, so replaying it removes the
+    host cost of issuing ~400 launches per step."""
+
+    def __init__(self, net: DN.Denoiser, batch: int, weighted: bool):
+        s, dev = net.spec, net.dev
+        self.net = net
+        self.x0 = torch.zeros((batch, s.T, s.D), device=dev)
+        self.qs = torch.zeros((batch, s.D), device=dev)
+        self.qg = torch.zeros((batch, s.D), device=dev)
+        self.goal = torch.zeros((batch, 7), device=dev)
+        self.goal[:, 3] = 1.0
+        self.occ = torch.zeros((batch, s.occ_n ** 3), device=dev)
+        self.k = torch.zeros((batch,), dtype=torch.int32, device=dev)
+        self.eps = torch.zeros((batch, s.T, s.D), device=dev)
+        self.w = torch.ones((batch,), device=dev) if weighted else None
+        args = (self.x0, self.qs, self.qg, self.goal, self.occ, self.k, self.eps, self.w)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                  # warm-up outside the capture
+            net.loss_and_grad(*args)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        net.grads.zero_()
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.loss = net.loss_and_grad(*args)
+        torch.cuda.synchronize()
+        net.grads.zero_()
+
+    def run(self):
+        self.graph.replay()
+        return self.loss
+
+
+def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: float = 3e-4, seed: int = 0,
+          log_every: int = 0, weighted: bool = True, graph: bool = True):
+    """DDPM training (Eq. 1 / Eq. 2 weights) with Adam and a cosine learning
+    rate; returns the loss curve [(step, loss)]."""
+    g = torch.Generator(device=data.x0.device)
+    g.manual_seed(seed)
+    M = data.x0.shape[0]
+    losses = []
+    gs = GraphStep(net, batch, weighted) if graph else None
+    for it in range(steps):
+        idx = torch.randint(0, M, (batch,), device=data.x0.device, generator=g)
+        k = torch.randint(0, net.spec.K, (batch,), device=data.x0.device, generator=g, dtype=torch.int32)
+        eps = torch.randn((batch, net.spec.T, net.spec.D), device=data.x0.device, generator=g)
+        if gs is not None:
+            gs.x0.copy_(data.x0[idx])
+            gs.qs.copy_(data.qs[idx])
+            gs.qg.copy_(data.qg[idx])
+            gs.goal.copy_(data.goal[idx])
+            gs.occ.copy_(data.occ[data.scene[idx]])
+            gs.k.copy_(k)
+            gs.eps.copy_(eps)
+            if weighted:
+                gs.w.copy_(data.weight[idx])
+            loss = gs.run()
+        else:
+            loss = net.loss_and_grad(data.x0[idx].contiguous(), data.qs[idx].contiguous(),
+                                     data.qg[idx].contiguous(), data.goal[idx].contiguous(),
+                                     data.occ[data.scene[idx]].contiguous(), k, eps,
+                                     data.weight[idx].contiguous() if weighted else None)
+        cos = 0.5 * (1 + math.cos(math.pi * it / max(steps, 1)))
+        net.adam_step(lr=lr * (0.1 + 0.9 * cos))
+        if log_every and (it % log_every == 0 or it == steps - 1):
+            losses.append((it, float(loss)))
+    return losses
+
+
+def propose(net: DN.Denoiser, robot: I.Robot, ps: ProblemSet, S: int, steps: int = 10, seed: int = 0,
+            bf16: bool = True) -> torch.Tensor:
+    """DDIM proposals: S seed trajectories per problem, [P][S][T][7] in joint
+    space.  DDIM generates the scaled residual from the straight start-goal
+    path, which is added back; the result is clipped to the joint limits like
+    the random seeds, then un-normalised."""
+    P = ps.q_start.shape[0]
+    dev = ps.q_start.device
+    g = torch.Generator(device=dev)
+    g.manual_seed(1000 + seed)
+    noise = torch.randn((P * S, net.spec.T, net.spec.D), device=dev, generator=g)
+    rows = torch.arange(P, device=dev, dtype=torch.int32).repeat_interleave(S)
+    qs = normalise(robot, ps.q_start.contiguous())
+    qg = normalise(robot, ps.q_goal.contiguous())
+    occ = ps.occ[ps.scene_of_problem.long()].contiguous()
+    r = net.ddim_sample(qs, qg, ps.goal.contiguous(), occ, noise, steps=steps, bf16=bf16, sample_problem=rows)
+    lin = linear_path(qs, qg, net.spec.T)[rows.long()]
+    x = from_residual(r, lin)
+    _nn("clamp_affine", x, 1.0, 0.0, -1.0, 1.0, x, x.numel())
+    return normalise(robot, x, inverse=True).view(P, S, net.spec.T, net.spec.D)
+
+
+def evaluate(planner: api.Planner, ps: ProblemSet, seeds, iters: int) -> dict:
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = solve(planner, ps, seeds, iters)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return dict(problems_solved=float((out["best"] >= 0).float().mean()),
+                seed_success=float(out["success"].float().mean()), plan_s=dt)

@@ -6,9 +6,10 @@ way the robot description is; neither side's arithmetic lives here.
 The network follows the paper's Sec. 4.2 ("Model Architecture"): a 3-level 1-D
 temporal-convolution U-Net of conditional residual blocks (conv - group norm -
 Mish, FiLM from the condition, conv - group norm - Mish, residual), a time-step
-MLP, a problem encoding of the start configuration and goal pose, and an
-observation encoding -- here a small 3-D convolutional encoder of a 32^3
-occupancy grid of the scene (in place of the paper's ViT on depth images).
+MLP, a problem encoding of the start and goal configurations and the goal
+pose, and an observation encoding -- here a small 3-D convolutional encoder of
+a 32^3 occupancy grid of the scene (in place of the paper's ViT on depth
+images).
 Channel widths (64, 128, 256) instead of the paper's (256, 512, 1024) give
 about 4M parameters.
 
@@ -68,7 +69,7 @@ def param_shapes(spec: NetSpec) -> "OrderedDict[str, tuple]":
     s["t.l1.b"] = (spec.t_dim,)
     s["t.l2.w"] = (spec.t_dim, spec.t_dim)
     s["t.l2.b"] = (spec.t_dim,)
-    s["p.l1.w"] = (spec.p_dim, spec.D + 7)      # start configuration + goal pose
+    s["p.l1.w"] = (spec.p_dim, 2 * spec.D + 7)  # start and goal configurations + goal pose
     s["p.l1.b"] = (spec.p_dim,)
     s["p.l2.w"] = (spec.p_dim, spec.p_dim)
     s["p.l2.b"] = (spec.p_dim,)

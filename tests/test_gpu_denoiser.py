@@ -16,6 +16,7 @@ def _inputs(spec, N, seed=0):
     rng = np.random.default_rng(seed)
     return dict(x0=rng.uniform(-1, 1, (N, spec.T, spec.D)).astype(np.float32),
                 qs=rng.uniform(-1, 1, (N, spec.D)).astype(np.float32),
+                qg=rng.uniform(-1, 1, (N, spec.D)).astype(np.float32),
                 goal=rng.normal(size=(N, 7)).astype(np.float32),
                 occ=(rng.random((N, spec.occ_n ** 3)) < 0.15).astype(np.float32),
                 k=rng.integers(0, spec.K, N).astype(np.int32),
@@ -48,8 +49,9 @@ def net():
 def test_forward_matches_oracle(gpu_lib, net):
     inp = _inputs(net.spec, 3)
     xk = inp["x0"]
-    got = net.forward(_cuda(xk), _cuda(inp["k"]), _cuda(inp["qs"]), _cuda(inp["goal"]), _cuda(inp["occ"]))
-    want = DO.predict(net.spec, net.params.cpu().numpy(), xk, inp["k"], inp["qs"], inp["goal"], inp["occ"])
+    got = net.forward(_cuda(xk), _cuda(inp["k"]), _cuda(inp["qs"]), _cuda(inp["qg"]), _cuda(inp["goal"]),
+                      _cuda(inp["occ"]))
+    want = DO.predict(net.spec, net.params.cpu().numpy(), xk, inp["k"], inp["qs"], inp["qg"], inp["goal"], inp["occ"])
     assert _rel(got.cpu().numpy(), want) <= 1e-4
 
 
@@ -57,10 +59,10 @@ def test_loss_and_gradients_match_oracle(gpu_lib, net):
     inp = _inputs(net.spec, 4, seed=1)
     w = np.array([1.0, 5.0, 1.0, 5.0], np.float32)        # Eq. 2 style per-sample weights
     net.grads.zero_()
-    loss = net.loss_and_grad(_cuda(inp["x0"]), _cuda(inp["qs"]), _cuda(inp["goal"]), _cuda(inp["occ"]),
-                             _cuda(inp["k"]), _cuda(inp["eps"]), _cuda(w))
-    ref_loss, ref_g = DO.loss_and_grads(net.spec, net.params.cpu().numpy(), inp["x0"], inp["qs"], inp["goal"],
-                                        inp["occ"], inp["k"], inp["eps"], net.abar.cpu().double().numpy(), w)
+    loss = net.loss_and_grad(_cuda(inp["x0"]), _cuda(inp["qs"]), _cuda(inp["qg"]), _cuda(inp["goal"]),
+                             _cuda(inp["occ"]), _cuda(inp["k"]), _cuda(inp["eps"]), _cuda(w))
+    ref_loss, ref_g = DO.loss_and_grads(net.spec, net.params.cpu().numpy(), inp["x0"], inp["qs"], inp["qg"],
+                                        inp["goal"], inp["occ"], inp["k"], inp["eps"], net.abar.cpu().double().numpy(), w)
     assert abs(float(loss) - ref_loss) <= 1e-4 * abs(ref_loss)
     g = net.grads.cpu().numpy()
     assert _rel(g, ref_g) <= 1e-3
@@ -75,7 +77,7 @@ def test_loss_and_gradients_match_oracle(gpu_lib, net):
 
 def test_bf16_inference_close_to_fp32(gpu_lib, net):
     inp = _inputs(net.spec, 64, seed=2)
-    args = [_cuda(inp[k]) for k in ("x0", "k", "qs", "goal", "occ")]
+    args = [_cuda(inp[k]) for k in ("x0", "k", "qs", "qg", "goal", "occ")]
     f32 = net.forward(*args).cpu().numpy()
     b16 = net.infer(*args).cpu().numpy()
     assert _rel(b16, f32) <= 3e-2
@@ -92,6 +94,24 @@ def test_gemm_kernels_against_float64():
         B.nn("gemm_f32", ta, tb, M, N, K, 1.5, _cuda(A), A.shape[1], _cuda(Bm), Bm.shape[1], 0.5, C, N, _cuda(bias))
         want = 1.5 * ((A.T if ta else A).astype(np.float64) @ (Bm.T if tb else Bm)) + 0.5 * C0 + bias
         assert _rel(C.cpu().numpy(), want) <= 1e-5
+    # accumulate into C with no bias and a long K: the split-K kernel
+    for (M, N, K, ta, tb) in [(64, 96, 4096, 1, 0), (33, 70, 2999, 0, 0), (128, 128, 1024, 1, 0)]:
+        A = rng.normal(size=(K, M) if ta else (M, K)).astype(np.float32)
+        Bm = rng.normal(size=(N, K) if tb else (K, N)).astype(np.float32)
+        C0 = rng.normal(size=(M, N)).astype(np.float32)
+        C = _cuda(C0.copy())
+        B.nn("gemm_f32", ta, tb, M, N, K, 0.75, _cuda(A), A.shape[1], _cuda(Bm), Bm.shape[1], 1.0, C, N, None)
+        want = 0.75 * ((A.T if ta else A).astype(np.float64) @ (Bm.T if tb else Bm)) + C0
+        assert _rel(C.cpu().numpy(), want) <= 1e-5
+    for (R, Cn) in [(1, 5), (1000, 70), (4099, 256)]:
+        y = rng.normal(size=(R, Cn)).astype(np.float32)
+        base = rng.normal(size=Cn).astype(np.float32)
+        out = _cuda(base.copy())
+        B.nn("colsum", _cuda(y), R, Cn, out, 0)
+        assert _rel(out.cpu().numpy(), y.astype(np.float64).sum(0)) <= 1e-5
+        out = _cuda(base.copy())
+        B.nn("colsum", _cuda(y), R, Cn, out, 1)
+        assert _rel(out.cpu().numpy(), y.astype(np.float64).sum(0) + base) <= 1e-5
     for (M, N, K) in [(300, 70, 48), (17, 129, 16), (1024, 256, 1280)]:
         A = rng.normal(size=(M, K)).astype(np.float32)
         W = rng.normal(size=(N, K)).astype(np.float32)
@@ -124,7 +144,7 @@ def test_training_reduces_the_loss(gpu_lib):
     """A few hundred Adam steps on a fixed batch: the kernels' gradients descend."""
     d = DN.Denoiser(NS.NetSpec(), seed=0)
     inp = _inputs(d.spec, 32, seed=6)
-    args = [_cuda(inp[k]) for k in ("x0", "qs", "goal", "occ", "k", "eps")]
+    args = [_cuda(inp[k]) for k in ("x0", "qs", "qg", "goal", "occ", "k", "eps")]
     losses = []
     for it in range(150):
         losses.append(float(d.loss_and_grad(*args)))

@@ -16,6 +16,7 @@ TINY = NS.NetSpec(T=8, D=3, chans=(4, 4, 8), kernel=3, groups=2, t_sin=4, t_dim=
 def _inputs(spec, N, seed=0):
     rng = np.random.default_rng(seed)
     return dict(x0=rng.uniform(-1, 1, (N, spec.T, spec.D)), qs=rng.uniform(-1, 1, (N, spec.D)),
+                qg=rng.uniform(-1, 1, (N, spec.D)),
                 goal=rng.normal(size=(N, 7)), occ=(rng.random((N, spec.occ_n ** 3)) < 0.2).astype(np.float64),
                 k=rng.integers(0, spec.K, N), eps=rng.normal(size=(N, spec.T, spec.D)))
 
@@ -32,13 +33,13 @@ def test_gradcheck_whole_network():
     def loss(f):
         P = DO.unpack(TINY, f)
         xk = DO.ddpm_noise(t(inp["x0"]), t(inp["eps"]), k, abar)
-        pred = DO.forward(TINY, P, xk, k, t(inp["qs"]), t(inp["goal"]), t(inp["occ"]))
+        pred = DO.forward(TINY, P, xk, k, t(inp["qs"]), t(inp["qg"]), t(inp["goal"]), t(inp["occ"]))
         return ((pred - t(inp["eps"])) ** 2).mean()
 
     assert torch.autograd.gradcheck(loss, (flat,), eps=1e-6, atol=1e-7, rtol=1e-5, fast_mode=True)
     # loss_and_grads returns the same gradient
-    l, g = DO.loss_and_grads(TINY, flat.detach().numpy(), inp["x0"], inp["qs"], inp["goal"], inp["occ"], inp["k"],
-                             inp["eps"], abar)
+    l, g = DO.loss_and_grads(TINY, flat.detach().numpy(), inp["x0"], inp["qs"], inp["qg"], inp["goal"], inp["occ"],
+                             inp["k"], inp["eps"], abar)
     flat.grad = None
     ref = loss(flat)
     ref.backward()
