@@ -468,6 +468,60 @@ int dseed_nn_clamp_affine(const float *x_dev, float a, float b, float lo, float 
 /* FP32 -> BF16 (round to nearest even). */
 int dseed_nn_to_bf16(const float *x_dev, void *y_dev, long long n, cudaStream_t stream);
 
+/* Inference convolution on the tensor cores (tcgen05 MMA with BF16 operands
+ * staged by TMA and FP32 accumulation in tensor memory), with the rest of the
+ * layer fused into its epilogue (Sec. 4.2: conditional residual blocks of
+ * conv - group norm - Mish, FiLM from the condition, residual add).
+ *
+ * out[n][lo][o] = bias[o] + sum_{j < taps} sum_c W[o][j][c] A[n][lo - pad + j][c]
+ * with A = the channel concatenation of a0 [n_samples][L][c0] and a1
+ * [n_samples][L][c1] (BF16, channels-last; rows outside [0, L) read as zero),
+ * W BF16 [cout_pad][taps][c0 + c1] (rows >= cout zero).  A plain GEMM
+ * out[m] = W a[m] is L = 1, taps = 1, pad = 0.
+ *
+ * epilogue 0: out FP32 [n_samples * L][out_ld], columns < cout.
+ * epilogue 1: out BF16 [..][out_ld], columns < cout.
+ * epilogue 2: y = Mish(GroupNorm(out)) over groups of cout / 8 channels and
+ *   rows_per_sample consecutive rows (affine gamma, beta; biased variance, eps
+ *   gn_eps); then y = y * film[s][o] + film[s][cout + o] when film_dev is given
+ *   (s = sample_problem[row / rows_per_sample], or row / rows_per_sample when
+ *   sample_problem_dev is NULL); then y += res[row][o] (BF16 [..][cout]) when
+ *   res_dev is given; out BF16 [..][out_ld].  Needs cout = cout_pad.
+ *
+ * Limits (EINVAL otherwise): c0, c1 multiples of 64 (c1 may be 0); L a power of
+ * two <= 128; 1 <= taps <= 8, 0 <= pad < taps; cout_pad in {16, 64, 128, 256}
+ * (16 only for epilogues 0/1), 1 <= cout <= cout_pad; rows_per_sample a power
+ * of two <= 32 dividing n_samples * L (epilogue 2); out_ld >= cout (a multiple
+ * of 8 for BF16 output); every pointer 16-byte aligned.  err_dev (optional, int)
+ * is set non-zero if a pipeline wait inside the kernel gave up (2 s); the
+ * output is then undefined.  Requires a GPU of compute capability 10.x. */
+typedef struct {
+    const void *a0_dev;
+    int c0;
+    const void *a1_dev;
+    int c1;
+    int n_samples, L, taps, pad;
+    const void *w_dev;
+    int cout, cout_pad;
+    const float *bias_dev;
+    int epilogue;
+    int rows_per_sample;
+    float gn_eps;
+    const float *gamma_dev, *beta_dev;
+    const float *film_dev;
+    const int *sample_problem_dev;
+    const void *res_dev;
+    void *out_dev;
+    int out_ld;
+    int *err_dev;
+} DseedConvTc;
+int dseed_nn_conv_tc(const DseedConvTc *desc, cudaStream_t stream);
+/* im2col of a BF16 activation (as dseed_nn_im2col1d, BF16 in and out). */
+int dseed_nn_im2col1d_bf16(const void *x_dev, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad,
+                           void *cols_dev, cudaStream_t stream);
+/* Nearest-neighbour x2 upsampling along L of a BF16 activation [N][L][C] -> [N][2L][C]. */
+int dseed_nn_upsample2_bf16(const void *x_dev, int N, int L, int C, void *y_dev, cudaStream_t stream);
+
 /* ------------------------------------------------ plan without allocation */
 
 /* The paper has no counterpart to this call; it exists for callers that

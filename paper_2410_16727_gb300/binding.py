@@ -78,6 +78,16 @@ class Request(C.Structure):
                 ("cost_host", C.c_void_p), ("success_host", C.c_void_p), ("best_host", C.c_void_p)]
 
 
+class ConvTc(C.Structure):
+    _fields_ = [("a0_dev", C.c_void_p), ("c0", C.c_int), ("a1_dev", C.c_void_p), ("c1", C.c_int),
+                ("n_samples", C.c_int), ("L", C.c_int), ("taps", C.c_int), ("pad", C.c_int),
+                ("w_dev", C.c_void_p), ("cout", C.c_int), ("cout_pad", C.c_int), ("bias_dev", C.c_void_p),
+                ("epilogue", C.c_int), ("rows_per_sample", C.c_int), ("gn_eps", C.c_float),
+                ("gamma_dev", C.c_void_p), ("beta_dev", C.c_void_p), ("film_dev", C.c_void_p),
+                ("sample_problem_dev", C.c_void_p), ("res_dev", C.c_void_p), ("out_dev", C.c_void_p),
+                ("out_ld", C.c_int), ("err_dev", C.c_void_p)]
+
+
 class ServerStats(C.Structure):
     _fields_ = [("submitted", C.c_longlong), ("admitted", C.c_longlong), ("completed", C.c_longlong),
                 ("failed", C.c_longlong), ("rounds", C.c_longlong), ("queued", C.c_int), ("active", C.c_int),
@@ -157,6 +167,10 @@ _SIGS = {
     "dseed_nn_to_bf16": ([C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p], C.c_int),
     "dseed_nn_clamp_affine": ([C.c_void_p, C.c_float, C.c_float, C.c_float, C.c_float, C.c_void_p, C.c_longlong,
                                C.c_void_p], C.c_int),
+    "dseed_nn_conv_tc": ([C.POINTER(ConvTc), C.c_void_p], C.c_int),
+    "dseed_nn_im2col1d_bf16": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_nn_upsample2_bf16": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
     "dseed_plan_batch_static": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -576,3 +590,44 @@ def nn(name: str, *args):
             conv.append(a)
     fn = getattr(load(), "dseed_nn_" + name)
     _check(fn(*conv, _stream()), "dseed_nn_" + name)
+
+
+EPI_F32, EPI_BF16, EPI_GN = 0, 1, 2
+
+
+def conv_tc(a0: torch.Tensor, w: torch.Tensor, out: torch.Tensor, *, n_samples: int, L: int, taps: int = 1,
+            pad: int = 0, cout: int, a1: Optional[torch.Tensor] = None, bias: Optional[torch.Tensor] = None,
+            epilogue: int = EPI_BF16, rows_per_sample: int = 1, gn_eps: float = 1e-5,
+            gamma: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None,
+            film: Optional[torch.Tensor] = None, sample_problem: Optional[torch.Tensor] = None,
+            res: Optional[torch.Tensor] = None, out_ld: Optional[int] = None, err: Optional[torch.Tensor] = None):
+    """dseed_nn_conv_tc: tensor-core convolution with a fused layer tail.
+    a0 / a1 BF16 [n_samples][L][c] (channels-last, contiguous); w BF16
+    [cout_pad][taps][c0 + c1]; out [n_samples * L][out_ld] (FP32 for EPI_F32)."""
+    def ptr(t, name, dtype=None):
+        if t is None:
+            return None
+        if not t.is_cuda or not t.is_contiguous():
+            raise DseedError(f"conv_tc: {name} must be a contiguous CUDA tensor")
+        if dtype is not None and t.dtype != dtype:
+            raise DseedError(f"conv_tc: {name} must be {dtype}")
+        return t.data_ptr()
+    d = ConvTc()
+    d.a0_dev = ptr(a0, "a0", torch.bfloat16)
+    d.c0 = int(a0.shape[-1])
+    d.a1_dev = ptr(a1, "a1", torch.bfloat16)
+    d.c1 = int(a1.shape[-1]) if a1 is not None else 0
+    d.n_samples, d.L, d.taps, d.pad = int(n_samples), int(L), int(taps), int(pad)
+    d.w_dev = ptr(w, "w", torch.bfloat16)
+    d.cout, d.cout_pad = int(cout), int(w.shape[0])
+    d.bias_dev = ptr(bias, "bias", torch.float32)
+    d.epilogue, d.rows_per_sample, d.gn_eps = int(epilogue), int(rows_per_sample), float(gn_eps)
+    d.gamma_dev, d.beta_dev = ptr(gamma, "gamma", torch.float32), ptr(beta, "beta", torch.float32)
+    d.film_dev = ptr(film, "film", torch.float32)
+    d.sample_problem_dev = ptr(sample_problem, "sample_problem", torch.int32)
+    d.res_dev = ptr(res, "res", torch.bfloat16)
+    d.out_dev = ptr(out, "out", torch.float32 if epilogue == EPI_F32 else torch.bfloat16)
+    d.out_ld = int(out_ld if out_ld is not None else cout)
+    d.err_dev = ptr(err, "err", torch.int32)
+    _check(load().dseed_nn_conv_tc(C.byref(d), _stream()), "dseed_nn_conv_tc")
+    return out

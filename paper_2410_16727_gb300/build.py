@@ -16,7 +16,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdseed.so")
-SOURCES = ["abi.cu", "kernels_esdf.cu", "kernels_eval.cu", "kernels_plan.cu", "kernels_serve.cu", "server.cu", "kernels_nn.cu", "abi_nn.cu"]
+SOURCES = ["abi.cu", "kernels_esdf.cu", "kernels_eval.cu", "kernels_plan.cu", "kernels_serve.cu", "server.cu",
+           "kernels_nn.cu", "abi_nn.cu", "kernels_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,5 +1,6 @@
 // abi_nn.cu -- C ABI of the denoiser layers (kernels in kernels_nn.cu).
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include "internal.h"
 
@@ -37,6 +38,11 @@ int nn_ddim_step(const float *xk, const float *eps, float ab_k, float ab_prev, l
                  cudaStream_t st);
 int nn_to_bf16(const float *x, void *y, long long n, cudaStream_t st);
 int nn_clamp_affine(const float *x, float a, float b, float lo, float hi, float *out, long long n, cudaStream_t st);
+int nn_conv_tc(const DseedConvTc &d, cudaStream_t st);
+bool tc_maps_available();
+int nn_im2col1d_bf16(const void *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols,
+                     cudaStream_t st);
+int nn_upsample2_bf16(const void *x, int N, int L, int C, void *y, cudaStream_t st);
 }  // namespace dseed
 
 using dseed::set_error;
@@ -189,6 +195,50 @@ int dseed_nn_clamp_affine(const float *x_dev, float a, float b, float lo, float 
                           cudaStream_t stream) {
     NEED(n >= 0 && x_dev && out_dev, "clamp_affine: bad arguments");
     return cu(dseed::nn_clamp_affine(x_dev, a, b, lo, hi, out_dev, n, stream), "clamp_affine");
+}
+
+namespace {
+bool pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+bool al16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+}  // namespace
+
+int dseed_nn_conv_tc(const DseedConvTc *d, cudaStream_t stream) {
+    NEED(d, "conv_tc: NULL descriptor");
+    NEED(d->n_samples >= 0 && pow2(d->L) && d->L <= 128, "conv_tc: L must be a power of two <= 128");
+    NEED(d->c0 > 0 && d->c0 % 64 == 0 && d->c1 >= 0 && d->c1 % 64 == 0, "conv_tc: channels must be multiples of 64");
+    NEED(d->taps >= 1 && d->taps <= 8 && d->pad >= 0 && d->pad < d->taps, "conv_tc: bad taps / pad");
+    NEED(d->cout_pad == 16 || d->cout_pad == 64 || d->cout_pad == 128 || d->cout_pad == 256,
+         "conv_tc: cout_pad must be 16, 64, 128 or 256");
+    NEED(d->cout >= 1 && d->cout <= d->cout_pad && d->out_ld >= d->cout, "conv_tc: bad cout / out_ld");
+    NEED(d->epilogue >= 0 && d->epilogue <= 2, "conv_tc: bad epilogue");
+    NEED(d->a0_dev && d->w_dev && d->out_dev && (d->c1 == 0 || d->a1_dev), "conv_tc: NULL operand");
+    NEED(al16(d->a0_dev) && al16(d->a1_dev) && al16(d->w_dev) && al16(d->out_dev) && al16(d->bias_dev) &&
+             al16(d->gamma_dev) && al16(d->beta_dev) && al16(d->film_dev) && al16(d->res_dev),
+         "conv_tc: pointers must be 16-byte aligned");
+    if (d->epilogue >= 1) NEED(d->out_ld % 8 == 0, "conv_tc: BF16 output rows must be multiples of 8");
+    if (d->epilogue == 2) {
+        NEED(d->cout == d->cout_pad && d->cout_pad >= 64, "conv_tc: group norm needs cout = cout_pad >= 64");
+        NEED(d->bias_dev && d->gamma_dev && d->beta_dev, "conv_tc: group norm needs bias, gamma and beta");
+        NEED(pow2(d->rows_per_sample) && d->rows_per_sample <= 32 &&
+                 ((long long)d->n_samples * d->L) % d->rows_per_sample == 0,
+             "conv_tc: rows_per_sample must be a power of two <= 32 dividing the rows");
+        NEED(d->gn_eps > 0.f, "conv_tc: gn_eps must be positive");
+    }
+    const int r = dseed::nn_conv_tc(*d, stream);
+    if (r == -1) return set_error(DSEED_ECUDA, "conv_tc: tensor map encoding failed (driver entry point missing?)");
+    return cu(r, "conv_tc");
+}
+
+int dseed_nn_im2col1d_bf16(const void *x_dev, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad,
+                           void *cols_dev, cudaStream_t stream) {
+    NEED(N >= 0 && L >= 1 && C >= 1 && k >= 1 && s >= 1 && p >= 0 && Lo >= 0 && kc_pad >= k * C && x_dev && cols_dev,
+         "im2col1d_bf16: bad arguments");
+    return cu(dseed::nn_im2col1d_bf16(x_dev, N, L, C, k, s, p, Lo, kc_pad, cols_dev, stream), "im2col1d_bf16");
+}
+
+int dseed_nn_upsample2_bf16(const void *x_dev, int N, int L, int C, void *y_dev, cudaStream_t stream) {
+    NEED(N >= 0 && L >= 1 && C >= 1 && x_dev && y_dev, "upsample2_bf16: bad arguments");
+    return cu(dseed::nn_upsample2_bf16(x_dev, N, L, C, y_dev, stream), "upsample2_bf16");
 }
 
 }  // extern "C"

@@ -186,6 +186,34 @@ __global__ void k_im2col1d(const float *__restrict__ x, int N, int L, int C, int
     }
 }
 
+// the same on BF16 activations (inference path)
+__global__ void k_im2col1d_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo,
+                             int kc_pad, __nv_bfloat16 *__restrict__ cols) {
+    const long long total = (long long)N * Lo * kc_pad;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int col = (int)(i % kc_pad);
+        const long long row = i / kc_pad;
+        const int lo = (int)(row % Lo), n = (int)(row / Lo);
+        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
+        if (col < k * C) {
+            const int j = col / C, c = col - j * C;
+            const int li = lo * s - p + j;
+            if (li >= 0 && li < L) v = x[((size_t)n * L + li) * C + c];
+        }
+        cols[i] = v;
+    }
+}
+
+__global__ void k_upsample2_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, __nv_bfloat16 *__restrict__ y) {
+    const long long total = (long long)N * 2 * L * C;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long r = i / C;
+        const int l2 = (int)(r % (2 * L)), n = (int)(r / (2 * L));
+        y[i] = x[((size_t)n * L + l2 / 2) * C + c];
+    }
+}
+
 // col2im (backward of im2col): dx[n][li][c] += sum over (lo, j) with lo*s - p + j = li.
 __global__ void k_col2im1d(const float *__restrict__ cols, int N, int L, int C, int k, int s, int p, int Lo,
                            int kc_pad, float *__restrict__ dx) {
@@ -554,6 +582,20 @@ int nn_im2col1d(const float *x, int N, int L, int C, int k, int s, int p, int Lo
     const long long total = (long long)N * Lo * kc_pad;
     if (bf16) k_im2col1d<__nv_bfloat16><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
     else k_im2col1d<float><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (float *)cols);
+    return (int)cudaGetLastError();
+}
+
+int nn_im2col1d_bf16(const void *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols,
+                     cudaStream_t st) {
+    const long long total = (long long)N * Lo * kc_pad;
+    k_im2col1d_b<<<grid_for(total), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, k, s, p, Lo, kc_pad,
+                                                   (__nv_bfloat16 *)cols);
+    return (int)cudaGetLastError();
+}
+
+int nn_upsample2_bf16(const void *x, int N, int L, int C, void *y, cudaStream_t st) {
+    const long long total = (long long)N * 2 * L * C;
+    k_upsample2_b<<<grid_for(total), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, (__nv_bfloat16 *)y);
     return (int)cudaGetLastError();
 }
 

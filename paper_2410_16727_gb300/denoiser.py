@@ -4,8 +4,11 @@ method, paper Sec. 4.2-4.3), built from libdseed's layer kernels.
 Orchestration only: each layer call below is one C-ABI kernel launch
 (binding.nn); this module decides their order, keeps the activations the
 backward pass needs (a tape of closures, replayed in reverse), and owns the
-parameter, gradient and Adam buffers (device tensors).  Training runs in FP32;
-`infer` runs every GEMM on the tensor cores in BF16 (FP32 accumulation).
+parameter, gradient and Adam buffers (device tensors).  Training runs in FP32.
+Sampling runs the U-Net through `unet_tc`: BF16 activations, every
+convolution one tcgen05 tensor-core kernel with its group norm, Mish, FiLM and
+residual fused in (dseed_nn_conv_tc).  `infer` (BF16 operands on the legacy
+mma.sync path, FP32 activations) is kept as the second BF16 reference.
 
 Inputs of one sample: the noisy trajectory x_k [T][D], the diffusion step k,
 the normalised start and goal configurations [D], the goal pose [7] and the
@@ -75,6 +78,7 @@ class Denoiser:
         self.abar = torch.tensor(cosine_abar(spec.K), dtype=torch.float32, device=self.dev)
         self.abar_host = cosine_abar(spec.K)
         self._bf16: Dict[str, torch.Tensor] = {}
+        self._tc_err = torch.zeros(1, dtype=torch.int32, device=self.dev)
         self.init_params(seed)
 
     # ------------------------------------------------------------------ parameters
@@ -415,8 +419,9 @@ class Denoiser:
         """DDIM (deterministic) from x_K = noise over `steps` evenly spaced steps
         of the K-step schedule; returns normalised trajectories [N][T][D].
         qs, qg, goal, occ are per problem; sample_problem [N] (int32) maps each
-        sample to its problem (default: sample n -> problem n).  The condition is
-        computed once per problem and step and broadcast to the samples."""
+        sample to its problem (default: sample n -> problem n).  The condition
+        and the FiLM rows are computed once per problem and step; with bf16 the
+        U-Net runs on the tensor cores (unet_tc), else in FP32."""
         K = self.spec.K
         ks = np.linspace(K - 1, 0, steps).round().astype(int)
         x = noise.clone()
@@ -425,20 +430,176 @@ class Denoiser:
         rows = sample_problem if sample_problem is not None else torch.arange(N, dtype=torch.int32, device=self.dev)
         for i, kk in enumerate(ks):
             kp = torch.full((P,), int(kk), dtype=torch.int32, device=self.dev)
-            self.bf16_mode = bf16
-            try:
-                mc_p = self.condition(kp, qs, qg, goal, occ, None)
+            mc_p = self.condition(kp, qs, qg, goal, occ, None)
+            if bf16:
+                eps = self.unet_tc(x, N, self.film_rows(mc_p), rows)
+            else:
                 mc = torch.empty((N, mc_p.shape[1]), dtype=torch.float32, device=self.dev)
                 _nn("gather_rows", mc_p, rows, N, mc_p.shape[1], mc)
                 eps = self.unet(x, N, mc, None)
-            finally:
-                self.bf16_mode = False
             ab_k = float(self.abar_host[kk])
             ab_prev = float(self.abar_host[ks[i + 1]]) if i + 1 < len(ks) else 1.0
             out = torch.empty_like(x)
             _nn("ddim_step", x, eps, ab_k, ab_prev, x.numel(), clip, out)
             x = out
+        if bf16:
+            self.check_tc()
         return x
+
+    # ------------------------------------------------------------------ tensor-core inference
+    def _tc_weights(self) -> dict:
+        """BF16 weights in the layouts dseed_nn_conv_tc reads, and 16-byte
+        aligned FP32 copies of biases and group-norm affines; rebuilt after any
+        parameter update (the cache is cleared with the BF16 one)."""
+        pk = self._bf16.get("__tc__")
+        if pk is not None:
+            return pk
+        s = self.spec
+        pk = {}
+
+        def f32(name):
+            t = torch.empty(self.offsets[name][1], dtype=torch.float32, device=self.dev)
+            t.copy_(self.P(name).view(t.shape))
+            return t
+
+        def packed(name, rows_pad=None, cols_pad=None):
+            co, k, ci = self.offsets[name + ".w"][1]
+            kc = k * ci
+            cp = cols_pad or kc
+            w = torch.zeros((rows_pad or co, cp), dtype=torch.bfloat16, device=self.dev)
+            _nn("im2col1d", self.P(name + ".w"), co, 1, kc, 1, 1, 0, 1, cp, w, 1)   # [co][kc] -> [co][cp]
+            return w
+
+        for name, cin, cout in NS.res_blocks(s):
+            first = cin == s.D
+            pk[name + ".c1"] = packed(name + ".c1", cols_pad=64 if first else None)
+            pk[name + ".c2"] = packed(name + ".c2")
+            if cin != cout:
+                pk[name + ".r"] = packed(name + ".r", cols_pad=64 if first else None)
+                pk[name + ".r.b"] = f32(name + ".r.b")
+            for t in ("c1.b", "c2.b", "g1.w", "g1.b", "g2.w", "g2.b"):
+                pk[name + "." + t] = f32(name + "." + t)
+        for name in ("down1", "down2", "up2", "up1", "fin.c"):
+            pk[name] = packed(name)
+            pk[name + ".b"] = f32(name + ".b")
+        pk["fin.o"] = packed("fin.o", rows_pad=16)
+        pk["fin.o.b"] = f32("fin.o.b")
+        for t in ("fin.g.w", "fin.g.b"):
+            pk[t] = f32(t)
+        self._bf16["__tc__"] = pk
+        return pk
+
+    def _tc_block(self, W, srcs, N, L, name, cin, cout, film, rows, plain_in=None):
+        """Conditional residual block: conv-GN-Mish-FiLM, conv-GN-Mish + residual,
+        as two (three with a 1x1 residual projection) fused kernels."""
+        s = self.spec
+        a0, a1 = srcs[0], (srcs[1] if len(srcs) > 1 else None)
+        gn = dict(epilogue=B.EPI_GN, rows_per_sample=L, gn_eps=s.gn_eps, cout=cout, err=self._tc_err)
+        h = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
+        if plain_in is not None:                      # first layer: im2col rows of the 7-channel input
+            B.conv_tc(plain_in[0], W[name + ".c1"], h, n_samples=N * L, L=1, bias=W[name + ".c1.b"],
+                      gamma=W[name + ".g1.w"], beta=W[name + ".g1.b"], film=film, sample_problem=rows, **gn)
+        else:
+            B.conv_tc(a0, W[name + ".c1"].view(cout, s.kernel, cin), h, a1=a1, n_samples=N, L=L, taps=s.kernel,
+                      pad=s.kernel // 2, bias=W[name + ".c1.b"], gamma=W[name + ".g1.w"], beta=W[name + ".g1.b"],
+                      film=film, sample_problem=rows, **gn)
+        if cin != cout:
+            r = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
+            if plain_in is not None:
+                B.conv_tc(plain_in[1], W[name + ".r"], r, n_samples=N * L, L=1, cout=cout, bias=W[name + ".r.b"],
+                          epilogue=B.EPI_BF16, err=self._tc_err)
+            else:
+                B.conv_tc(a0, W[name + ".r"].view(cout, 1, cin), r, a1=a1, n_samples=N, L=L, cout=cout,
+                          bias=W[name + ".r.b"], epilogue=B.EPI_BF16, err=self._tc_err)
+        else:
+            r = a0
+        out = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
+        B.conv_tc(h, W[name + ".c2"].view(cout, s.kernel, cout), out, n_samples=N, L=L, taps=s.kernel,
+                  pad=s.kernel // 2, bias=W[name + ".c2.b"], gamma=W[name + ".g2.w"], beta=W[name + ".g2.b"],
+                  res=r, **gn)
+        return out
+
+    def _tc_conv(self, W, x, N, L, name, k, pad, cout):
+        y = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
+        cin = x.shape[-1]
+        B.conv_tc(x, W[name].view(cout, k, cin), y, n_samples=N, L=L, taps=k, pad=pad, cout=cout,
+                  bias=W[name + ".b"], epilogue=B.EPI_BF16, err=self._tc_err)
+        return y
+
+    def _tc_down(self, W, x, N, L, name, cout):
+        """Stride-2 convolution (k = 3, pad 1): BF16 im2col rows, then one plain GEMM."""
+        cin = x.shape[-1]
+        Lo = L // 2
+        cols = torch.empty((N * Lo, 3 * cin), dtype=torch.bfloat16, device=self.dev)
+        _nn("im2col1d_bf16", x, N, L, cin, 3, 2, 1, Lo, 3 * cin, cols)
+        y = torch.empty((N, Lo, cout), dtype=torch.bfloat16, device=self.dev)
+        B.conv_tc(cols, W[name], y, n_samples=N * Lo, L=1, cout=cout, bias=W[name + ".b"], epilogue=B.EPI_BF16,
+                  err=self._tc_err)
+        return y, Lo
+
+    def _tc_up(self, x, N, L):
+        C = x.shape[-1]
+        y = torch.empty((N, 2 * L, C), dtype=torch.bfloat16, device=self.dev)
+        _nn("upsample2_bf16", x, N, L, C, y)
+        return y
+
+    def unet_tc(self, x, N, film_p: Dict[str, torch.Tensor], rows: torch.Tensor) -> torch.Tensor:
+        """Predicted noise [N][T][D] (FP32) of x [N][T][D] (FP32) on the tensor
+        cores.  film_p[block] = FiLM rows [P][2 cout] per problem; rows [N] int32
+        = the problem of each sample."""
+        s = self.spec
+        c1, c2, c3 = s.chans
+        T, D = s.T, s.D
+        W = self._tc_weights()
+        cols = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
+        _nn("im2col1d", x, N, T, D, s.kernel, 1, s.kernel // 2, T, 64, cols, 1)
+        x64 = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
+        _nn("im2col1d", x, N, T, D, 1, 1, 0, T, 64, x64, 1)
+        blk = lambda srcs, L, name, ci, co, plain=None: self._tc_block(W, srcs, N, L, name, ci, co, film_p[name],
+                                                                        rows, plain)
+        h = blk([None], T, "d1a", D, c1, (cols, x64))
+        h = blk([h], T, "d1b", c1, c1)
+        h, L2 = self._tc_down(W, h, N, T, "down1", c1)
+        h = blk([h], L2, "d2a", c1, c2)
+        s2 = blk([h], L2, "d2b", c2, c2)
+        h, L3 = self._tc_down(W, s2, N, L2, "down2", c2)
+        h = blk([h], L3, "d3a", c2, c3)
+        s3 = blk([h], L3, "d3b", c3, c3)
+        h = blk([s3], L3, "mid", c3, c3)
+        h = blk([h, s3], L3, "u2a", 2 * c3, c2)
+        h = blk([h], L3, "u2b", c2, c2)
+        h = self._tc_conv(W, self._tc_up(h, N, L3), N, L2, "up2", 3, 1, c2)
+        h = blk([h, s2], L2, "u1a", 2 * c2, c1)
+        h = blk([h], L2, "u1b", c1, c1)
+        h = self._tc_conv(W, self._tc_up(h, N, L2), N, T, "up1", 3, 1, c1)
+        g = torch.empty((N, T, c1), dtype=torch.bfloat16, device=self.dev)
+        B.conv_tc(h, W["fin.c"].view(c1, s.kernel, c1), g, n_samples=N, L=T, taps=s.kernel, pad=s.kernel // 2,
+                  cout=c1, bias=W["fin.c.b"], epilogue=B.EPI_GN, rows_per_sample=T, gn_eps=s.gn_eps,
+                  gamma=W["fin.g.w"], beta=W["fin.g.b"], err=self._tc_err)
+        out = torch.empty((N, T, D), dtype=torch.float32, device=self.dev)
+        B.conv_tc(g, W["fin.o"], out, n_samples=N * T, L=1, cout=D, bias=W["fin.o.b"], epilogue=B.EPI_F32,
+                  out_ld=D, err=self._tc_err)
+        return out
+
+    def film_rows(self, mc_p: torch.Tensor) -> Dict[str, torch.Tensor]:
+        """FiLM scale/shift rows of every residual block from per-problem conditions."""
+        return {name: self.linear(mc_p, name + ".f", None) for name, _, _ in NS.res_blocks(self.spec)}
+
+    def check_tc(self):
+        """Raise if a tensor-core kernel reported a pipeline wait that gave up."""
+        code = int(self._tc_err.item())
+        if code != 0:
+            self._tc_err.zero_()
+            raise B.DseedError(f"conv_tc: a pipeline wait gave up (code {code})")
+
+    def infer_tc(self, xk, k, qs, qg, goal, occ):
+        """Predicted noise with the tensor-core U-Net (condition per sample)."""
+        N = xk.shape[0]
+        mc = self.condition(k, qs, qg, goal, occ, None)
+        rows = torch.arange(N, dtype=torch.int32, device=self.dev)
+        out = self.unet_tc(xk.contiguous(), N, self.film_rows(mc), rows)
+        self.check_tc()
+        return out
 
     # ------------------------------------------------------------------ checkpoints
     def state(self) -> dict:

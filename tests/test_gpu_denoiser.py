@@ -83,6 +83,36 @@ def test_bf16_inference_close_to_fp32(gpu_lib, net):
     assert _rel(b16, f32) <= 3e-2
 
 
+def test_tensor_core_unet_matches_oracle(gpu_lib, net):
+    """The sampling path (BF16 activations, tcgen05 convolutions with fused
+    group norm / Mish / FiLM / residual) against the FP64 oracle forward."""
+    inp = _inputs(net.spec, 40, seed=12)
+    args = [_cuda(inp[k]) for k in ("x0", "k", "qs", "qg", "goal", "occ")]
+    got = net.infer_tc(*args).cpu().numpy()
+    want = DO.predict(net.spec, net.params.cpu().numpy(), inp["x0"], inp["k"], inp["qs"], inp["qg"], inp["goal"],
+                      inp["occ"])
+    assert _rel(got, want) <= 3e-2
+    # per sample too: no sample (tile position, ragged last tile) is off
+    for n in range(40):
+        assert _rel(got[n], want[n]) <= 6e-2, n
+
+
+def test_ddim_sampling_paths_agree(gpu_lib, net):
+    """DDIM with shared per-problem conditions: the tensor-core path and the
+    FP32 path give the same trajectories up to BF16 rounding."""
+    rng = np.random.default_rng(13)
+    P, S = 3, 5
+    qs = _cuda(rng.uniform(-1, 1, (P, 7)).astype(np.float32))
+    qg = _cuda(rng.uniform(-1, 1, (P, 7)).astype(np.float32))
+    goal = _cuda(rng.normal(size=(P, 7)).astype(np.float32))
+    occ = _cuda((rng.random((P, net.spec.occ_n ** 3)) < 0.1).astype(np.float32))
+    noise = _cuda(rng.normal(size=(P * S, 32, 7)).astype(np.float32))
+    rows = torch.arange(P, dtype=torch.int32, device="cuda").repeat_interleave(S)
+    a = net.ddim_sample(qs, qg, goal, occ, noise, steps=4, bf16=True, sample_problem=rows).cpu().numpy()
+    b = net.ddim_sample(qs, qg, goal, occ, noise, steps=4, bf16=False, sample_problem=rows).cpu().numpy()
+    assert _rel(a, b) <= 3e-2
+
+
 def test_gemm_kernels_against_float64():
     rng = np.random.default_rng(4)
     for (M, N, K, ta, tb) in [(37, 65, 29, 0, 0), (130, 3, 71, 1, 0), (5, 200, 16, 0, 1), (64, 64, 64, 1, 1)]:
