@@ -484,8 +484,8 @@ int dseed_nn_to_bf16(const float *x_dev, void *y_dev, long long n, cudaStream_t 
  * epilogue 2: y = Mish(GroupNorm(out)) over groups of cout / 8 channels and
  *   rows_per_sample consecutive rows (affine gamma, beta; biased variance, eps
  *   gn_eps); then y = y * film[s][o] + film[s][cout + o] when film_dev is given
- *   (s = sample_problem[row / rows_per_sample], or row / rows_per_sample when
- *   sample_problem_dev is NULL); then y += res[row][o] (BF16 [..][cout]) when
+ *   (rows film_ld floats apart; s = sample_problem[row / rows_per_sample], or
+ *   row / rows_per_sample when sample_problem_dev is NULL); then y += res[row][o] (BF16 [..][cout]) when
  *   res_dev is given; out BF16 [..][out_ld].  Needs cout = cout_pad.
  *
  * Limits (EINVAL otherwise): c0, c1 multiples of 64 (c1 may be 0); L a power of
@@ -509,6 +509,7 @@ typedef struct {
     float gn_eps;
     const float *gamma_dev, *beta_dev;
     const float *film_dev;
+    int film_ld;             /* floats between FiLM rows (0: 2 cout) */
     const int *sample_problem_dev;
     const void *res_dev;
     void *out_dev;

@@ -84,7 +84,7 @@ class ConvTc(C.Structure):
                 ("w_dev", C.c_void_p), ("cout", C.c_int), ("cout_pad", C.c_int), ("bias_dev", C.c_void_p),
                 ("epilogue", C.c_int), ("rows_per_sample", C.c_int), ("gn_eps", C.c_float),
                 ("gamma_dev", C.c_void_p), ("beta_dev", C.c_void_p), ("film_dev", C.c_void_p),
-                ("sample_problem_dev", C.c_void_p), ("res_dev", C.c_void_p), ("out_dev", C.c_void_p),
+                ("film_ld", C.c_int), ("sample_problem_dev", C.c_void_p), ("res_dev", C.c_void_p), ("out_dev", C.c_void_p),
                 ("out_ld", C.c_int), ("err_dev", C.c_void_p)]
 
 
@@ -600,7 +600,8 @@ def conv_tc(a0: torch.Tensor, w: torch.Tensor, out: torch.Tensor, *, n_samples: 
             epilogue: int = EPI_BF16, rows_per_sample: int = 1, gn_eps: float = 1e-5,
             gamma: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None,
             film: Optional[torch.Tensor] = None, sample_problem: Optional[torch.Tensor] = None,
-            res: Optional[torch.Tensor] = None, out_ld: Optional[int] = None, err: Optional[torch.Tensor] = None):
+            res: Optional[torch.Tensor] = None, out_ld: Optional[int] = None, err: Optional[torch.Tensor] = None,
+            film_ld: int = 0):
     """dseed_nn_conv_tc: tensor-core convolution with a fused layer tail.
     a0 / a1 BF16 [n_samples][L][c] (channels-last, contiguous); w BF16
     [cout_pad][taps][c0 + c1]; out [n_samples * L][out_ld] (FP32 for EPI_F32)."""
@@ -623,7 +624,13 @@ def conv_tc(a0: torch.Tensor, w: torch.Tensor, out: torch.Tensor, *, n_samples: 
     d.bias_dev = ptr(bias, "bias", torch.float32)
     d.epilogue, d.rows_per_sample, d.gn_eps = int(epilogue), int(rows_per_sample), float(gn_eps)
     d.gamma_dev, d.beta_dev = ptr(gamma, "gamma", torch.float32), ptr(beta, "beta", torch.float32)
-    d.film_dev = ptr(film, "film", torch.float32)
+    if film is not None and film_ld:
+        if not film.is_cuda or film.dtype != torch.float32 or film.stride(-1) != 1:
+            raise DseedError("conv_tc: film must be FP32 CUDA rows")
+        d.film_dev = film.data_ptr()                 # a column slice of a wider row-major buffer
+    else:
+        d.film_dev = ptr(film, "film", torch.float32)
+    d.film_ld = int(film_ld)
     d.sample_problem_dev = ptr(sample_problem, "sample_problem", torch.int32)
     d.res_dev = ptr(res, "res", torch.bfloat16)
     d.out_dev = ptr(out, "out", torch.float32 if epilogue == EPI_F32 else torch.bfloat16)

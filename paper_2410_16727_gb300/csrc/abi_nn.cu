@@ -223,6 +223,8 @@ int dseed_nn_conv_tc(const DseedConvTc *d, cudaStream_t stream) {
                  ((long long)d->n_samples * d->L) % d->rows_per_sample == 0,
              "conv_tc: rows_per_sample must be a power of two <= 32 dividing the rows");
         NEED(d->gn_eps > 0.f, "conv_tc: gn_eps must be positive");
+        NEED(d->film_ld == 0 || (d->film_ld >= 2 * d->cout && d->film_ld % 4 == 0),
+             "conv_tc: film_ld must be 0 or a multiple of 4 >= 2 cout");
     }
     const int r = dseed::nn_conv_tc(*d, stream);
     if (r == -1) return set_error(DSEED_ECUDA, "conv_tc: tensor map encoding failed (driver entry point missing?)");
@@ -233,11 +235,14 @@ int dseed_nn_im2col1d_bf16(const void *x_dev, int N, int L, int C, int k, int s,
                            void *cols_dev, cudaStream_t stream) {
     NEED(N >= 0 && L >= 1 && C >= 1 && k >= 1 && s >= 1 && p >= 0 && Lo >= 0 && kc_pad >= k * C && x_dev && cols_dev,
          "im2col1d_bf16: bad arguments");
+    NEED(C % 8 == 0 && kc_pad % 8 == 0 && al16(x_dev) && al16(cols_dev),
+         "im2col1d_bf16: C and kc_pad must be multiples of 8, pointers 16-byte aligned");
     return cu(dseed::nn_im2col1d_bf16(x_dev, N, L, C, k, s, p, Lo, kc_pad, cols_dev, stream), "im2col1d_bf16");
 }
 
 int dseed_nn_upsample2_bf16(const void *x_dev, int N, int L, int C, void *y_dev, cudaStream_t stream) {
     NEED(N >= 0 && L >= 1 && C >= 1 && x_dev && y_dev, "upsample2_bf16: bad arguments");
+    NEED(C % 8 == 0 && al16(x_dev) && al16(y_dev), "upsample2_bf16: C must be a multiple of 8, pointers 16-byte aligned");
     return cu(dseed::nn_upsample2_bf16(x_dev, N, L, C, y_dev, stream), "upsample2_bf16");
 }
 

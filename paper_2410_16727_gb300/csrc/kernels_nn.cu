@@ -186,31 +186,60 @@ __global__ void k_im2col1d(const float *__restrict__ x, int N, int L, int C, int
     }
 }
 
-// the same on BF16 activations (inference path)
-__global__ void k_im2col1d_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo,
-                             int kc_pad, __nv_bfloat16 *__restrict__ cols) {
-    const long long total = (long long)N * Lo * kc_pad;
+// BF16 rows of 8-column chunks (16-byte stores): FP32 input, any C
+__global__ void k_im2col1d_v8(const float *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo,
+                              int kc_pad, __nv_bfloat16 *__restrict__ cols) {
+    const int chunks = kc_pad / 8;
+    const long long total = (long long)N * Lo * chunks;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int col = (int)(i % kc_pad);
-        const long long row = i / kc_pad;
+        const int ch = (int)(i % chunks);
+        const long long row = i / chunks;
         const int lo = (int)(row % Lo), n = (int)(row / Lo);
-        __nv_bfloat16 v = __float2bfloat16_rn(0.f);
-        if (col < k * C) {
-            const int j = col / C, c = col - j * C;
-            const int li = lo * s - p + j;
-            if (li >= 0 && li < L) v = x[((size_t)n * L + li) * C + c];
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+            const int col = ch * 8 + e;
+            float f = 0.f;
+            if (col < k * C) {
+                const int j = col / C, c = col - j * C;
+                const int li = lo * s - p + j;
+                if (li >= 0 && li < L) f = x[((size_t)n * L + li) * C + c];
+            }
+            v[e] = __float2bfloat16_rn(f);
         }
-        cols[i] = v;
+        *reinterpret_cast<uint4 *>(cols + row * kc_pad + ch * 8) = *reinterpret_cast<const uint4 *>(v);
     }
 }
 
-__global__ void k_upsample2_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, __nv_bfloat16 *__restrict__ y) {
-    const long long total = (long long)N * 2 * L * C;
+// the same on BF16 activations with C % 8 == 0: each thread moves 8 channels of one tap
+__global__ void k_im2col1d_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo,
+                             int kc_pad, __nv_bfloat16 *__restrict__ cols) {
+    const int chunks = kc_pad / 8, cch = C / 8;
+    const long long total = (long long)N * Lo * chunks;
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int c = (int)(i % C);
-        const long long r = i / C;
+        const int ch = (int)(i % chunks);
+        const long long row = i / chunks;
+        const int lo = (int)(row % Lo), n = (int)(row / Lo);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (ch < k * cch) {
+            const int j = ch / cch, c8 = ch - j * cch;
+            const int li = lo * s - p + j;
+            if (li >= 0 && li < L) v = *reinterpret_cast<const uint4 *>(x + ((size_t)n * L + li) * C + c8 * 8);
+        }
+        *reinterpret_cast<uint4 *>(cols + row * kc_pad + ch * 8) = v;
+    }
+}
+
+// nearest x2 upsampling of BF16 rows, 8 channels per thread (C % 8 == 0)
+__global__ void k_upsample2_b(const __nv_bfloat16 *__restrict__ x, int N, int L, int C, __nv_bfloat16 *__restrict__ y) {
+    const int cch = C / 8;
+    const long long total = (long long)N * 2 * L * cch;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int c8 = (int)(i % cch);
+        const long long r = i / cch;
         const int l2 = (int)(r % (2 * L)), n = (int)(r / (2 * L));
-        y[i] = x[((size_t)n * L + l2 / 2) * C + c];
+        *reinterpret_cast<uint4 *>(y + r * C + c8 * 8) =
+            *reinterpret_cast<const uint4 *>(x + ((size_t)n * L + l2 / 2) * C + c8 * 8);
     }
 }
 
@@ -580,7 +609,9 @@ int nn_gemm_bf16(int M, int N, int K, const void *A, const void *W, float *C, co
 int nn_im2col1d(const float *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols, int bf16,
                 cudaStream_t st) {
     const long long total = (long long)N * Lo * kc_pad;
-    if (bf16) k_im2col1d<__nv_bfloat16><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
+    if (bf16 && kc_pad % 8 == 0 && ((uintptr_t)cols & 15) == 0)
+        k_im2col1d_v8<<<grid_for(total / 8), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
+    else if (bf16) k_im2col1d<__nv_bfloat16><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
     else k_im2col1d<float><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (float *)cols);
     return (int)cudaGetLastError();
 }
@@ -588,14 +619,14 @@ int nn_im2col1d(const float *x, int N, int L, int C, int k, int s, int p, int Lo
 int nn_im2col1d_bf16(const void *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols,
                      cudaStream_t st) {
     const long long total = (long long)N * Lo * kc_pad;
-    k_im2col1d_b<<<grid_for(total), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, k, s, p, Lo, kc_pad,
-                                                   (__nv_bfloat16 *)cols);
+    k_im2col1d_b<<<grid_for(total / 8), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, k, s, p, Lo, kc_pad,
+                                                       (__nv_bfloat16 *)cols);
     return (int)cudaGetLastError();
 }
 
 int nn_upsample2_bf16(const void *x, int N, int L, int C, void *y, cudaStream_t st) {
     const long long total = (long long)N * 2 * L * C;
-    k_upsample2_b<<<grid_for(total), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, (__nv_bfloat16 *)y);
+    k_upsample2_b<<<grid_for(total / 8), 256, 0, st>>>((const __nv_bfloat16 *)x, N, L, C, (__nv_bfloat16 *)y);
     return (int)cudaGetLastError();
 }
 

@@ -4,8 +4,8 @@
 // rest of the layer: bias, group norm, Mish, FiLM and the residual add of the
 // U-Net's conditional residual blocks (Sec. 4.2), writing BF16 activations.
 //
-// Geometry.  Activations are channels-last BF16 [samples][L][C].  One CTA owns
-// 128 output rows = 128 / L whole samples, and every output channel (N = COUT,
+// Geometry.  Activations are channels-last BF16 [samples][L][C].  A tile is
+// 128 output rows = 128 / L whole samples by every output channel (N = COUT,
 // <= 256, one MMA wide).  The K loop runs over (tap j, 64-channel block): the A
 // tile of tap j is the TMA box {64 channels, L rows starting at row j - pad,
 // 128 / L samples} of the input; rows outside [0, L) fall out of the tensor and
@@ -13,11 +13,14 @@
 // im2col buffer exists.  A second source tensor supplies the channels past c0
 // (the U-Net's skip concatenations).  A plain GEMM is the case L = 1, one tap.
 //
-// Roles: thread 0 issues TMA loads into a ring of STAGES stages; thread 32
-// issues the MMAs (4 x K=16 per stage) and returns each stage with
-// tcgen05.commit; all 8 warps then run the epilogue, warp w reading TMEM lanes
-// 32 (w % 4) .. +31 and columns of half w / 4.  Every wait is bounded (2 s);
-// one that gives up sets *err and the CTA still releases its tensor memory.
+// Roles (persistent CTAs, one per SM, tiles strided by the grid): one lane of
+// warp 0 issues TMA loads into a ring of STAGES stages; one lane of warp 1
+// issues the MMAs (4 x K=16 per stage), returns each stage with tcgen05.commit
+// and alternates between two TMEM accumulator buffers; the remaining warps
+// (8 or 16) run the epilogue of one tile while the next tile accumulates, warp
+// w reading TMEM lanes 32 (w % 4) .. +31 and column part (w - 2) / 4.  Every wait is
+// bounded (2 s); one that gives up sets *err and the CTA still releases its
+// tensor memory.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -33,7 +36,7 @@ namespace {
 
 constexpr int kTileM = 128;
 constexpr int kBlockK = 64;                  // BF16 channels per K block: one 128-byte swizzle row
-constexpr int kTcThreads = 256;
+
 constexpr int kGroups = 8;                   // group-norm groups (the network's)
 constexpr unsigned long long kWaitNs = 2000000000ull;
 
@@ -48,7 +51,7 @@ struct TcParams {
     const int *sample_problem;
     const __nv_bfloat16 *res;
     void *out;
-    int out_ld;
+    int out_ld, film_ld;
     int *err;
 };
 
@@ -142,11 +145,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float mish_f(float x) {
-    const float sp = x > 20.f ? x : log1pf(expf(x));
-    return x * tanhf(sp);
-}
-
 __device__ __forceinline__ void load8(const float *p, float (&v)[8]) {
     const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
@@ -179,108 +177,190 @@ __device__ __forceinline__ void record_failure(int *err, int code) {
 }
 
 // ---------------------------------------------------------------- epilogues
+// Columns are read from tensor memory in chunks of CH (32, or the whole half
+// for narrow outputs) in one load; a chunk holds whole normalisation groups,
+// so the group statistics come from registers (two passes: mean, then the
+// centred second moment) reduced over the sample's Lg lanes by shuffles.
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float (&v)[N]);
+
+template <>
+__device__ __forceinline__ void tmem_ld<8>(uint32_t taddr, float (&v)[8]) {
+    tmem_ld8(taddr, v);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<16>(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <>
+__device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];\n"
+        "tcgen05.wait::ld.sync.aligned;\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// Mish(x) = x tanh(softplus(x)); with e = exp(x), tanh(log(1 + e)) =
+// ((1 + e)^2 - 1) / ((1 + e)^2 + 1) = n / (n + 2), n = e (e + 2).
+__device__ __forceinline__ float mish_fast(float x) {
+    if (x > 15.f) return x;                   // n / (n + 2) = 1 to FP32 precision
+    const float e = __expf(x);
+    const float n = e * (e + 2.f);
+    return x * __fdividef(n, n + 2.f);
+}
+
+// Per-layer constants, staged in shared memory once per CTA.
+struct EpiConst {
+    float bias[256], gamma[256], beta[256];
+};
+
+// Epilogue warps per CTA: 16 for outputs up to 128 channels (a quarter of
+// the columns each, chunks of 16), 8 for wider ones (half the columns, chunks
+// of 32), keeping the per-thread registers within the CTA's budget.
+template <int COUT>
+struct EpiShape {
+    static constexpr int EW = COUT <= 128 && COUT >= 64 ? 16 : 8;
+    static constexpr int PART = COUT / (EW / 4);            // columns per warp
+    static constexpr int CH = EW == 16 ? 16 : (PART < 32 ? PART : 32);
+};
+
 template <int COUT, int MODE>
-__device__ __forceinline__ void epilogue(const TcParams &p, uint32_t tmem, int m0, int warp, int lane) {
-    constexpr int HALF = COUT / 2;
-    const int q = warp & 3, half = warp >> 2;
+__device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, uint32_t tmem, int m0, int q,
+                                         int part, int lane) {
+    constexpr int HALF = EpiShape<COUT>::PART;
+    constexpr int CH = EpiShape<COUT>::CH;
     const int gm = m0 + q * 32 + lane;
     const bool valid = gm < p.M;
     const uint32_t trow = tmem + ((uint32_t)(q * 32) << 16);
-    const int cb = half * HALF;
+    const int cb = part * HALF;
     if constexpr (MODE == kEpiGN) {
-        constexpr int CG = COUT / kGroups, GH = kGroups / 2;
-        static_assert(CG % 8 == 0, "group width must be a multiple of 8 columns");
+        constexpr int CG = COUT / kGroups;
+        static_assert(CH % CG == 0, "a chunk must hold whole groups");
+        constexpr int GPC = CH / CG;            // groups per chunk
         const int Lg = p.rows_per_sample;
-        float mean[GH], rstd[GH];
-        // pass 1: group means over the sample's rows (Lg consecutive lanes)
-#pragma unroll
-        for (int g = 0; g < GH; ++g) {
-            float s = 0.f;
-#pragma unroll
-            for (int c8 = 0; c8 < CG; c8 += 8) {
-                const int c = cb + g * CG + c8;
-                float v[8], b[8];
-                tmem_ld8(trow + c, v);
-                load8(p.bias + c, b);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) s += v[i] + b[i];
-            }
-            for (int off = 1; off < Lg; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            mean[g] = s / (float)(Lg * CG);
-        }
-        // pass 2: centred second moments (biased variance)
-#pragma unroll
-        for (int g = 0; g < GH; ++g) {
-            float s = 0.f;
-#pragma unroll
-            for (int c8 = 0; c8 < CG; c8 += 8) {
-                const int c = cb + g * CG + c8;
-                float v[8], b[8];
-                tmem_ld8(trow + c, v);
-                load8(p.bias + c, b);
-#pragma unroll
-                for (int i = 0; i < 8; ++i) {
-                    const float d = v[i] + b[i] - mean[g];
-                    s += d * d;
-                }
-            }
-            for (int off = 1; off < Lg; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
-            rstd[g] = rsqrtf(s / (float)(Lg * CG) + p.gn_eps);
-        }
-        // pass 3: normalise, affine, Mish, FiLM, residual; BF16 out
+        const float inv_n = 1.f / (float)(Lg * CG);
         const float *film = nullptr;
         if (p.film && valid) {
             const int prob = p.sample_problem ? p.sample_problem[gm / Lg] : gm / Lg;
-            film = p.film + (size_t)prob * 2 * COUT;
+            film = p.film + (size_t)prob * p.film_ld;
         }
+        const __nv_bfloat16 *res = (p.res && valid) ? p.res + (size_t)gm * COUT : nullptr;
         __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(p.out) + (size_t)gm * p.out_ld;
+#pragma unroll 1
+        for (int c0 = cb; c0 < cb + HALF; c0 += CH) {
+            // FiLM rows and the residual do not depend on the accumulator: issue
+            // their loads first so their latency hides behind the statistics
+            float4 fsc[CH / 4], fsh[CH / 4];
+            uint4 rr[CH / 8];
+            if (film) {
 #pragma unroll
-        for (int g = 0; g < GH; ++g) {
+                for (int j = 0; j < CH / 4; ++j) {
+                    fsc[j] = *reinterpret_cast<const float4 *>(film + c0 + 4 * j);
+                    fsh[j] = *reinterpret_cast<const float4 *>(film + COUT + c0 + 4 * j);
+                }
+            }
+            if (res) {
 #pragma unroll
-            for (int c8 = 0; c8 < CG; c8 += 8) {
-                const int c = cb + g * CG + c8;
-                float v[8], b[8], ga[8], be[8];
-                tmem_ld8(trow + c, v);
-                if (valid) {
-                    load8(p.bias + c, b);
-                    load8(p.gamma + c, ga);
-                    load8(p.beta + c, be);
+                for (int j = 0; j < CH / 8; ++j) rr[j] = *reinterpret_cast<const uint4 *>(res + c0 + 8 * j);
+            }
+            float v[CH];
+            tmem_ld<CH>(trow + c0, v);
 #pragma unroll
-                    for (int i = 0; i < 8; ++i) v[i] = mish_f((v[i] + b[i] - mean[g]) * rstd[g] * ga[i] + be[i]);
-                    if (film) {
-                        float sc[8], sh[8];
-                        load8(film + c, sc);
-                        load8(film + COUT + c, sh);
+            for (int i = 0; i < CH; ++i) v[i] += kc.bias[c0 + i];
+            float mean[GPC], rstd[GPC];
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] = v[i] * sc[i] + sh[i];
+            for (int g = 0; g < GPC; ++g) {
+                float s = 0.f;
+#pragma unroll
+                for (int i = 0; i < CG; ++i) s += v[g * CG + i];
+                for (int off = 1; off < Lg; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
+                mean[g] = s * inv_n;
+                float t = 0.f;
+#pragma unroll
+                for (int i = 0; i < CG; ++i) {
+                    const float d = v[g * CG + i] - mean[g];
+                    t += d * d;
+                }
+                for (int off = 1; off < Lg; off <<= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
+                rstd[g] = rsqrtf(t * inv_n + p.gn_eps);
+            }
+#pragma unroll
+            for (int i = 0; i < CH; ++i) {
+                const int g = i / CG;
+                v[i] = mish_fast((v[i] - mean[g]) * rstd[g] * kc.gamma[c0 + i] + kc.beta[c0 + i]);
+            }
+            if (film) {
+#pragma unroll
+                for (int j = 0; j < CH / 4; ++j) {
+                    v[4 * j] = v[4 * j] * fsc[j].x + fsh[j].x;
+                    v[4 * j + 1] = v[4 * j + 1] * fsc[j].y + fsh[j].y;
+                    v[4 * j + 2] = v[4 * j + 2] * fsc[j].z + fsh[j].z;
+                    v[4 * j + 3] = v[4 * j + 3] * fsc[j].w + fsh[j].w;
+                }
+            }
+            if (res) {
+#pragma unroll
+                for (int j = 0; j < CH / 8; ++j) {
+                    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&rr[j]);
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 f = __bfloat1622float2(h[e]);
+                        v[8 * j + 2 * e] += f.x;
+                        v[8 * j + 2 * e + 1] += f.y;
                     }
-                    if (p.res) {
-                        float r[8];
-                        load8_bf16(p.res + (size_t)gm * COUT + c, r);
+                }
+            }
+            if (valid) {
 #pragma unroll
-                        for (int i = 0; i < 8; ++i) v[i] += r[i];
-                    }
-                    store8_bf16(out + c, v);
+                for (int j = 0; j < CH / 8; ++j) {
+                    float y[8];
+#pragma unroll
+                    for (int e = 0; e < 8; ++e) y[e] = v[8 * j + e];
+                    store8_bf16(out + c0 + 8 * j, y);
                 }
             }
         }
     } else {
+#pragma unroll 1
+        for (int c0 = cb; c0 < cb + HALF; c0 += CH) {
+            float v[CH];
+            tmem_ld<CH>(trow + c0, v);
 #pragma unroll
-        for (int c8 = 0; c8 < HALF; c8 += 8) {
-            const int c = cb + c8;
-            float v[8];
-            tmem_ld8(trow + c, v);
-            if (valid && c < p.cout) {
+            for (int i = 0; i < CH && valid; i += 8) {
+                const int c = c0 + i;
+                if (c >= p.cout) break;
+                float y[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) v[i] += (p.bias && c + i < p.cout) ? p.bias[c + i] : 0.f;
+                for (int e = 0; e < 8; ++e) y[e] = v[i + e] + kc.bias[c + e];
                 if constexpr (MODE == kEpiBF16) {
                     __nv_bfloat16 *out = reinterpret_cast<__nv_bfloat16 *>(p.out) + (size_t)gm * p.out_ld + c;
-                    if (c + 8 <= p.cout) store8_bf16(out, v);
+                    if (c + 8 <= p.cout) store8_bf16(out, y);
                     else
-                        for (int i = 0; i < 8 && c + i < p.cout; ++i) out[i] = __float2bfloat16_rn(v[i]);
+                        for (int e = 0; e < 8 && c + e < p.cout; ++e) out[e] = __float2bfloat16_rn(y[e]);
                 } else {
                     float *out = reinterpret_cast<float *>(p.out) + (size_t)gm * p.out_ld + c;
-                    for (int i = 0; i < 8 && c + i < p.cout; ++i) out[i] = v[i];
+                    for (int e = 0; e < 8 && c + e < p.cout; ++e) out[e] = y[e];
                 }
             }
         }
@@ -288,31 +368,44 @@ __device__ __forceinline__ void epilogue(const TcParams &p, uint32_t tmem, int m
 }
 
 // ---------------------------------------------------------------- kernel
+// Persistent: one CTA per SM walks the tiles blockIdx.x, +gridDim.x, ...
+// Warp 0 (one lane) streams stages through the smem ring, warp 1 (one lane)
+// issues the MMAs of tile i into accumulator buffer i % 2, and the epilogue warps run
+// the epilogue of tile i while the MMAs of tile i + 1 fill the other buffer.
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 template <int COUT, int STAGES, int MODE>
-__global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant__ TcParams p) {
+__global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(const __grid_constant__ TcParams p) {
     constexpr int A_BYTES = kTileM * kBlockK * 2;
     constexpr int B_BYTES = COUT * kBlockK * 2;
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    constexpr uint32_t TMEM_COLS = COUT < 32 ? 32 : COUT;
+    constexpr uint32_t TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;    // two accumulator buffers
     constexpr uint32_t IDESC = bf16_idesc(kTileM, COUT);
+    constexpr int kEpiWarps = EpiShape<COUT>::EW;
     static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= 256, "MMA N");
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], done_bar;
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
     __shared__ uint32_t tmem_slot;
     __shared__ int s_issued, s_consumed, s_fail;
+    __shared__ EpiConst s_const;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * kTileM;
     const int nk = p.taps * p.c_blocks;
+    const int n_tiles = (p.M + kTileM - 1) / kTileM;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
             mbar_init(&empty_bar[s], 1);
         }
-        mbar_init(&done_bar, 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accf_bar[b], 1);
+            mbar_init(&acce_bar[b], kEpiWarps);
+        }
         s_issued = 0;
         s_consumed = 0;
         s_fail = 0;
@@ -329,60 +422,98 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_conv_tc(const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    volatile int *fail = &s_fail;
 
-    if (warp == 0 && lane == 0) {
-        // producer: one stage = the A box of (tap, channel block) and the matching weight box
-        const int sample0 = m0 / p.L;
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (kb >= STAGES && !mbar_wait(&empty_bar[s], ((kb / STAGES) - 1) & 1)) {
-                record_failure(p.err, 1);
-                s_fail = 1;
-                break;
+    if (warp == 0) {
+        if (lane == 0) {
+            // producer
+            int g = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
+                const int sample0 = tile * kTileM / p.L;
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (g >= STAGES && !mbar_wait(&empty_bar[s], ((g / STAGES) - 1) & 1)) {
+                        record_failure(p.err, 1);
+                        *fail = 1;
+                        break;
+                    }
+                    const int tap = kb / p.c_blocks, cblk = kb - tap * p.c_blocks;
+                    uint8_t *sa = smem + s * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                    if (cblk < p.c0_blocks)
+                        tma_load_3d(sa, &p.a0, &full_bar[s], cblk * kBlockK, tap - p.pad, sample0);
+                    else
+                        tma_load_3d(sa, &p.a1, &full_bar[s], (cblk - p.c0_blocks) * kBlockK, tap - p.pad, sample0);
+                    tma_load_3d(sa + A_BYTES, &p.w, &full_bar[s], cblk * kBlockK, tap, 0);
+                }
             }
-            const int tap = kb / p.c_blocks, cblk = kb - tap * p.c_blocks;
-            uint8_t *sa = smem + s * STAGE_BYTES;
-            mbar_expect_tx(&full_bar[s], STAGE_BYTES);
-            if (cblk < p.c0_blocks) tma_load_3d(sa, &p.a0, &full_bar[s], cblk * kBlockK, tap - p.pad, sample0);
-            else tma_load_3d(sa, &p.a1, &full_bar[s], (cblk - p.c0_blocks) * kBlockK, tap - p.pad, sample0);
-            tma_load_3d(sa + A_BYTES, &p.w, &full_bar[s], cblk * kBlockK, tap, 0);
+            s_issued = g;
         }
-        s_issued = kb;
-    } else if (warp == 1 && lane == 0) {
-        // MMA issuer: 4 MMAs of K = 16 per stage, the stage returned by commit
-        int kb = 0;
-        for (; kb < nk; ++kb) {
-            const int s = kb % STAGES;
-            if (!mbar_wait(&full_bar[s], (kb / STAGES) & 1)) {
-                record_failure(p.err, 2);
-                s_fail = 1;
-                break;
-            }
-            tc_fence_after();
-            const uint32_t a = smem_u32(smem + s * STAGE_BYTES), b = a + A_BYTES;
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            int g = 0, it = 0;
+            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x, ++it) {
+                const int b = it & 1;
+                if (it >= 2 && !mbar_wait(&acce_bar[b], ((it >> 1) - 1) & 1)) {
+                    record_failure(p.err, 4);
+                    *fail = 1;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * COUT);
+                for (int kb = 0; kb < nk; ++kb, ++g) {
+                    const int s = g % STAGES;
+                    if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
+                        record_failure(p.err, 2);
+                        *fail = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t a = smem_u32(smem + s * STAGE_BYTES), bb = a + A_BYTES;
 #pragma unroll
-            for (int k = 0; k < kBlockK / 16; ++k)
-                umma_bf16(tmem, sw128_desc(a + 32 * k), sw128_desc(b + 32 * k), IDESC, (kb | k) != 0);
-            umma_commit(&empty_bar[s]);
+                    for (int k = 0; k < kBlockK / 16; ++k)
+                        umma_bf16(d, sw128_desc(a + 32 * k), sw128_desc(bb + 32 * k), IDESC, (kb | k) != 0);
+                    umma_commit(&empty_bar[s]);
+                }
+                umma_commit(&accf_bar[b]);     // arrives once this tile's MMAs have completed
+            }
+            s_consumed = g;
         }
-        s_consumed = kb;
-        umma_commit(&done_bar);      // arrives once every MMA issued above has completed
+    } else {
+        // epilogue warps: TMEM lanes of quadrant warp % 4, column part (warp - 2) / 4
+        const int q = warp & 3, half = (warp - 2) >> 2;
+        for (int c = threadIdx.x - 64; c < COUT; c += 32 * kEpiWarps) {
+            s_const.bias[c] = (p.bias && c < p.cout) ? p.bias[c] : 0.f;
+            s_const.gamma[c] = p.gamma ? p.gamma[c] : 1.f;
+            s_const.beta[c] = p.beta ? p.beta[c] : 0.f;
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // epilogue warps only
+        int it = 0;
+        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const int b = it & 1;
+            if (!mbar_wait(&accf_bar[b], (it >> 1) & 1)) {
+                record_failure(p.err, 3);
+                *fail = 1;
+                break;
+            }
+            __syncwarp();                      // the tensor-memory loads are warp-collective
+            tc_fence_after();
+            if (!*fail) epilogue<COUT, MODE>(p, s_const, tmem + (uint32_t)(b * COUT), tile * kTileM, q, half, lane);
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&acce_bar[b]);
+        }
     }
-    __syncwarp();
-
-    if (!mbar_wait(&done_bar, 0)) record_failure(p.err, 3);
-    __syncwarp();                    // the tensor-memory loads below are warp-collective
-    tc_fence_after();
-    epilogue<COUT, MODE>(p, tmem, m0, warp, lane);
+    __syncthreads();
+    if (threadIdx.x == 0 && *fail) {
+        // loads issued but never consumed: let them land before the CTA leaves
+        for (int g = *(volatile int *)&s_consumed; g < *(volatile int *)&s_issued; ++g)
+            if (!mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1)) break;
+    }
     tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && *(volatile int *)&s_fail) {
-        // loads issued but never consumed: let them land before the CTA leaves
-        for (int kb = *(volatile int *)&s_consumed; kb < *(volatile int *)&s_issued; ++kb)
-            if (!mbar_wait(&full_bar[kb % STAGES], (kb / STAGES) & 1)) break;
-    }
-    __syncthreads();
+    tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
 }
@@ -429,8 +560,15 @@ int launch_tc(const TcParams &p, cudaStream_t st) {
         if (e != cudaSuccess) return (int)e;
         configured = true;
     }
-    const unsigned grid = (unsigned)((p.M + kTileM - 1) / kTileM);
-    k_conv_tc<COUT, STAGES, MODE><<<grid, kTcThreads, smem, st>>>(p);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+    }
+    const int tiles = (p.M + kTileM - 1) / kTileM;
+    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
+    k_conv_tc<COUT, STAGES, MODE><<<grid, 32 * (2 + EpiShape<COUT>::EW), smem, st>>>(p);
     return (int)cudaGetLastError();
 }
 
@@ -439,9 +577,9 @@ int launch_mode(int cout_pad, const TcParams &p, cudaStream_t st) {
     switch (cout_pad) {
         case 16:
             if constexpr (MODE == kEpiGN) return (int)cudaErrorInvalidValue;
-            else return launch_tc<16, 4, MODE>(p, st);
-        case 64: return launch_tc<64, 4, MODE>(p, st);
-        case 128: return launch_tc<128, 3, MODE>(p, st);
+            else return launch_tc<16, 8, MODE>(p, st);
+        case 64: return launch_tc<64, 8, MODE>(p, st);
+        case 128: return launch_tc<128, 6, MODE>(p, st);
         case 256: return launch_tc<256, 4, MODE>(p, st);
         default: return (int)cudaErrorInvalidValue;
     }
@@ -487,6 +625,7 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     p.res = reinterpret_cast<const __nv_bfloat16 *>(d.res_dev);
     p.out = d.out_dev;
     p.out_ld = d.out_ld;
+    p.film_ld = d.film_ld > 0 ? d.film_ld : 2 * d.cout;
     p.err = d.err_dev;
     if (p.M == 0) return cudaSuccess;
     switch (d.epilogue) {

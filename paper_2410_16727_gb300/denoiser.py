@@ -319,16 +319,19 @@ class Denoiser:
             r = x
         return self.add(h, r, tape)
 
-    def condition(self, k, qs, qg, goal, occ, tape):
-        """cond = [time MLP (sinusoid(k)), problem MLP (q_start, q_goal, goal pose),
-        occupancy encoder]; returns Mish(cond) [N][cond_dim], the input of every
-        FiLM layer."""
+    def time_embed(self, k, tape):
+        """Time-step MLP of sinusoidal features of k [R] (int32) -> [R][t_dim]."""
+        s = self.spec
+        R = k.shape[0]
+        te = torch.empty((R, s.t_sin), dtype=torch.float32, device=self.dev)
+        _nn("sinusoid", k, R, s.t_sin, te)
+        t1 = self.mish(self.linear(te, "t.l1", tape), tape)
+        return self.linear(t1, "t.l2", tape)
+
+    def problem_embed(self, qs, qg, goal, occ, tape):
+        """Problem MLP (q_start, q_goal, goal pose) and occupancy encoder -> [P][p_dim], [P][o_dim]."""
         s = self.spec
         N = qs.shape[0]
-        te = torch.empty((N, s.t_sin), dtype=torch.float32, device=self.dev)
-        _nn("sinusoid", k, N, s.t_sin, te)
-        t1 = self.mish(self.linear(te, "t.l1", tape), tape)
-        t2 = self.linear(t1, "t.l2", tape)
         pin = self.concat([qs, qg, goal], N, tape)
         p1 = self.mish(self.linear(pin, "p.l1", tape), tape)
         p2 = self.linear(p1, "p.l2", tape)
@@ -337,6 +340,15 @@ class Denoiser:
         o2 = self.gather(o1, self.map2, N, s.occ_g1 ** 3 * s.occ_c1, tape)           # [N][4^3][2^3 c1]
         o3 = self.mish(self.linear(o2, "o.c2", tape, R=N * s.occ_g2 ** 3), tape)     # [N*4^3][c2]
         o4 = self.linear(o3, "o.l", tape, R=N)                                       # flattened per sample
+        return p2, o4
+
+    def condition(self, k, qs, qg, goal, occ, tape):
+        """cond = [time MLP (sinusoid(k)), problem MLP (q_start, q_goal, goal pose),
+        occupancy encoder]; returns Mish(cond) [N][cond_dim], the input of every
+        FiLM layer."""
+        N = qs.shape[0]
+        t2 = self.time_embed(k, tape)
+        p2, o4 = self.problem_embed(qs, qg, goal, occ, tape)
         cond = self.concat([t2, p2, o4], N, tape)
         return self.mish(cond, tape)
 
@@ -428,12 +440,14 @@ class Denoiser:
         N = x.shape[0]
         P = qs.shape[0]
         rows = sample_problem if sample_problem is not None else torch.arange(N, dtype=torch.int32, device=self.dev)
+        Fs = self.film_static(qs, qg, goal, occ) if bf16 else None
         for i, kk in enumerate(ks):
-            kp = torch.full((P,), int(kk), dtype=torch.int32, device=self.dev)
-            mc_p = self.condition(kp, qs, qg, goal, occ, None)
             if bf16:
-                eps = self.unet_tc(x, N, self.film_rows(mc_p), rows)
+                k1 = torch.full((1,), int(kk), dtype=torch.int32, device=self.dev)
+                eps = self.unet_tc(x, N, self.film_add_time(Fs, k1), rows)
             else:
+                kp = torch.full((P,), int(kk), dtype=torch.int32, device=self.dev)
+                mc_p = self.condition(kp, qs, qg, goal, occ, None)
                 mc = torch.empty((N, mc_p.shape[1]), dtype=torch.float32, device=self.dev)
                 _nn("gather_rows", mc_p, rows, N, mc_p.shape[1], mc)
                 eps = self.unet(x, N, mc, None)
@@ -482,6 +496,23 @@ class Denoiser:
         for name in ("down1", "down2", "up2", "up1", "fin.c"):
             pk[name] = packed(name)
             pk[name + ".b"] = f32(name + ".b")
+        # every block's FiLM linear stacked: rows [sum 2 cout], columns split into the
+        # time-embedding part and the problem/occupancy part of the condition
+        ft_rows = sum(2 * co for _, _, co in NS.res_blocks(s))
+        Wt = torch.empty((ft_rows, s.t_dim), dtype=torch.float32, device=self.dev)
+        Wpo = torch.empty((ft_rows, s.cond_dim - s.t_dim), dtype=torch.float32, device=self.dev)
+        bf = torch.empty((ft_rows,), dtype=torch.float32, device=self.dev)
+        off = 0
+        pk["film_off"] = {}
+        for name, _, co in NS.res_blocks(s):
+            Wf = self.P(name + ".f.w")
+            _nn("copy_cols", Wf, 2 * co, s.t_dim, s.cond_dim, 0, Wt[off:], s.t_dim, 0, 0)
+            _nn("copy_cols", Wf, 2 * co, s.cond_dim - s.t_dim, s.cond_dim, s.t_dim, Wpo[off:],
+                s.cond_dim - s.t_dim, 0, 0)
+            bf[off:off + 2 * co].copy_(self.P(name + ".f.b"))
+            pk["film_off"][name] = off
+            off += 2 * co
+        pk["film_Wt"], pk["film_Wpo"], pk["film_b"], pk["film_rows"] = Wt, Wpo, bf, ft_rows
         pk["fin.o"] = packed("fin.o", rows_pad=16)
         pk["fin.o.b"] = f32("fin.o.b")
         for t in ("fin.g.w", "fin.g.b"):
@@ -489,20 +520,21 @@ class Denoiser:
         self._bf16["__tc__"] = pk
         return pk
 
-    def _tc_block(self, W, srcs, N, L, name, cin, cout, film, rows, plain_in=None):
+    def _tc_block(self, W, srcs, N, L, name, cin, cout, film, rows, plain_in=None, film_ld=0):
         """Conditional residual block: conv-GN-Mish-FiLM, conv-GN-Mish + residual,
         as two (three with a 1x1 residual projection) fused kernels."""
         s = self.spec
         a0, a1 = srcs[0], (srcs[1] if len(srcs) > 1 else None)
         gn = dict(epilogue=B.EPI_GN, rows_per_sample=L, gn_eps=s.gn_eps, cout=cout, err=self._tc_err)
+        fm = dict(film=film, film_ld=film_ld, sample_problem=rows)
         h = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
         if plain_in is not None:                      # first layer: im2col rows of the 7-channel input
             B.conv_tc(plain_in[0], W[name + ".c1"], h, n_samples=N * L, L=1, bias=W[name + ".c1.b"],
-                      gamma=W[name + ".g1.w"], beta=W[name + ".g1.b"], film=film, sample_problem=rows, **gn)
+                      gamma=W[name + ".g1.w"], beta=W[name + ".g1.b"], **fm, **gn)
         else:
             B.conv_tc(a0, W[name + ".c1"].view(cout, s.kernel, cin), h, a1=a1, n_samples=N, L=L, taps=s.kernel,
                       pad=s.kernel // 2, bias=W[name + ".c1.b"], gamma=W[name + ".g1.w"], beta=W[name + ".g1.b"],
-                      film=film, sample_problem=rows, **gn)
+                      **fm, **gn)
         if cin != cout:
             r = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
             if plain_in is not None:
@@ -543,10 +575,10 @@ class Denoiser:
         _nn("upsample2_bf16", x, N, L, C, y)
         return y
 
-    def unet_tc(self, x, N, film_p: Dict[str, torch.Tensor], rows: torch.Tensor) -> torch.Tensor:
+    def unet_tc(self, x, N, film: torch.Tensor, rows: torch.Tensor) -> torch.Tensor:
         """Predicted noise [N][T][D] (FP32) of x [N][T][D] (FP32) on the tensor
-        cores.  film_p[block] = FiLM rows [P][2 cout] per problem; rows [N] int32
-        = the problem of each sample."""
+        cores.  film [P][sum 2 cout] = every block's FiLM rows per problem (from
+        film_static / film_add_time); rows [N] int32 = the problem of each sample."""
         s = self.spec
         c1, c2, c3 = s.chans
         T, D = s.T, s.D
@@ -555,8 +587,9 @@ class Denoiser:
         _nn("im2col1d", x, N, T, D, s.kernel, 1, s.kernel // 2, T, 64, cols, 1)
         x64 = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
         _nn("im2col1d", x, N, T, D, 1, 1, 0, T, 64, x64, 1)
-        blk = lambda srcs, L, name, ci, co, plain=None: self._tc_block(W, srcs, N, L, name, ci, co, film_p[name],
-                                                                        rows, plain)
+        FT, offs = W["film_rows"], W["film_off"]
+        blk = lambda srcs, L, name, ci, co, plain=None: self._tc_block(W, srcs, N, L, name, ci, co,
+                                                                        film[:, offs[name]:], rows, plain, FT)
         h = blk([None], T, "d1a", D, c1, (cols, x64))
         h = blk([h], T, "d1b", c1, c1)
         h, L2 = self._tc_down(W, h, N, T, "down1", c1)
@@ -581,9 +614,40 @@ class Denoiser:
                   out_ld=D, err=self._tc_err)
         return out
 
-    def film_rows(self, mc_p: torch.Tensor) -> Dict[str, torch.Tensor]:
-        """FiLM scale/shift rows of every residual block from per-problem conditions."""
-        return {name: self.linear(mc_p, name + ".f", None) for name, _, _ in NS.res_blocks(self.spec)}
+    def film_static(self, qs, qg, goal, occ) -> torch.Tensor:
+        """The per-problem part of every block's FiLM rows, [P][sum 2 cout]:
+        W_f[:, problem/occupancy columns] Mish([p, o]) + b_f (the condition is
+        Mish of a concatenation, so the FiLM linear splits into a time part and
+        this part, which stays fixed over the DDIM steps)."""
+        s = self.spec
+        W = self._tc_weights()
+        P = qs.shape[0]
+        p2, o4 = self.problem_embed(qs, qg, goal, occ, None)
+        po = self.mish(self.concat([p2, o4], P, None), None)
+        F = torch.empty((P, W["film_rows"]), dtype=torch.float32, device=self.dev)
+        K = s.cond_dim - s.t_dim
+        _nn("gemm_f32", 0, 1, P, W["film_rows"], K, 1.0, po, K, W["film_Wpo"], K, 0.0, F, W["film_rows"],
+            W["film_b"])
+        return F
+
+    def film_add_time(self, Fs: torch.Tensor, k: torch.Tensor) -> torch.Tensor:
+        """FiLM rows = Fs + W_f[:, time columns] Mish(t(k)); k [1] (one step for
+        every problem, a rank-1 update) or [P] (a step per row)."""
+        s = self.spec
+        W = self._tc_weights()
+        FT = W["film_rows"]
+        mt = self.mish(self.time_embed(k, None), None)                  # [R][t_dim]
+        R = k.shape[0]
+        Ft = torch.empty((R, FT), dtype=torch.float32, device=self.dev)
+        _nn("gemm_f32", 0, 1, R, FT, s.t_dim, 1.0, mt, s.t_dim, W["film_Wt"], s.t_dim, 0.0, Ft, FT, None)
+        F = Fs.clone()
+        P = Fs.shape[0]
+        if R == 1:
+            ones = torch.ones((P, 1), dtype=torch.float32, device=self.dev)
+            _nn("gemm_f32", 0, 0, P, FT, 1, 1.0, ones, 1, Ft, FT, 1.0, F, FT, None)
+        else:
+            _nn("axpby", 1.0, Fs, 1.0, Ft, F, F.numel())
+        return F
 
     def check_tc(self):
         """Raise if a tensor-core kernel reported a pipeline wait that gave up."""
@@ -595,9 +659,9 @@ class Denoiser:
     def infer_tc(self, xk, k, qs, qg, goal, occ):
         """Predicted noise with the tensor-core U-Net (condition per sample)."""
         N = xk.shape[0]
-        mc = self.condition(k, qs, qg, goal, occ, None)
+        film = self.film_add_time(self.film_static(qs, qg, goal, occ), k)
         rows = torch.arange(N, dtype=torch.int32, device=self.dev)
-        out = self.unet_tc(xk.contiguous(), N, self.film_rows(mc), rows)
+        out = self.unet_tc(xk.contiguous(), N, film, rows)
         self.check_tc()
         return out
 

@@ -143,3 +143,32 @@ def test_rejects_bad_descriptors(gpu_lib):
     w = torch.zeros((32, 64), dtype=torch.bfloat16, device="cuda")           # cout_pad 32 unsupported
     with pytest.raises(B.DseedError):
         B.conv_tc(a, w, out, n_samples=64, L=1, cout=32, epilogue=B.EPI_F32)
+
+
+def test_persistent_tiles(gpu_lib):
+    """More tiles than SMs several times over: every CTA walks many tiles,
+    alternating its two accumulator buffers and wrapping the stage ring."""
+    rng = np.random.default_rng(11)
+    M, K, cout = 128 * 997 + 45, 128, 64
+    a = _bf(rng.normal(size=(M, K)))
+    w = _bf(rng.normal(size=(cout, K)) / np.sqrt(K))
+    bias = torch.as_tensor(rng.normal(size=cout).astype(np.float32)).cuda()
+    out = torch.full((M, cout), np.nan, dtype=torch.float32, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    B.conv_tc(a, w, out, n_samples=M, L=1, cout=cout, bias=bias, epilogue=B.EPI_F32, err=err)
+    ref = _f64(a) @ _f64(w).T + bias.cpu().double().numpy()
+    assert int(err.item()) == 0
+    assert np.abs(out.cpu().double().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+    # group-norm epilogue over many tiles (2500 trajectories of 32 rows = 625 tiles)
+    N, L, C = 2500, 32, 64
+    x = _bf(rng.normal(size=(N, L, C)))
+    w5 = _bf(rng.normal(size=(C, 5, C)) / np.sqrt(5 * C))
+    ones, zeros = torch.ones(C, device="cuda"), torch.zeros(C, device="cuda")
+    y = torch.zeros((N * L, C), dtype=torch.bfloat16, device="cuda")
+    B.conv_tc(x, w5, y, n_samples=N, L=L, taps=5, pad=2, cout=C, bias=zeros, epilogue=B.EPI_GN, rows_per_sample=L,
+              gamma=ones, beta=zeros, err=err)
+    r = _conv_ref(_f64(x), _f64(w5), 2).reshape(N, L, 8, 8)
+    r = (r - r.mean(axis=(1, 3), keepdims=True)) / np.sqrt(r.var(axis=(1, 3), keepdims=True) + 1e-5)
+    r = _mish(r.reshape(N * L, C))
+    assert int(err.item()) == 0
+    assert np.all(np.abs(_f64(y) - r) <= 8e-3 * np.abs(r) + 4e-3)
