@@ -51,6 +51,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
+    ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
+    ap.add_argument("--learned-steps", type=int, default=4000, help="denoiser training steps (batch 256)")
+    ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
     ap.add_argument("--problems", type=int, default=None,
                     help="smaller case for profiling: this many problems (and scenes) of the workload")
     return ap.parse_args()
@@ -310,6 +314,142 @@ def run_serving(args, rank: int) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------- learned proposal
+
+def run_learned(args) -> dict:
+    """Learned seeding against the plain method on held-out problems.
+
+    Training: problems on generated shelf scenes (196 per scene), solved by the
+    plain optimiser (64 random seeds x 100 iterations); the best successful
+    trajectory of each solved problem trains the denoiser (Adam, batch 256).
+    Evaluation: 512 problems on 64 unseen shelf scenes.  Offline: problems
+    solved and wall time of the plain method at several iteration budgets and of
+    DDIM proposals + 20 refinement iterations, and the plain method's result at
+    the learned pipeline's wall time.  Serving: the same problems as Poisson
+    arrivals at one offered load, plain (64 seeds x 100 iterations) vs seeded
+    (proposals on arrival + 20 iterations), p50/p99 latency and plans/s."""
+    import torch
+    from paper_2410_16727_gb300 import api, denoiser as DN, learned as L, netspec as NS, serving as SV
+
+    robot = I.make_robot()
+    planner = api.Planner(robot)
+    out = {}
+    t0 = time.perf_counter()
+    tr = L.make_problems(planner, args.learned_scenes, 196, seed=0)
+    data = L.build_dataset(planner, robot, tr)
+    torch.cuda.synchronize()
+    out["train_data"] = {"problems": int(tr.q_start.shape[0]), "trajectories": int(data.x0.shape[0]),
+                         "seconds": round(time.perf_counter() - t0, 1)}
+    net = DN.Denoiser(NS.NetSpec(), seed=0)
+    t0 = time.perf_counter()
+    losses = L.train(net, data, args.learned_steps, batch=256, lr=3e-4, log_every=max(1, args.learned_steps // 4))
+    torch.cuda.synchronize()
+    out["training"] = {"steps": args.learned_steps, "batch": 256, "params": int(net.n_params),
+                       "seconds": round(time.perf_counter() - t0, 1), "loss": [round(l, 4) for _, l in losses]}
+    del data, tr
+    te = L.make_problems(planner, 64, 8, seed=1)
+    P = int(te.q_start.shape[0])
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t
+
+    def score(o):
+        return float((o["best"] >= 0).float().mean()), float(o["success"].float().mean())
+
+    rnd = torch.as_tensor(L.random_seeds(te, robot, 64, 32, seed=5)).cuda()
+    L.solve(planner, te, rnd, 100, chunk=P)                                   # warm-up
+    plain = {}
+    for it in (100, 50, 30, 20, 10, 5):
+        o, dt = timed(lambda: L.solve(planner, te, rnd, it, chunk=P))
+        sv, ss = score(o)
+        plain[it] = {"iters": it, "solved": round(sv, 4), "seed_success": round(ss, 4), "ms": round(dt * 1e3, 2)}
+    out["heldout"] = {"problems": P, "scenes": 64, "plain_seeds": 64, "plain": list(plain.values())}
+    learned = []
+    for S, d, it in ((64, 10, 20), (12, 5, 20), (12, 5, 10)):
+        L.propose(net, robot, te, S, steps=d)                                  # warm-up
+        seeds, t_d = timed(lambda: L.propose(net, robot, te, S, steps=d))
+        o, t_p = timed(lambda: L.solve(planner, te, seeds, it, chunk=P))
+        sv, ss = score(o)
+        total = (t_d + t_p) * 1e3
+        # the plain method at the same wall time: its largest measured budget that fits
+        fit = [v for v in plain.values() if v["ms"] <= total]
+        eq = max(fit, key=lambda v: v["iters"]) if fit else None
+        learned.append({"samples": S, "ddim_steps": d, "iters": it, "solved": round(sv, 4),
+                        "seed_success": round(ss, 4), "ddim_ms": round(t_d * 1e3, 2), "plan_ms": round(t_p * 1e3, 2),
+                        "total_ms": round(total, 2),
+                        "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
+                                                if eq else None)})
+    out["heldout"]["learned"] = learned
+    # the (12, 5) proposal for all 512 problems as one CUDA-graph replay
+    gall = L.ProposalGraph(net, robot, P, 12, 5, seed=1)
+    occ_all = te.occ[te.scene_of_problem.long()]
+    gall(te.q_start, te.q_goal, te.goal, occ_all)
+    seeds, t_d = timed(lambda: gall(te.q_start, te.q_goal, te.goal, occ_all))
+    o, t_p = timed(lambda: L.solve(planner, te, seeds.contiguous(), 20, chunk=P))
+    gall.check()
+    sv_, ss_ = score(o)
+    out["heldout"]["learned_graph"] = {"samples": 12, "ddim_steps": 5, "iters": 20, "solved": round(sv_, 4),
+                                       "seed_success": round(ss_, 4), "ddim_ms": round(t_d * 1e3, 2),
+                                       "plan_ms": round(t_p * 1e3, 2), "total_ms": round((t_d + t_p) * 1e3, 2)}
+    del gall
+
+    # serving: the held-out problems as Poisson arrivals
+    budget = 16 * 10 ** 9
+    problems = [(int(te.scene_of_problem[p]), te.q_start[p].cpu().numpy(), te.goal[p].cpu().numpy())
+                for p in range(P)]
+    rng = np.random.default_rng(77)
+    n = args.learned_requests
+    reqs = [int(x) for x in rng.integers(0, P, n)]
+    rnd_host = rnd.cpu().numpy()
+
+    def server(iters):
+        sv = SV.Server(robot, budget, max_requests=4096, round_iters=10, opt=I.OptParams(iters=iters))
+        for s, (c, g) in enumerate(zip(te.cuboids, te.grids)):
+            sv.add_scene(s, c, g)
+        torch.cuda.synchronize()
+        return sv
+
+    sw = SV.ServingWorkload(robot, te.cuboids, te.grids,
+                            [SV.ServingProblem(pr[0], pr[1], pr[2], {(64, 32): rnd_host[p]}) for p, pr in
+                             enumerate(problems)], [(p, 64, 32) for p in reqs])
+    sv = server(100)
+    SV.run_trace(sv, SV.ServingWorkload(robot, te.cuboids, te.grids, sw.problems, sw.requests[:64]), None)
+    sat = SV.summarize(SV.run_trace(sv, sw, None))
+    sv.close()
+    occ = te.occ[te.scene_of_problem.long()]
+    S_l, d_l, it_l = 12, 5, 20
+    graph = L.ProposalGraphs(net, robot, (2, 8, 64), S_l, d_l)     # a group of arrivals = one replay
+
+    def propose(idx):
+        ix = torch.as_tensor(idx, dtype=torch.long, device=occ.device)
+        return graph(te.q_start[ix], te.q_goal[ix], te.goal[ix], occ[ix])
+
+    svl = server(it_l)
+    SV.run_trace_seeded(svl, problems, reqs[:64], None, propose)
+    sat_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, None, propose))
+    svl.close()
+    rate = 0.5 * sat["plans_per_s"]
+    arr = SV.poisson_arrivals(n, rate, seed=5)
+    sv = server(100)
+    res_p = SV.summarize(SV.run_trace(sv, sw, arr))
+    sv.close()
+    svl = server(it_l)
+    res_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, arr, propose))
+    svl.close()
+    graph.check()
+    out["serving"] = {"workload": f"{n} requests over the {P} held-out problems, T = 32, 16 GB budget, rounds of "
+                                  f"10 iterations; offered load = half the plain method's saturation",
+                      "plain": {"seeds": 64, "iters": 100, "saturation": sat, "at_load": res_p},
+                      "seeded": {"samples": S_l, "ddim_steps": d_l, "iters": it_l, "saturation": sat_l,
+                                 "at_load": res_l},
+                      "offered_plans_per_s": rate}
+    return out
+
+
 # ---------------------------------------------------------------------------- CPU oracle
 
 def oracle_sample(spec, budget_s: float, seed_offset: int = 0):
@@ -376,6 +516,8 @@ def main():
     res, wl = run_gpu(args, rank, world)
     if not args.no_serving:
         res["serving"] = run_serving(args, rank)
+    if rank == 0 and not args.no_learned:
+        res["learned"] = run_learned(args)
     if rank == 0 and not args.no_cpu_baseline:
         v, k, t, cores = oracle_sample(I.WORKLOADS[args.workload], args.cpu_seconds)
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",

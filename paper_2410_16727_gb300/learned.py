@@ -71,16 +71,26 @@ def occupancy(planner: api.Planner, cuboids) -> torch.Tensor:
     return occ
 
 
+_AFFINE_CACHE: dict = {}
+
+
 def _limits_affine(robot: I.Robot, dev, inverse: bool) -> torch.Tensor:
     """FiLM vector [1][14] (scale, shift) mapping joints to [-1, 1] by the
-    mechanical limits (App. A.4), or back."""
+    mechanical limits (App. A.4), or back (cached per device: no host copy
+    once built, so the proposal can be captured in a CUDA graph)."""
+    key = (robot.limits.tobytes(), str(dev), inverse)
+    t = _AFFINE_CACHE.get(key)
+    if t is not None:
+        return t
     lo = robot.limits[:, 0].astype(np.float64)
     hi = robot.limits[:, 1].astype(np.float64)
     if not inverse:
         sc, sh = 2.0 / (hi - lo), -2.0 * lo / (hi - lo) - 1.0
     else:
         sc, sh = (hi - lo) / 2.0, lo + (hi - lo) / 2.0
-    return torch.tensor(np.concatenate([sc, sh])[None], dtype=torch.float32, device=dev)
+    t = torch.tensor(np.concatenate([sc, sh])[None], dtype=torch.float32, device=dev)
+    _AFFINE_CACHE[key] = t
+    return t
 
 
 def normalise(robot, q: torch.Tensor, inverse: bool = False) -> torch.Tensor:
@@ -96,13 +106,16 @@ def linear_path(qs_n: torch.Tensor, qg_n: torch.Tensor, T: int) -> torch.Tensor:
     normalised start and goal configurations: one GEMM of [q_s, q_g] against
     the constant interpolation matrix [14][T*7]."""
     N, D = qs_n.shape
-    tau = np.arange(1, T + 1, dtype=np.float64) / T
-    W = np.zeros((2 * D, T * D), np.float32)
-    for t in range(T):
-        for d in range(D):
-            W[d, t * D + d] = 1.0 - tau[t]
-            W[D + d, t * D + d] = tau[t]
-    W = torch.from_numpy(W).to(qs_n.device)
+    key = ("lin", T, D, str(qs_n.device))
+    W = _AFFINE_CACHE.get(key)
+    if W is None:
+        tau = np.arange(1, T + 1, dtype=np.float64) / T
+        Wh = np.zeros((2 * D, T * D), np.float32)
+        for t in range(T):
+            for d in range(D):
+                Wh[d, t * D + d] = 1.0 - tau[t]
+                Wh[D + d, t * D + d] = tau[t]
+        W = _AFFINE_CACHE[key] = torch.from_numpy(Wh).to(qs_n.device)
     A = torch.cat([qs_n, qg_n], 1).contiguous()
     out = torch.empty((N, T, D), dtype=torch.float32, device=qs_n.device)
     _nn("gemm_f32", 0, 0, N, T * D, 2 * D, 1.0, A, 2 * D, W, T * D, 0.0, out, T * D, None)
@@ -264,26 +277,109 @@ def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: flo
     return losses
 
 
-def propose(net: DN.Denoiser, robot: I.Robot, ps: ProblemSet, S: int, steps: int = 10, seed: int = 0,
-            bf16: bool = True) -> torch.Tensor:
-    """DDIM proposals: S seed trajectories per problem, [P][S][T][7] in joint
-    space.  DDIM generates the scaled residual from the straight start-goal
-    path, which is added back; the result is clipped to the joint limits like
-    the random seeds, then un-normalised."""
-    P = ps.q_start.shape[0]
-    dev = ps.q_start.device
+def _propose_core(net: DN.Denoiser, robot: I.Robot, q_start, q_goal, goal, occ, noise, rows, steps: int,
+                  bf16: bool, check: bool) -> torch.Tensor:
+    qs = normalise(robot, q_start.contiguous())
+    qg = normalise(robot, q_goal.contiguous())
+    r = net.ddim_sample(qs, qg, goal.contiguous(), occ.contiguous(), noise, steps=steps, bf16=bf16,
+                        sample_problem=rows, check=check)
+    lin = linear_path(qs, qg, net.spec.T)[rows.long()]
+    x = from_residual(r, lin)
+    _nn("clamp_affine", x, 1.0, 0.0, -1.0, 1.0, x, x.numel())
+    P, S = q_start.shape[0], noise.shape[0] // q_start.shape[0]
+    return normalise(robot, x, inverse=True).view(P, S, net.spec.T, net.spec.D)
+
+
+def propose_for(net: DN.Denoiser, robot: I.Robot, q_start: torch.Tensor, q_goal: torch.Tensor, goal: torch.Tensor,
+                occ: torch.Tensor, S: int, steps: int = 10, seed: int = 0, bf16: bool = True) -> torch.Tensor:
+    """DDIM proposals for P problems given as device tensors (q_start, q_goal,
+    goal [P][7], occupancy rows [P][32^3]): S seed trajectories per problem,
+    [P][S][T][7] in joint space.  DDIM generates the scaled residual from the
+    straight start-goal path, which is added back; the result is clipped to
+    the joint limits like the random seeds, then un-normalised."""
+    P = q_start.shape[0]
+    dev = q_start.device
     g = torch.Generator(device=dev)
     g.manual_seed(1000 + seed)
     noise = torch.randn((P * S, net.spec.T, net.spec.D), device=dev, generator=g)
     rows = torch.arange(P, device=dev, dtype=torch.int32).repeat_interleave(S)
-    qs = normalise(robot, ps.q_start.contiguous())
-    qg = normalise(robot, ps.q_goal.contiguous())
-    occ = ps.occ[ps.scene_of_problem.long()].contiguous()
-    r = net.ddim_sample(qs, qg, ps.goal.contiguous(), occ, noise, steps=steps, bf16=bf16, sample_problem=rows)
-    lin = linear_path(qs, qg, net.spec.T)[rows.long()]
-    x = from_residual(r, lin)
-    _nn("clamp_affine", x, 1.0, 0.0, -1.0, 1.0, x, x.numel())
-    return normalise(robot, x, inverse=True).view(P, S, net.spec.T, net.spec.D)
+    return _propose_core(net, robot, q_start, q_goal, goal, occ, noise, rows, steps, bf16, True)
+
+
+class ProposalGraph:
+    """DDIM proposals for up to G problems captured once as a CUDA graph over
+    static buffers: the launch sequence of a fixed group size never changes,
+    so a replay replaces the host cost of issuing every kernel of the U-Net at
+    every step (a serving loop proposes for each group of arrivals).  Call with
+    g <= G problems; rows past g compute on stale inputs and are not returned."""
+
+    def __init__(self, net: DN.Denoiser, robot: I.Robot, G: int, S: int, steps: int, seed: int = 0):
+        dev = net.dev
+        s = net.spec
+        self.G, self.S, self.net = G, S, net
+        self.q_start = torch.zeros((G, 7), device=dev)
+        self.q_goal = torch.zeros((G, 7), device=dev)
+        self.goal = torch.zeros((G, 7), device=dev)
+        self.goal[:, 3] = 1.0
+        self.occ = torch.zeros((G, s.occ_n ** 3), device=dev)
+        self.noise = torch.zeros((G * S, s.T, s.D), device=dev)
+        self.rows = torch.arange(G, device=dev, dtype=torch.int32).repeat_interleave(S)
+        self.gen = torch.Generator(device=dev)
+        self.gen.manual_seed(2000 + seed)
+        args = (net, robot, self.q_start, self.q_goal, self.goal, self.occ, self.noise, self.rows, steps, True, False)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):                  # warm-up outside the capture (weight caches, constants)
+            _propose_core(*args)
+        torch.cuda.current_stream().wait_stream(side)
+        torch.cuda.synchronize()
+        self.weights = net._tc_weights()              # the buffers the graph reads; kept alive here
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.out = _propose_core(*args)
+        torch.cuda.synchronize()
+
+    def __call__(self, q_start, q_goal, goal, occ) -> torch.Tensor:
+        g = q_start.shape[0]
+        if self.net._tc_weights() is not self.weights:
+            raise RuntimeError("the denoiser's parameters changed after capture: build a new ProposalGraph")
+        if g > self.G:
+            raise ValueError(f"group of {g} problems exceeds the captured size {self.G}")
+        self.q_start[:g].copy_(q_start)
+        self.q_goal[:g].copy_(q_goal)
+        self.goal[:g].copy_(goal)
+        self.occ[:g].copy_(occ)
+        torch.randn(self.noise.shape, device=self.noise.device, generator=self.gen, out=self.noise)
+        self.graph.replay()
+        return self.out[:g]
+
+    def check(self):
+        self.net.check_tc()
+
+
+class ProposalGraphs:
+    """Several captured group sizes; a group of g problems replays the
+    smallest graph with G >= g (less padded work for small groups)."""
+
+    def __init__(self, net: DN.Denoiser, robot: I.Robot, sizes, S: int, steps: int, seed: int = 0):
+        self.graphs = [ProposalGraph(net, robot, G, S, steps, seed + i) for i, G in enumerate(sorted(sizes))]
+
+    def __call__(self, q_start, q_goal, goal, occ) -> torch.Tensor:
+        g = q_start.shape[0]
+        for pg in self.graphs:
+            if g <= pg.G:
+                return pg(q_start, q_goal, goal, occ)
+        raise ValueError(f"group of {g} problems exceeds the largest captured size {self.graphs[-1].G}")
+
+    def check(self):
+        self.graphs[0].check()
+
+
+def propose(net: DN.Denoiser, robot: I.Robot, ps: ProblemSet, S: int, steps: int = 10, seed: int = 0,
+            bf16: bool = True) -> torch.Tensor:
+    """DDIM proposals for every problem of a problem set: [P][S][T][7]."""
+    occ = ps.occ[ps.scene_of_problem.long()]
+    return propose_for(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, S, steps, seed, bf16)
 
 
 def evaluate(planner: api.Planner, ps: ProblemSet, seeds, iters: int) -> dict:

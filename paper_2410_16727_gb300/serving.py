@@ -224,7 +224,7 @@ def run_trace(server: Server, wl: ServingWorkload, arrivals: Optional[np.ndarray
                 st, ts, td = server.poll(t)
                 if st == 2 or st == -1:
                     k, S, T, out = open_t.pop(t)
-                    lat[k] = td - ts
+                    lat[k] = td - min(ts, t0 + arr[k])        # from the request's arrival
                     if st == 2:
                         sc = out["success"].numpy()
                         succ_seeds += int(sc.sum())
@@ -256,3 +256,75 @@ def summarize(res: dict) -> dict:
     return dict(plans_per_s=res["plans_per_s"], p50_ms=float(np.nanpercentile(lat, 50) * 1e3),
                 p99_ms=float(np.nanpercentile(lat, 99) * 1e3), mean_ms=float(np.nanmean(lat) * 1e3),
                 seed_success=res["seed_success"], problems_solved=res["problems_solved"], rounds=res["rounds"])
+
+
+def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequence[int], arrivals: Optional[np.ndarray],
+                     propose: Callable[[List[int]], torch.Tensor], max_group: int = 64,
+                     timeout_s: float = 600.0) -> dict:
+    """Replay requests whose seeds are proposed on the GPU when they arrive
+    (the learned seeding): problems[p] = (scene_id, q_start [7], goal [7]);
+    requests[i] = problem index.  Arrived requests are grouped (up to
+    max_group), propose(problem indices) enqueues their seeds [g][S][T][7] on
+    the current stream (overlapping the server's own stream), the seeds are
+    copied to pinned host memory, and each request is submitted once its copy
+    has landed.  Latency runs from the arrival to the server's completion, so
+    it includes the proposal."""
+    n = len(requests)
+    arr = np.zeros(n) if arrivals is None else np.asarray(arrivals, np.float64)
+    pin = {p: (torch.as_tensor(np.asarray(q, np.float32)).pin_memory(),
+               torch.as_tensor(np.asarray(g, np.float32)).pin_memory()) for p, (_, q, g) in enumerate(problems)}
+    lat = np.full(n, np.nan)
+    waiting: List[int] = []
+    props: List[tuple] = []
+    open_t: Dict[int, tuple] = {}
+    succ_seeds = tot_seeds = solved = 0
+    i = done = 0
+    t0 = time.monotonic()
+    t_first, t_last = None, t0
+    while done < n:
+        now = time.monotonic() - t0
+        while i < n and arr[i] <= now:
+            waiting.append(i)
+            if t_first is None:
+                t_first = time.monotonic()
+            i += 1
+        if waiting and len(props) < 2:
+            grp, waiting = waiting[:max_group], waiting[max_group:]
+            seeds = propose([requests[k] for k in grp])
+            host = torch.empty(seeds.shape, dtype=torch.float32).pin_memory()
+            host.copy_(seeds, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record()
+            props.append((ev, grp, host))
+        while props and props[0][0].query():
+            _, grp, host = props.pop(0)
+            for j, k in enumerate(grp):
+                p = requests[k]
+                S, T = int(host.shape[1]), int(host.shape[2])
+                out = alloc_outputs(S, T)
+                ins = dict(q=pin[p][0], g=pin[p][1], s=host[j])
+                t = server.submit_pinned(problems[p][0], ins, out)
+                open_t[t] = (k, S, out)
+        nd = server.step(wait=False)
+        if nd:
+            for t in list(open_t.keys()):
+                st, ts, td = server.poll(t)
+                if st == 2 or st == -1:
+                    k, S, out = open_t.pop(t)
+                    lat[k] = td - (t0 + arr[k])
+                    if st == 2:
+                        succ_seeds += int(out["success"].numpy().sum())
+                        tot_seeds += S
+                        solved += int(out["best"][0] >= 0)
+                    server.release(t)
+                    done += 1
+                    t_last = time.monotonic()
+        if time.monotonic() - t0 > timeout_s:
+            raise TimeoutError(f"trace did not finish: {done} of {n} done")
+        if nd == 0 and i < n and not open_t and not props and not waiting:
+            time.sleep(max(0.0, min(arr[i] - (time.monotonic() - t0), 0.001)))
+    span = t_last - (t_first if t_first is not None else t0)
+    st = server.stats()
+    return dict(latency_s=lat, plans_per_s=n / span if span > 0 else float("inf"), span_s=span,
+                seed_success=succ_seeds / max(tot_seeds, 1), problems_solved=solved / n,
+                rounds=int(st.rounds), arena_peak=int(st.arena_peak))

@@ -70,3 +70,21 @@ def test_checkpoint_round_trip(trained):
     a = L.propose(net, robot, te, 4, steps=5, seed=3)
     b = L.propose(other, robot, te, 4, steps=5, seed=3)
     assert torch.equal(a, b)
+
+
+def test_proposal_graph_matches_direct_calls(trained):
+    """The CUDA-graph proposal (fixed group size, padded) returns what the
+    direct calls return for the same problems and noise."""
+    robot, planner, tr, data, net, losses, te = trained
+    occ = te.occ[te.scene_of_problem.long()]
+    graphs = L.ProposalGraphs(net, robot, (4, 16), S=6, steps=4)
+    for g in (3, 4, 11):
+        got = graphs(te.q_start[:g], te.q_goal[:g], te.goal[:g], occ[:g]).clone()
+        pg = next(x for x in graphs.graphs if g <= x.G)
+        noise = pg.noise[:g * 6].clone()
+        rows = torch.arange(g, device="cuda", dtype=torch.int32).repeat_interleave(6)
+        want = L._propose_core(net, robot, te.q_start[:g], te.q_goal[:g], te.goal[:g], occ[:g], noise, rows, 4,
+                               True, True)
+        assert got.shape == want.shape
+        assert float((got - want).abs().max()) <= 1e-5
+    graphs.check()
