@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
-    ap.add_argument("--learned-steps", type=int, default=4000, help="denoiser training steps (batch 256)")
+    ap.add_argument("--learned-steps", type=int, default=6000, help="denoiser training steps (batch 256)")
     ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
     ap.add_argument("--problems", type=int, default=None,
                     help="smaller case for profiling: this many problems (and scenes) of the workload")
@@ -407,7 +407,9 @@ def run_learned(args) -> dict:
     rnd_host = rnd.cpu().numpy()
 
     def server(iters):
-        sv = SV.Server(robot, budget, max_requests=4096, round_iters=10, opt=I.OptParams(iters=iters))
+        # rounds of 10 iterations let new requests join a 100-iteration batch; a
+        # 20-iteration seeded request runs in one round
+        sv = SV.Server(robot, budget, max_requests=4096, round_iters=min(iters, 20), opt=I.OptParams(iters=iters))
         for s, (c, g) in enumerate(zip(te.cuboids, te.grids)):
             sv.add_scene(s, c, g)
         torch.cuda.synchronize()
@@ -442,7 +444,7 @@ def run_learned(args) -> dict:
     svl.close()
     graph.check()
     out["serving"] = {"workload": f"{n} requests over the {P} held-out problems, T = 32, 16 GB budget, rounds of "
-                                  f"10 iterations; offered load = half the plain method's saturation",
+                                  f"20 iterations; offered load = half the plain method's saturation",
                       "plain": {"seeds": 64, "iters": 100, "saturation": sat, "at_load": res_p},
                       "seeded": {"samples": S_l, "ddim_steps": d_l, "iters": it_l, "saturation": sat_l,
                                  "at_load": res_l},

@@ -484,7 +484,8 @@ int dseed_nn_to_bf16(const float *x_dev, void *y_dev, long long n, cudaStream_t 
  * epilogue 2: y = Mish(GroupNorm(out)) over groups of cout / 8 channels and
  *   rows_per_sample consecutive rows (affine gamma, beta; biased variance, eps
  *   gn_eps); then y = y * film[s][o] + film[s][cout + o] when film_dev is given
- *   (rows film_ld floats apart; s = sample_problem[row / rows_per_sample], or
+ *   (rows film_ld floats apart, plus film_add[o] / film_add[cout + o] when
+ *   film_add_dev is given; s = sample_problem[row / rows_per_sample], or
  *   row / rows_per_sample when sample_problem_dev is NULL); then y += res[row][o] (BF16 [..][cout]) when
  *   res_dev is given; out BF16 [..][out_ld].  Needs cout = cout_pad.
  *
@@ -510,6 +511,7 @@ typedef struct {
     const float *gamma_dev, *beta_dev;
     const float *film_dev;
     int film_ld;             /* floats between FiLM rows (0: 2 cout) */
+    const float *film_add_dev;   /* optional [2 cout], added to every FiLM row */
     const int *sample_problem_dev;
     const void *res_dev;
     void *out_dev;

@@ -84,7 +84,7 @@ class ConvTc(C.Structure):
                 ("w_dev", C.c_void_p), ("cout", C.c_int), ("cout_pad", C.c_int), ("bias_dev", C.c_void_p),
                 ("epilogue", C.c_int), ("rows_per_sample", C.c_int), ("gn_eps", C.c_float),
                 ("gamma_dev", C.c_void_p), ("beta_dev", C.c_void_p), ("film_dev", C.c_void_p),
-                ("film_ld", C.c_int), ("sample_problem_dev", C.c_void_p), ("res_dev", C.c_void_p), ("out_dev", C.c_void_p),
+                ("film_ld", C.c_int), ("film_add_dev", C.c_void_p), ("sample_problem_dev", C.c_void_p), ("res_dev", C.c_void_p), ("out_dev", C.c_void_p),
                 ("out_ld", C.c_int), ("err_dev", C.c_void_p)]
 
 
@@ -601,7 +601,7 @@ def conv_tc(a0: torch.Tensor, w: torch.Tensor, out: torch.Tensor, *, n_samples: 
             gamma: Optional[torch.Tensor] = None, beta: Optional[torch.Tensor] = None,
             film: Optional[torch.Tensor] = None, sample_problem: Optional[torch.Tensor] = None,
             res: Optional[torch.Tensor] = None, out_ld: Optional[int] = None, err: Optional[torch.Tensor] = None,
-            film_ld: int = 0):
+            film_ld: int = 0, film_add: Optional[torch.Tensor] = None):
     """dseed_nn_conv_tc: tensor-core convolution with a fused layer tail.
     a0 / a1 BF16 [n_samples][L][c] (channels-last, contiguous); w BF16
     [cout_pad][taps][c0 + c1]; out [n_samples * L][out_ld] (FP32 for EPI_F32)."""
@@ -631,6 +631,10 @@ def conv_tc(a0: torch.Tensor, w: torch.Tensor, out: torch.Tensor, *, n_samples: 
     else:
         d.film_dev = ptr(film, "film", torch.float32)
     d.film_ld = int(film_ld)
+    if film_add is not None:
+        if not film_add.is_cuda or film_add.dtype != torch.float32 or film_add.stride(-1) != 1:
+            raise DseedError("conv_tc: film_add must be FP32 CUDA values")
+        d.film_add_dev = film_add.data_ptr()       # may be a column slice of a wider row
     d.sample_problem_dev = ptr(sample_problem, "sample_problem", torch.int32)
     d.res_dev = ptr(res, "res", torch.bfloat16)
     d.out_dev = ptr(out, "out", torch.float32 if epilogue == EPI_F32 else torch.bfloat16)

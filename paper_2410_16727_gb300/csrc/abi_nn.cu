@@ -213,7 +213,8 @@ int dseed_nn_conv_tc(const DseedConvTc *d, cudaStream_t stream) {
     NEED(d->epilogue >= 0 && d->epilogue <= 2, "conv_tc: bad epilogue");
     NEED(d->a0_dev && d->w_dev && d->out_dev && (d->c1 == 0 || d->a1_dev), "conv_tc: NULL operand");
     NEED(al16(d->a0_dev) && al16(d->a1_dev) && al16(d->w_dev) && al16(d->out_dev) && al16(d->bias_dev) &&
-             al16(d->gamma_dev) && al16(d->beta_dev) && al16(d->film_dev) && al16(d->res_dev),
+             al16(d->gamma_dev) && al16(d->beta_dev) && al16(d->film_dev) && al16(d->res_dev) &&
+             al16(d->film_add_dev),
          "conv_tc: pointers must be 16-byte aligned");
     if (d->epilogue >= 1) NEED(d->out_ld % 8 == 0, "conv_tc: BF16 output rows must be multiples of 8");
     if (d->epilogue == 2) {

@@ -47,7 +47,7 @@ struct TcParams {
     int M, L, taps, pad, c0_blocks, c_blocks;
     int cout, rows_per_sample;
     float gn_eps;
-    const float *bias, *gamma, *beta, *film;
+    const float *bias, *gamma, *beta, *film, *film_add;
     const int *sample_problem;
     const __nv_bfloat16 *res;
     void *out;
@@ -278,6 +278,15 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
                 for (int j = 0; j < CH / 4; ++j) {
                     fsc[j] = *reinterpret_cast<const float4 *>(film + c0 + 4 * j);
                     fsh[j] = *reinterpret_cast<const float4 *>(film + COUT + c0 + 4 * j);
+                }
+                if (p.film_add) {
+#pragma unroll
+                    for (int j = 0; j < CH / 4; ++j) {
+                        const float4 a = *reinterpret_cast<const float4 *>(p.film_add + c0 + 4 * j);
+                        const float4 b = *reinterpret_cast<const float4 *>(p.film_add + COUT + c0 + 4 * j);
+                        fsc[j].x += a.x; fsc[j].y += a.y; fsc[j].z += a.z; fsc[j].w += a.w;
+                        fsh[j].x += b.x; fsh[j].y += b.y; fsh[j].z += b.z; fsh[j].w += b.w;
+                    }
                 }
             }
             if (res) {
@@ -621,6 +630,7 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     p.gamma = d.gamma_dev;
     p.beta = d.beta_dev;
     p.film = d.film_dev;
+    p.film_add = d.film_add_dev;
     p.sample_problem = d.sample_problem_dev;
     p.res = reinterpret_cast<const __nv_bfloat16 *>(d.res_dev);
     p.out = d.out_dev;

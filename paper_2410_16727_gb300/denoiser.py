@@ -79,6 +79,7 @@ class Denoiser:
         self.abar_host = cosine_abar(spec.K)
         self._bf16: Dict[str, torch.Tensor] = {}
         self._tc_err = torch.zeros(1, dtype=torch.int32, device=self.dev)
+        self._ks_cache: Dict[int, torch.Tensor] = {}
         self.init_params(seed)
 
     # ------------------------------------------------------------------ parameters
@@ -441,11 +442,15 @@ class Denoiser:
         N = x.shape[0]
         P = qs.shape[0]
         rows = sample_problem if sample_problem is not None else torch.arange(N, dtype=torch.int32, device=self.dev)
-        Fs = self.film_static(qs, qg, goal, occ) if bf16 else None
+        if bf16:
+            Fs = self.film_static(qs, qg, goal, occ)
+            kdev = self._ks_cache.get(steps)
+            if kdev is None:                 # made once, outside any graph capture (no host copy inside one)
+                kdev = self._ks_cache[steps] = torch.tensor(ks, dtype=torch.int32).to(self.dev)
+            Ft = self.film_time_rows(kdev)
         for i, kk in enumerate(ks):
             if bf16:
-                k1 = torch.full((1,), int(kk), dtype=torch.int32, device=self.dev)
-                eps = self.unet_tc(x, N, self.film_add_time(Fs, k1), rows)
+                eps = self.unet_tc(x, N, Fs, rows, film_add=Ft[i])
             else:
                 kp = torch.full((P,), int(kk), dtype=torch.int32, device=self.dev)
                 mc_p = self.condition(kp, qs, qg, goal, occ, None)
@@ -521,13 +526,13 @@ class Denoiser:
         self._bf16["__tc__"] = pk
         return pk
 
-    def _tc_block(self, W, srcs, N, L, name, cin, cout, film, rows, plain_in=None, film_ld=0):
+    def _tc_block(self, W, srcs, N, L, name, cin, cout, film, rows, plain_in=None, film_ld=0, film_add=None):
         """Conditional residual block: conv-GN-Mish-FiLM, conv-GN-Mish + residual,
         as two (three with a 1x1 residual projection) fused kernels."""
         s = self.spec
         a0, a1 = srcs[0], (srcs[1] if len(srcs) > 1 else None)
         gn = dict(epilogue=B.EPI_GN, rows_per_sample=L, gn_eps=s.gn_eps, cout=cout, err=self._tc_err)
-        fm = dict(film=film, film_ld=film_ld, sample_problem=rows)
+        fm = dict(film=film, film_ld=film_ld, sample_problem=rows, film_add=film_add)
         h = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
         if plain_in is not None:                      # first layer: im2col rows of the 7-channel input
             B.conv_tc(plain_in[0], W[name + ".c1"], h, n_samples=N * L, L=1, bias=W[name + ".c1.b"],
@@ -576,10 +581,13 @@ class Denoiser:
         _nn("upsample2_bf16", x, N, L, C, y)
         return y
 
-    def unet_tc(self, x, N, film: torch.Tensor, rows: torch.Tensor) -> torch.Tensor:
+    def unet_tc(self, x, N, film: torch.Tensor, rows: torch.Tensor,
+                film_add: Optional[torch.Tensor] = None) -> torch.Tensor:
         """Predicted noise [N][T][D] (FP32) of x [N][T][D] (FP32) on the tensor
         cores.  film [P][sum 2 cout] = every block's FiLM rows per problem (from
-        film_static / film_add_time); rows [N] int32 = the problem of each sample."""
+        film_static / film_add_time); film_add [sum 2 cout] (optional) is added
+        to every row (the time part shared by all problems at one DDIM step);
+        rows [N] int32 = the problem of each sample."""
         s = self.spec
         c1, c2, c3 = s.chans
         T, D = s.T, s.D
@@ -589,8 +597,10 @@ class Denoiser:
         x64 = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
         _nn("im2col1d", x, N, T, D, 1, 1, 0, T, 64, x64, 1)
         FT, offs = W["film_rows"], W["film_off"]
+        fa = (lambda name: film_add[offs[name]:]) if film_add is not None else (lambda name: None)
         blk = lambda srcs, L, name, ci, co, plain=None: self._tc_block(W, srcs, N, L, name, ci, co,
-                                                                        film[:, offs[name]:], rows, plain, FT)
+                                                                        film[:, offs[name]:], rows, plain, FT,
+                                                                        fa(name))
         h = blk([None], T, "d1a", D, c1, (cols, x64))
         h = blk([h], T, "d1b", c1, c1)
         h, L2 = self._tc_down(W, h, N, T, "down1", c1)
@@ -630,6 +640,18 @@ class Denoiser:
         _nn("gemm_f32", 0, 1, P, W["film_rows"], K, 1.0, po, K, W["film_Wpo"], K, 0.0, F, W["film_rows"],
             W["film_b"])
         return F
+
+    def film_time_rows(self, k: torch.Tensor) -> torch.Tensor:
+        """The time part of every block's FiLM rows, W_f[:, time columns]
+        Mish(t(k)), for a vector of steps k [R]: [R][sum 2 cout]."""
+        s = self.spec
+        W = self._tc_weights()
+        FT = W["film_rows"]
+        mt = self.mish(self.time_embed(k, None), None)
+        R = k.shape[0]
+        Ft = torch.empty((R, FT), dtype=torch.float32, device=self.dev)
+        _nn("gemm_f32", 0, 1, R, FT, s.t_dim, 1.0, mt, s.t_dim, W["film_Wt"], s.t_dim, 0.0, Ft, FT, None)
+        return Ft
 
     def film_add_time(self, Fs: torch.Tensor, k: torch.Tensor) -> torch.Tensor:
         """FiLM rows = Fs + W_f[:, time columns] Mish(t(k)); k [1] (one step for

@@ -268,7 +268,8 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
     the current stream (overlapping the server's own stream), the seeds are
     copied to pinned host memory, and each request is submitted once its copy
     has landed.  Latency runs from the arrival to the server's completion, so
-    it includes the proposal."""
+    it includes the proposal.  Pinned buffers come from pools (allocating
+    pinned memory can synchronise the device)."""
     n = len(requests)
     arr = np.zeros(n) if arrivals is None else np.asarray(arrivals, np.float64)
     pin = {p: (torch.as_tensor(np.asarray(q, np.float32)).pin_memory(),
@@ -277,6 +278,9 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
     waiting: List[int] = []
     props: List[tuple] = []
     open_t: Dict[int, tuple] = {}
+    free_out: Dict[tuple, list] = {}
+    free_blocks: Dict[tuple, list] = {}
+    refs: Dict[int, list] = {}                    # id(block) -> [block, requests still using it]
     succ_seeds = tot_seeds = solved = 0
     i = done = 0
     t0 = time.monotonic()
@@ -291,32 +295,42 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
         if waiting and len(props) < 2:
             grp, waiting = waiting[:max_group], waiting[max_group:]
             seeds = propose([requests[k] for k in grp])
-            host = torch.empty(seeds.shape, dtype=torch.float32).pin_memory()
-            host.copy_(seeds, non_blocking=True)
+            key = tuple(seeds.shape[1:])
+            lst = free_blocks.setdefault(key, [])
+            block = lst.pop() if lst else torch.empty((max_group,) + key, dtype=torch.float32).pin_memory()
+            block[:len(grp)].copy_(seeds, non_blocking=True)
             ev = torch.cuda.Event()
             ev.record()
-            props.append((ev, grp, host))
+            props.append((ev, grp, block))
         while props and props[0][0].query():
-            _, grp, host = props.pop(0)
+            _, grp, block = props.pop(0)
+            refs[id(block)] = [block, len(grp)]
+            S, T = int(block.shape[1]), int(block.shape[2])
             for j, k in enumerate(grp):
                 p = requests[k]
-                S, T = int(host.shape[1]), int(host.shape[2])
-                out = alloc_outputs(S, T)
-                ins = dict(q=pin[p][0], g=pin[p][1], s=host[j])
+                lo = free_out.setdefault((S, T), [])
+                out = lo.pop() if lo else alloc_outputs(S, T)
+                ins = dict(q=pin[p][0], g=pin[p][1], s=block[j])
                 t = server.submit_pinned(problems[p][0], ins, out)
-                open_t[t] = (k, S, out)
+                open_t[t] = (k, S, T, out, block)
         nd = server.step(wait=False)
         if nd:
             for t in list(open_t.keys()):
                 st, ts, td = server.poll(t)
                 if st == 2 or st == -1:
-                    k, S, out = open_t.pop(t)
+                    k, S, T, out, block = open_t.pop(t)
                     lat[k] = td - (t0 + arr[k])
                     if st == 2:
                         succ_seeds += int(out["success"].numpy().sum())
                         tot_seeds += S
                         solved += int(out["best"][0] >= 0)
                     server.release(t)
+                    free_out[(S, T)].append(out)
+                    r = refs[id(block)]
+                    r[1] -= 1
+                    if r[1] == 0:
+                        del refs[id(block)]
+                        free_blocks[tuple(block.shape[1:])].append(block)
                     done += 1
                     t_last = time.monotonic()
         if time.monotonic() - t0 > timeout_s:
