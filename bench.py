@@ -37,6 +37,11 @@ UNIT = "ST-evals/s"
 FLOP_PER_ST = 5800.0
 # 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one k_plan launch per problem of the batched workload
+# (64 seeds x 32 waypoints x 100 iterations, 128^3 shelf ESDF): ncu capture of the
+# 32-problem case, 35.43 MB per launch (profiles/k_plan_batched_small.md), scaled
+# by the problems processed.
+K_PLAN_DRAM_BYTES_PER_PROBLEM = 35.43e6 / 32
 
 
 def parse():
@@ -261,7 +266,9 @@ def run_gpu(args, rank: int, world: int):
         roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                  "traffic": None},
+                  "traffic": (K_PLAN_DRAM_BYTES_PER_PROBLEM * P
+                              if spec.name == "batched" and S == 64 and T == 32 and iters == 100 else None),
+                  "traffic_source": "ncu dram__bytes_read+write of a 32-problem launch, scaled by problems"},
         clocks=sampler.summary(),
     )
     return res, wl

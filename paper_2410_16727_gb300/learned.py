@@ -390,3 +390,43 @@ def evaluate(planner: api.Planner, ps: ProblemSet, seeds, iters: int) -> dict:
     dt = time.perf_counter() - t0
     return dict(problems_solved=float((out["best"] >= 0).float().mean()),
                 seed_success=float(out["success"].float().mean()), plan_s=dt)
+
+
+def main(argv=None):
+    """Time DDIM proposals on generated shelf problems (untrained weights: the
+    timing does not depend on them): python -m paper_2410_16727_gb300.learned
+    --problems 512 --samples 64 --ddim-steps 10."""
+    import argparse
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--problems", type=int, default=512, help="problems (8 per scene)")
+    ap.add_argument("--samples", type=int, default=64)
+    ap.add_argument("--ddim-steps", type=int, default=10)
+    ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--graph", action="store_true", help="replay a captured CUDA graph")
+    a = ap.parse_args(argv)
+    robot = I.make_robot()
+    planner = api.Planner(robot)
+    ps = make_problems(planner, max(1, a.problems // 8), 8, seed=1)
+    net = DN.Denoiser(NS.NetSpec(), seed=0)
+    occ = ps.occ[ps.scene_of_problem.long()]
+    if a.graph:
+        pg = ProposalGraph(net, robot, ps.q_start.shape[0], a.samples, a.ddim_steps)
+        run = lambda: pg(ps.q_start, ps.q_goal, ps.goal, occ)
+    else:
+        run = lambda: propose_for(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, a.samples, a.ddim_steps)
+    run()
+    times = []
+    for _ in range(a.repeat):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        run()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t)
+    net.check_tc()
+    n = ps.q_start.shape[0] * a.samples
+    print(f"DDIM proposal: {ps.q_start.shape[0]} problems x {a.samples} samples = {n} trajectories, "
+          f"{a.ddim_steps} steps: {min(times) * 1e3:.2f} ms ({min(times) / a.ddim_steps * 1e3:.2f} ms per step)")
+
+
+if __name__ == "__main__":
+    main()
