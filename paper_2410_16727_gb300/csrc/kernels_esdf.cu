@@ -7,7 +7,7 @@
 // deepest-penetration reading of min_k sdf_k); otherwise min_k sdf_k is the
 // square root of the former.  Both equal min_k sdf_k exactly.
 //
-// One block owns an 8x8x8 tile of voxels (one thread per voxel) of one scene;
+// One block owns an 8x8x8 tile of voxels (a thread per 4-voxel column) of one scene;
 // a launch covers up to kMaxJobs scenes (job descriptors travel in the kernel
 // parameters, so no device-side table is needed).  Before the per-voxel loop
 // the block drops the boxes that cannot be the minimum anywhere in the tile:
@@ -28,8 +28,9 @@
 namespace dseed {
 
 constexpr int kTile = 8;
-constexpr int kEsdfThreads = kTile * kTile * kTile;   // 512
-constexpr int kEsdfChunk = 1024;                      // boxes staged per pass
+constexpr int kZPer = 4;                              // voxels per thread along z
+constexpr int kEsdfThreads = kTile * kTile * kTile / kZPer;   // 128
+constexpr int kEsdfChunk = 512;                       // boxes staged per pass
 
 struct EsdfBatch {
     int n_jobs;
@@ -46,8 +47,10 @@ __device__ __forceinline__ float box_sdf(float px, float py, float pz, const flo
     return sqrtf(fmaf(ox, ox, fmaf(oy, oy, oz * oz))) + fminf(in, 0.f);
 }
 
+// One block = one 8^3 tile of one scene; a thread owns a column of kZPer voxels
+// along z, so each box's x and y terms are formed once for the column.
 __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_constant__ EsdfBatch batch) {
-    __shared__ float sb[kEsdfChunk * 6];                 // kept boxes
+    __shared__ float4 sb[kEsdfChunk * 2];              // kept boxes: (cx, cy, cz, hx), (hy, hz, -, -)
     __shared__ float s_red[kEsdfThreads / 32];
     __shared__ int s_count;
     const int jid = blockIdx.z / batch.tiles_z;
@@ -59,11 +62,12 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
     const float *__restrict__ cub = job.cuboids_dev;
     const int n = job.n;
     const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-    const int i = tx * kTile + lx, j = ty * kTile + ly, k = tz * kTile + lz;
-    const bool live = i < g.nx && j < g.ny && k < g.nz;
+    const int i = tx * kTile + lx, j = ty * kTile + ly, k0 = tz * kTile + lz * kZPer;
     const float px = fmaf((float)i + 0.5f, g.res, g.origin[0]);
     const float py = fmaf((float)j + 0.5f, g.res, g.origin[1]);
-    const float pz = fmaf((float)k + 0.5f, g.res, g.origin[2]);
+    float pz[kZPer];
+#pragma unroll
+    for (int e = 0; e < kZPer; ++e) pz[e] = fmaf((float)(k0 + e) + 0.5f, g.res, g.origin[2]);
     // tile extent in voxel centres (the full 8^3 tile, also past the grid edge)
     float lo[3], hi[3];
     lo[0] = fmaf((float)(tx * kTile) + 0.5f, g.res, g.origin[0]);
@@ -106,7 +110,9 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
     tau += 1e-4f;
 
     // pass 2: per chunk, keep the boxes whose lower bound over the tile is <= tau
-    float out2 = CUDART_INF_F, in = CUDART_INF_F;
+    float out2[kZPer], in[kZPer];
+#pragma unroll
+    for (int e = 0; e < kZPer; ++e) { out2[e] = CUDART_INF_F; in[e] = CUDART_INF_F; }
     for (int c0 = 0; c0 < n; c0 += kEsdfChunk) {
         const int cnt = min(kEsdfChunk, n - c0);
         __syncthreads();
@@ -129,25 +135,37 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
             const float lb = gap2 > 0.f ? sqrtf(gap2) : -CUDART_INF_F;
             if (lb <= tau) {
                 const int slot = atomicAdd(&s_count, 1);
-#pragma unroll
-                for (int c = 0; c < 6; ++c) sb[slot * 6 + c] = bx[c];
+                sb[2 * slot] = make_float4(bx[0], bx[1], bx[2], bx[3]);
+                sb[2 * slot + 1] = make_float4(bx[4], bx[5], 0.f, 0.f);
             }
         }
         __syncthreads();
         const int kept = s_count;
         for (int q = 0; q < kept; ++q) {
-            const float *bx = sb + q * 6;
-            const float dx = fabsf(px - bx[0]) - bx[3];
-            const float dy = fabsf(py - bx[1]) - bx[4];
-            const float dz = fabsf(pz - bx[2]) - bx[5];
-            const float ox = fmaxf(dx, 0.f), oy = fmaxf(dy, 0.f), oz = fmaxf(dz, 0.f);
-            out2 = fminf(out2, fmaf(ox, ox, fmaf(oy, oy, oz * oz)));
-            in = fminf(in, fmaxf(dx, fmaxf(dy, dz)));
+            const float4 b0 = sb[2 * q], b1 = sb[2 * q + 1];
+            const float dx = fabsf(px - b0.x) - b0.w;
+            const float dy = fabsf(py - b0.y) - b1.x;
+            const float ox = fmaxf(dx, 0.f), oy = fmaxf(dy, 0.f);
+            const float sxy = fmaf(ox, ox, oy * oy);
+            const float mxy = fmaxf(dx, dy);
+#pragma unroll
+            for (int e = 0; e < kZPer; ++e) {
+                const float dz = fabsf(pz[e] - b0.z) - b1.y;
+                const float oz = fmaxf(dz, 0.f);
+                out2[e] = fminf(out2[e], fmaf(oz, oz, sxy));
+                in[e] = fminf(in[e], fmaxf(mxy, dz));
+            }
         }
     }
-    if (live) {
-        const float s = in <= 0.f ? in : sqrtf(out2);
-        job.esdf_dev[((size_t)k * g.ny + j) * g.nx + i] = fminf(s, DSEED_ESDF_FAR);
+    if (i < g.nx && j < g.ny) {
+#pragma unroll
+        for (int e = 0; e < kZPer; ++e) {
+            const int k = k0 + e;
+            if (k < g.nz) {
+                const float s = in[e] <= 0.f ? in[e] : sqrtf(out2[e]);
+                job.esdf_dev[((size_t)k * g.ny + j) * g.nx + i] = fminf(s, DSEED_ESDF_FAR);
+            }
+        }
     }
 }
 
