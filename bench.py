@@ -390,18 +390,30 @@ def run_learned(args) -> dict:
                         "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
                                                 if eq else None)})
     out["heldout"]["learned"] = learned
-    # the (12, 5) proposal for all 512 problems as one CUDA-graph replay
-    gall = L.ProposalGraph(net, robot, P, 12, 5, seed=1)
+    # the (12, 5) proposal for all 512 problems as one CUDA-graph replay, without and
+    # with cost-gradient guidance (Eq. 5, k = 60, n = 20)
     occ_all = te.occ[te.scene_of_problem.long()]
-    gall(te.q_start, te.q_goal, te.goal, occ_all)
-    seeds, t_d = timed(lambda: gall(te.q_start, te.q_goal, te.goal, occ_all))
-    o, t_p = timed(lambda: L.solve(planner, te, seeds.contiguous(), 20, chunk=P))
-    gall.check()
-    sv_, ss_ = score(o)
-    out["heldout"]["learned_graph"] = {"samples": 12, "ddim_steps": 5, "iters": 20, "solved": round(sv_, 4),
-                                       "seed_success": round(ss_, 4), "ddim_ms": round(t_d * 1e3, 2),
-                                       "plan_ms": round(t_p * 1e3, 2), "total_ms": round((t_d + t_p) * 1e3, 2)}
-    del gall
+    graphed = []
+    for guided in (False, True):
+        kw = dict(guidance=L.Guidance(), planner=planner, table=te.table) if guided else {}
+        gall = L.ProposalGraph(net, robot, P, 12, 5, seed=1, **kw)
+        gall(te.q_start, te.q_goal, te.goal, occ_all, te.scene_of_problem)
+        seeds, t_d = timed(lambda: gall(te.q_start, te.q_goal, te.goal, occ_all, te.scene_of_problem))
+        seeds = seeds.contiguous().clone()
+        gall.check()
+        for it in (10, 20):
+            o, t_p = timed(lambda: L.solve(planner, te, seeds, it, chunk=P))
+            sv_, ss_ = score(o)
+            total = (t_d + t_p) * 1e3
+            fit = [v for v in plain.values() if v["ms"] <= total]
+            eq = max(fit, key=lambda v: v["iters"]) if fit else None
+            graphed.append({"samples": 12, "ddim_steps": 5, "guided": guided, "iters": it, "solved": round(sv_, 4),
+                            "seed_success": round(ss_, 4), "ddim_ms": round(t_d * 1e3, 2),
+                            "plan_ms": round(t_p * 1e3, 2), "total_ms": round(total, 2),
+                            "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
+                                                    if eq else None)})
+        del gall
+    out["heldout"]["learned_graph"] = graphed
 
     # serving: the held-out problems as Poisson arrivals
     budget = 16 * 10 ** 9
@@ -429,32 +441,35 @@ def run_learned(args) -> dict:
     sat = SV.summarize(SV.run_trace(sv, sw, None))
     sv.close()
     occ = te.occ[te.scene_of_problem.long()]
-    S_l, d_l, it_l = 12, 5, 20
-    graph = L.ProposalGraphs(net, robot, (2, 8, 64), S_l, d_l)     # a group of arrivals = one replay
-
-    def propose(idx):
-        ix = torch.as_tensor(idx, dtype=torch.long, device=occ.device)
-        return graph(te.q_start[ix], te.q_goal[ix], te.goal[ix], occ[ix])
-
-    svl = server(it_l)
-    SV.run_trace_seeded(svl, problems, reqs[:64], None, propose)
-    sat_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, None, propose))
-    svl.close()
     rate = 0.5 * sat["plans_per_s"]
     arr = SV.poisson_arrivals(n, rate, seed=5)
     sv = server(100)
     res_p = SV.summarize(SV.run_trace(sv, sw, arr))
     sv.close()
-    svl = server(it_l)
-    res_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, arr, propose))
-    svl.close()
-    graph.check()
     out["serving"] = {"workload": f"{n} requests over the {P} held-out problems, T = 32, 16 GB budget, rounds of "
-                                  f"20 iterations; offered load = half the plain method's saturation",
+                                  f"up to 20 iterations; offered load = half the plain method's saturation",
                       "plain": {"seeds": 64, "iters": 100, "saturation": sat, "at_load": res_p},
-                      "seeded": {"samples": S_l, "ddim_steps": d_l, "iters": it_l, "saturation": sat_l,
-                                 "at_load": res_l},
                       "offered_plans_per_s": rate}
+    S_l, d_l = 12, 5
+    for key, it_l, kw in (("seeded", 20, {}),
+                          ("seeded_guided", 10, dict(guidance=L.Guidance(), planner=planner, table=te.table))):
+        graph = L.ProposalGraphs(net, robot, (2, 8, 64), S_l, d_l, **kw)     # a group of arrivals = one replay
+
+        def propose(idx):
+            ix = torch.as_tensor(idx, dtype=torch.long, device=occ.device)
+            return graph(te.q_start[ix], te.q_goal[ix], te.goal[ix], occ[ix], te.scene_of_problem[ix])
+
+        svl = server(it_l)
+        SV.run_trace_seeded(svl, problems, reqs[:64], None, propose)
+        sat_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, None, propose))
+        svl.close()
+        svl = server(it_l)
+        res_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, arr, propose))
+        svl.close()
+        graph.check()
+        out["serving"][key] = {"samples": S_l, "ddim_steps": d_l, "guided": bool(kw), "iters": it_l,
+                               "saturation": sat_l, "at_load": res_l}
+        del graph
     return out
 
 

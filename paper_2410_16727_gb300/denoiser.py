@@ -428,14 +428,17 @@ class Denoiser:
             self.bf16_mode = False
 
     def ddim_sample(self, qs, qg, goal, occ, noise, steps: int = 10, bf16: bool = True, clip: float = 2.0,
-                    sample_problem: Optional[torch.Tensor] = None, check: bool = True):
+                    sample_problem: Optional[torch.Tensor] = None, check: bool = True,
+                    guide: Optional[Callable] = None):
         """DDIM (deterministic) from x_K = noise over `steps` evenly spaced steps
         of the K-step schedule; returns normalised trajectories [N][T][D].
         qs, qg, goal, occ are per problem; sample_problem [N] (int32) maps each
         sample to its problem (default: sample n -> problem n).  The condition
         and the FiLM rows are computed once per problem and step; with bf16 the
         U-Net runs on the tensor cores (unet_tc), else in FP32.  check=False
-        skips reading the kernels' error flag (a host sync), for graph capture."""
+        skips reading the kernels' error flag (a host sync), for graph capture.
+        guide(i, k_reached, x, last) -> x, when given, is applied after every
+        step (cost-gradient guidance)."""
         K = self.spec.K
         ks = np.linspace(K - 1, 0, steps).round().astype(int)
         x = noise.clone()
@@ -462,6 +465,9 @@ class Denoiser:
             out = torch.empty_like(x)
             _nn("ddim_step", x, eps, ab_k, ab_prev, x.numel(), clip, out)
             x = out
+            if guide is not None:
+                k_reached = int(ks[i + 1]) if i + 1 < len(ks) else -1
+                x = guide(i, k_reached, x, i + 1 == len(ks))
         if bf16 and check:
             self.check_tc()
         return x

@@ -278,12 +278,17 @@ def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: flo
 
 
 def _propose_core(net: DN.Denoiser, robot: I.Robot, q_start, q_goal, goal, occ, noise, rows, steps: int,
-                  bf16: bool, check: bool) -> torch.Tensor:
+                  bf16: bool, check: bool, guide_ctx=None) -> torch.Tensor:
     qs = normalise(robot, q_start.contiguous())
     qg = normalise(robot, q_goal.contiguous())
+    lin = linear_path(qs, qg, net.spec.T)[rows.long()].contiguous()
+    guide = None
+    if guide_ctx is not None:
+        planner, table, scene_of_problem, gd = guide_ctx
+        guide = _guide_fn(robot, planner, table, q_start, goal, scene_of_problem, lin,
+                          noise.shape[0] // q_start.shape[0], net.spec.T, gd)
     r = net.ddim_sample(qs, qg, goal.contiguous(), occ.contiguous(), noise, steps=steps, bf16=bf16,
-                        sample_problem=rows, check=check)
-    lin = linear_path(qs, qg, net.spec.T)[rows.long()]
+                        sample_problem=rows, check=check, guide=guide)
     x = from_residual(r, lin)
     _nn("clamp_affine", x, 1.0, 0.0, -1.0, 1.0, x, x.numel())
     P, S = q_start.shape[0], noise.shape[0] // q_start.shape[0]
@@ -306,6 +311,76 @@ def propose_for(net: DN.Denoiser, robot: I.Robot, q_start: torch.Tensor, q_goal:
     return _propose_core(net, robot, q_start, q_goal, goal, occ, noise, rows, steps, bf16, True)
 
 
+@dataclasses.dataclass
+class Guidance:
+    """Cost-gradient guidance of the DDIM sampler (the paper's appendix, Eq. 5):
+    after every denoising step that reaches a step index below k_guide, except
+    the last one, the sampled trajectories take n_grad descent steps on the
+    plan cost of their own problem (collision, smoothness, goal, limits; the
+    cost kernel the optimiser uses): x <- x - clip(alpha dC/dx, +-cap), with
+    dC/dx = dC/dq dq/dx through the residual and limit normalisation.  The
+    paper prints the step as +alpha grad C with alpha = 1 on cuRobo's cost
+    scale; read as a descent step, alpha here is on this cost's scale and each
+    step is capped per entry (cap, in diffused units)."""
+    k_guide: int = 60
+    n_grad: int = 20
+    alpha: float = 1e-3
+    cap: float = 0.02
+
+
+def _guide_fn(robot: I.Robot, planner: api.Planner, table: B.SceneTable, q_start, goal, scene_of_problem,
+              lin: torch.Tensor, S: int, T: int, gd: Guidance):
+    P = q_start.shape[0]
+    dev = q_start.device
+    batch = api.Batch(q_start, goal, scene_of_problem, table, S, T, planner.cost, None, dev)
+    # dq/dx per joint: (hi - lo) / 2 (un-normalising) / RES_SCALE, as a FiLM row (scale, shift 0);
+    # cached, so that no host copy happens inside a graph capture
+    key = ("jac", robot.limits.tobytes(), str(dev))
+    jac = _AFFINE_CACHE.get(key)
+    if jac is None:
+        lo = robot.limits[:, 0].astype(np.float64)
+        hi = robot.limits[:, 1].astype(np.float64)
+        jac = _AFFINE_CACHE[key] = torch.tensor(np.concatenate([(hi - lo) / 2.0 / RES_SCALE, np.zeros(7)])[None],
+                                                dtype=torch.float32, device=dev)
+
+    def guide(i, k_reached, x, last):
+        if last or k_reached < 0 or k_reached >= gd.k_guide or gd.alpha == 0.0:
+            return x
+        for _ in range(gd.n_grad):
+            xn = from_residual(x, lin)
+            _nn("clamp_affine", xn, 1.0, 0.0, -1.0, 1.0, xn, xn.numel())
+            q = normalise(robot, xn, inverse=True)
+            _, gq = B.cost_grad(planner.robot, batch.desc, batch.pr, q.view(P, S, T, 7))
+            gx = torch.empty_like(x)
+            _nn("film", gq.view(-1, 7), jac, 1, P * S * T, 7, gx, None, None, None, 0)
+            step = torch.empty_like(x)
+            _nn("clamp_affine", gx, -gd.alpha, 0.0, -gd.cap, gd.cap, step, x.numel())
+            out = torch.empty_like(x)
+            _nn("axpby", 1.0, x, 1.0, step, out, x.numel())
+            x = out
+        return x
+
+    guide.batch = batch            # keeps the descriptors' tensors alive
+    return guide
+
+
+def propose_guided(net: DN.Denoiser, robot: I.Robot, planner: api.Planner, ps: ProblemSet, S: int,
+                   steps: int = 10, guidance: Optional[Guidance] = None, seed: int = 0) -> torch.Tensor:
+    """Cost-gradient-guided DDIM proposals (Guidance) for every problem of a
+    problem set: [P][S][T][7].  With alpha = 0 they equal propose()."""
+    gd = guidance or Guidance()
+    P = ps.q_start.shape[0]
+    dev = ps.q_start.device
+    T, D = net.spec.T, net.spec.D
+    g = torch.Generator(device=dev)
+    g.manual_seed(1000 + seed)
+    noise = torch.randn((P * S, T, D), device=dev, generator=g)
+    rows = torch.arange(P, device=dev, dtype=torch.int32).repeat_interleave(S)
+    occ = ps.occ[ps.scene_of_problem.long()].contiguous()
+    return _propose_core(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, noise, rows, steps, True, True,
+                         guide_ctx=(planner, ps.table, ps.scene_of_problem, gd))
+
+
 class ProposalGraph:
     """DDIM proposals for up to G problems captured once as a CUDA graph over
     static buffers: the launch sequence of a fixed group size never changes,
@@ -313,7 +388,9 @@ class ProposalGraph:
     every step (a serving loop proposes for each group of arrivals).  Call with
     g <= G problems; rows past g compute on stale inputs and are not returned."""
 
-    def __init__(self, net: DN.Denoiser, robot: I.Robot, G: int, S: int, steps: int, seed: int = 0):
+    def __init__(self, net: DN.Denoiser, robot: I.Robot, G: int, S: int, steps: int, seed: int = 0,
+                 guidance: Optional[Guidance] = None, planner: Optional[api.Planner] = None,
+                 table: Optional[B.SceneTable] = None):
         dev = net.dev
         s = net.spec
         self.G, self.S, self.net = G, S, net
@@ -321,12 +398,15 @@ class ProposalGraph:
         self.q_goal = torch.zeros((G, 7), device=dev)
         self.goal = torch.zeros((G, 7), device=dev)
         self.goal[:, 3] = 1.0
+        self.scene = torch.zeros((G,), dtype=torch.int32, device=dev)
         self.occ = torch.zeros((G, s.occ_n ** 3), device=dev)
         self.noise = torch.zeros((G * S, s.T, s.D), device=dev)
         self.rows = torch.arange(G, device=dev, dtype=torch.int32).repeat_interleave(S)
         self.gen = torch.Generator(device=dev)
         self.gen.manual_seed(2000 + seed)
-        args = (net, robot, self.q_start, self.q_goal, self.goal, self.occ, self.noise, self.rows, steps, True, False)
+        ctx = (planner, table, self.scene, guidance) if guidance is not None else None
+        args = (net, robot, self.q_start, self.q_goal, self.goal, self.occ, self.noise, self.rows, steps, True, False,
+                ctx)
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):                  # warm-up outside the capture (weight caches, constants)
@@ -339,7 +419,9 @@ class ProposalGraph:
             self.out = _propose_core(*args)
         torch.cuda.synchronize()
 
-    def __call__(self, q_start, q_goal, goal, occ) -> torch.Tensor:
+    def __call__(self, q_start, q_goal, goal, occ, scene: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Seeds [g][S][T][7] for g <= G problems; scene (int32 [g], indices
+        into the captured scene table) is needed with guidance."""
         g = q_start.shape[0]
         if self.net._tc_weights() is not self.weights:
             raise RuntimeError("the denoiser's parameters changed after capture: build a new ProposalGraph")
@@ -348,6 +430,8 @@ class ProposalGraph:
         self.q_start[:g].copy_(q_start)
         self.q_goal[:g].copy_(q_goal)
         self.goal[:g].copy_(goal)
+        if scene is not None:
+            self.scene[:g].copy_(scene)
         self.occ[:g].copy_(occ)
         torch.randn(self.noise.shape, device=self.noise.device, generator=self.gen, out=self.noise)
         self.graph.replay()
@@ -361,14 +445,15 @@ class ProposalGraphs:
     """Several captured group sizes; a group of g problems replays the
     smallest graph with G >= g (less padded work for small groups)."""
 
-    def __init__(self, net: DN.Denoiser, robot: I.Robot, sizes, S: int, steps: int, seed: int = 0):
-        self.graphs = [ProposalGraph(net, robot, G, S, steps, seed + i) for i, G in enumerate(sorted(sizes))]
+    def __init__(self, net: DN.Denoiser, robot: I.Robot, sizes, S: int, steps: int, seed: int = 0, **guide_kw):
+        self.graphs = [ProposalGraph(net, robot, G, S, steps, seed + i, **guide_kw)
+                       for i, G in enumerate(sorted(sizes))]
 
-    def __call__(self, q_start, q_goal, goal, occ) -> torch.Tensor:
+    def __call__(self, q_start, q_goal, goal, occ, scene: Optional[torch.Tensor] = None) -> torch.Tensor:
         g = q_start.shape[0]
         for pg in self.graphs:
             if g <= pg.G:
-                return pg(q_start, q_goal, goal, occ)
+                return pg(q_start, q_goal, goal, occ, scene)
         raise ValueError(f"group of {g} problems exceeds the largest captured size {self.graphs[-1].G}")
 
     def check(self):
