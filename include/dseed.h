@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define DSEED_ABI_VERSION 1
+#define DSEED_ABI_VERSION 2
 
 #define DSEED_MAX_SPHERES 64    /* collision spheres per robot */
 #define DSEED_MAX_T 128         /* waypoints per trajectory */
@@ -74,6 +74,12 @@ typedef struct {
     int   sphere_frame[DSEED_MAX_SPHERES];   /* frame 1..8 the sphere is fixed to */
     float sphere_offset[DSEED_MAX_SPHERES][3]; /* centre in that frame (m) */
     float sphere_radius[DSEED_MAX_SPHERES];  /* radius (m), > 0 */
+    /* Self-collision pairs (C_self of the App. A.5 objective): spheres on frames
+     * at least two apart whose surfaces are at least self_margin apart at the
+     * reference configuration self_ref (closer pairs overlap by construction of
+     * the sphere model and are never checked). */
+    float self_ref[7];                       /* rad */
+    float self_margin;                       /* m */
 } DseedRobotDesc;
 
 typedef struct DseedRobot DseedRobot;        /* opaque, host memory */
@@ -110,6 +116,11 @@ typedef struct {
     float w_p;    /* goal position weight */
     float w_R;    /* goal orientation weight */
     float w_l;    /* joint-limit weight */
+    float w_self;   /* self-collision hinge weight w_s (0: no self term); C_self = w_s sum over the
+                     * robot's checked sphere pairs and waypoints of max(0, r_i + r_j + eta_self - |c_i - c_j|),
+                     * added to the collision term; with w_self > 0 a trajectory is collision free
+                     * only if it is also free of self-collision */
+    float eta_self; /* self-collision margin (m) */
 } DseedCostParams;
 
 /* L-BFGS settings.  One iteration = one cost+gradient evaluation of the trial
@@ -167,6 +178,11 @@ const char *dseed_last_error(void);
  * lower > upper or a non-finite entry. */
 int  dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out);
 void dseed_robot_destroy(DseedRobot *robot);
+/* The self-collision pairs the robot checks (rule in DseedRobotDesc), in the
+ * caller's sphere order: bit j of mask_host[i] set for a checked pair (i, j),
+ * symmetric; *n_pairs (optional) receives the number of pairs.  mask_host
+ * holds n_spheres entries.  Host-only; EINVAL on a null robot or mask. */
+int  dseed_robot_self_pairs(const DseedRobot *robot, unsigned long long *mask_host, int *n_pairs);
 
 /* ------------------------------------------------------------------ ESDF */
 

@@ -20,6 +20,8 @@
  *     start held at rest,
  *   - goal: w_p |p - p*|^2 + w_R (1 - <q, q*>^2) at the last waypoint,
  *   - joint limits: quadratic penalty outside [lower, upper],
+ *   - self collision (C_self, optional): linear hinge w_s * max(0, r_i + r_j +
+ *     eta_s - |c_i - c_j|) over the sphere pairs the robot marks as checked,
  *   - success (Sec. 5.1 and Appendix A.6): collision free, translation error
  *     below delta_t, rotation error below delta_r, within limits,
  *   - optimiser: L-BFGS (history m) with Armijo accept/reject and step halving.
@@ -47,10 +49,12 @@ typedef struct {
     const int *sph_frame;    /* [ns]: frame 1..8 the sphere is fixed to */
     const double *sph_o;     /* [ns][3]: offset in that frame */
     const double *sph_r;     /* [ns]: radius */
+    const unsigned char *self_pair;  /* [ns][ns]: 1 = pair checked for self-collision (or NULL) */
 } orc_robot;
 
 typedef struct {
     double w_c, eta, dt, w_v, w_a, w_j, w_p, w_R, w_l;
+    double w_s, eta_s;       /* self-collision hinge weight and margin (w_s = 0: off) */
 } orc_cost_params;
 
 typedef struct {
@@ -182,6 +186,32 @@ void orc_sphere_centres(const orc_robot *rb, const double *q, double *c /* [ns][
     orc_fk(rb->dh, q, frames);
     for (int k = 0; k < rb->ns; ++k)
         sphere_centre(frames, rb->sph_frame[k], rb->sph_o + 3 * k, c + 3 * k);
+}
+
+/* Sphere pairs checked for self-collision: spheres fixed to frames at least two
+ * apart (a frame and its neighbours in the chain are never tested against each
+ * other) whose surfaces are at least `margin` apart at the reference
+ * configuration q_ref (pairs that are close there overlap by construction of
+ * the sphere model).  mask[i * ns + j] = mask[j * ns + i] = 1 for such pairs. */
+int orc_self_pairs(const orc_robot *rb, const double *q_ref, double margin, unsigned char *mask)
+{
+    int ns = rb->ns, count = 0;
+    double *c = (double *)malloc(sizeof(double) * 3 * ns);
+    orc_sphere_centres(rb, q_ref, c);
+    memset(mask, 0, (size_t)ns * ns);
+    for (int i = 0; i < ns; ++i)
+        for (int j = i + 1; j < ns; ++j) {
+            int df = rb->sph_frame[i] - rb->sph_frame[j];
+            if (df < 2 && df > -2) continue;
+            double d[3] = { c[3 * i] - c[3 * j], c[3 * i + 1] - c[3 * j + 1], c[3 * i + 2] - c[3 * j + 2] };
+            double gap = sqrt(dot3(d, d)) - rb->sph_r[i] - rb->sph_r[j];
+            if (gap >= margin) {
+                mask[i * ns + j] = mask[j * ns + i] = 1;
+                ++count;
+            }
+        }
+    free(c);
+    return count;
 }
 
 /* Unit quaternion (w, x, y, z) of a rotation matrix, taking the square root of
@@ -322,7 +352,7 @@ static void quat_normalise(const double *in, double out[4])
 }
 
 /* Total cost of x = [T][7] (waypoints 1..T).  grad (optional) receives dC/dx,
- * terms (optional) receives [C_world, C_smooth, C_goal, C_limit]. */
+ * terms (optional) receives [C_world (+ C_self), C_smooth, C_goal, C_limit]. */
 double orc_cost(const orc_problem *pb, const double *x, double *grad, double *terms)
 {
     const orc_robot *rb = pb->robot;
@@ -365,8 +395,10 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
             }
         }
 
-    /* C_world at every waypoint, and C_goal at the last one */
+    /* C_world (and C_self) at every waypoint, and C_goal at the last one */
     double frames[9 * 16];
+    const int use_self = cp->w_s > 0.0 && rb->self_pair != NULL;
+    double *cent = use_self ? (double *)malloc(sizeof(double) * 3 * rb->ns) : NULL;
     for (int t = 1; t <= T; ++t) {
         const double *q = x + 7 * (t - 1);
         orc_fk(rb->dh, q, frames);
@@ -374,6 +406,37 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
         for (int i = 1; i <= 7; ++i) {
             frame_zaxis(frames + 16 * i, zax[i]);
             frame_origin(frames + 16 * i, org[i]);
+        }
+        if (use_self) {
+            /* C_self: for each checked pair, w_s * max(0, r_i + r_j + eta_s - |c_i - c_j|);
+             * dC/dc_i = -w_s (c_i - c_j) / |c_i - c_j| = -dC/dc_j, through the joints
+             * that move each sphere (velocity z_m x (c - p_m) per unit angle) */
+            for (int k = 0; k < rb->ns; ++k)
+                sphere_centre(frames, rb->sph_frame[k], rb->sph_o + 3 * k, cent + 3 * k);
+            for (int i = 0; i < rb->ns; ++i)
+                for (int j = i + 1; j < rb->ns; ++j) {
+                    if (!rb->self_pair[i * rb->ns + j]) continue;
+                    double d[3] = { cent[3 * i] - cent[3 * j], cent[3 * i + 1] - cent[3 * j + 1],
+                                    cent[3 * i + 2] - cent[3 * j + 2] };
+                    double dist = sqrt(dot3(d, d));
+                    double h = rb->sph_r[i] + rb->sph_r[j] + cp->eta_s - dist;
+                    if (h <= 0.0) continue;
+                    c_world += cp->w_s * h;
+                    if (!grad) continue;
+                    for (int side = 0; side < 2; ++side) {
+                        int k = side == 0 ? i : j;
+                        double sgn = side == 0 ? -1.0 : 1.0;
+                        double dc[3] = { sgn * cp->w_s * d[0] / dist, sgn * cp->w_s * d[1] / dist,
+                                         sgn * cp->w_s * d[2] / dist };
+                        int L = rb->sph_frame[k], top = L < 7 ? L : 7;
+                        for (int m = 1; m <= top; ++m) {
+                            double r[3] = { cent[3 * k] - org[m][0], cent[3 * k + 1] - org[m][1],
+                                            cent[3 * k + 2] - org[m][2] }, J[3];
+                            cross3(zax[m], r, J);
+                            grad[7 * (t - 1) + (m - 1)] += dot3(dc, J);
+                        }
+                    }
+                }
         }
         for (int k = 0; k < rb->ns; ++k) {
             int L = rb->sph_frame[k];
@@ -421,6 +484,7 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
                 }
         }
     }
+    free(cent);
     if (terms) { terms[0] = c_world; terms[1] = c_smooth; terms[2] = c_goal; terms[3] = c_limit; }
     return c_world + c_smooth + c_goal + c_limit;
 }
@@ -429,7 +493,8 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
 /* Success test and trajectory metrics (Sec. 5.1, Appendix A.6)              */
 /* ------------------------------------------------------------------------ */
 
-/* metrics[7] = min over waypoints/spheres of (phi - r), translation error |p - p*|,
+/* metrics[7] = min over waypoints/spheres of (phi - r) (and, with the self cost
+ * on, of the checked pairs' |c_i - c_j| - r_i - r_j), translation error |p - p*|,
  * rotation error 2 acos(|<q, q*>|), max |jerk| over waypoints and joints,
  * worst joint-limit violation, total cost, 1/0 collision free.
  * thr = [delta_t, delta_r].  Returns 1 on success. */
@@ -446,6 +511,17 @@ int orc_evaluate(const orc_problem *pb, const double *x, const double *thr, doub
             double clr = orc_esdf_lookup(pb->grid, c, NULL) - rb->sph_r[k];
             if (clr < min_clear) min_clear = clr;
         }
+        if (pb->cp->w_s > 0.0 && rb->self_pair != NULL)
+            for (int i = 0; i < rb->ns; ++i)
+                for (int j = i + 1; j < rb->ns; ++j) {
+                    if (!rb->self_pair[i * rb->ns + j]) continue;
+                    double ci[3], cj[3];
+                    sphere_centre(frames, rb->sph_frame[i], rb->sph_o + 3 * i, ci);
+                    sphere_centre(frames, rb->sph_frame[j], rb->sph_o + 3 * j, cj);
+                    double d[3] = { ci[0] - cj[0], ci[1] - cj[1], ci[2] - cj[2] };
+                    double clr = sqrt(dot3(d, d)) - rb->sph_r[i] - rb->sph_r[j];
+                    if (clr < min_clear) min_clear = clr;
+                }
         for (int j = 0; j < 7; ++j) {
             double jk = (traj_y(pb, x, t, j) - 3.0 * traj_y(pb, x, t - 1, j)
                          + 3.0 * traj_y(pb, x, t - 2, j) - traj_y(pb, x, t - 3, j))

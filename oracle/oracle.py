@@ -24,11 +24,12 @@ _ip = C.POINTER(C.c_int)
 
 class _Robot(C.Structure):
     _fields_ = [("dh", _dp), ("lim", _dp), ("ns", C.c_int), ("sph_frame", _ip),
-                ("sph_o", _dp), ("sph_r", _dp)]
+                ("sph_o", _dp), ("sph_r", _dp), ("self_pair", C.POINTER(C.c_ubyte))]
 
 
 class _CostParams(C.Structure):
-    _fields_ = [(k, C.c_double) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l")]
+    _fields_ = [(k, C.c_double) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l",
+                                          "w_s", "eta_s")]
 
 
 class _Grid(C.Structure):
@@ -78,6 +79,8 @@ def load():
     lib.orc_lbfgs_quadratic.argtypes = [_dp, _dp, C.c_int, C.POINTER(_Opt), _dp, _dp, _dp, _dp]
     lib.orc_lbfgs_quadratic.restype = C.c_int
     lib.orc_num_threads.restype = C.c_int
+    lib.orc_self_pairs.argtypes = [C.POINTER(_Robot), _dp, C.c_double, C.POINTER(C.c_ubyte)]
+    lib.orc_self_pairs.restype = C.c_int
     _lib = lib
     return lib
 
@@ -195,7 +198,14 @@ class Oracle:
         self.sph_o = _d(robot.sph_o)
         self.sph_r = _d(robot.sph_r)
         self.robot = _Robot(_ptr(self.dh), _ptr(self.lim), int(self.sph_r.shape[0]),
-                            _ptr(self.sph_frame), _ptr(self.sph_o), _ptr(self.sph_r))
+                            _ptr(self.sph_frame), _ptr(self.sph_o), _ptr(self.sph_r), None)
+        # sphere pairs checked for self-collision, by the rule applied at the robot's reference pose
+        ns = int(self.sph_r.shape[0])
+        self.self_mask = np.zeros((ns, ns), dtype=np.uint8)
+        self.n_self_pairs = int(self._lib.orc_self_pairs(C.byref(self.robot), _ptr(_d(robot.self_ref)),
+                                                         float(robot.self_margin),
+                                                         self.self_mask.ctypes.data_as(C.POINTER(C.c_ubyte))))
+        self.robot.self_pair = self.self_mask.ctypes.data_as(C.POINTER(C.c_ubyte))
         self.cp = _CostParams(*[float(v) for v in cost.as_array()])
         self.grids_meta = list(grids)
         self.phis = [esdf_build(c, g) for c, g in zip(cuboids, grids)]

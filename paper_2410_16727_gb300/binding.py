@@ -12,6 +12,7 @@ import math
 import os
 from typing import Optional, Sequence
 
+import numpy as np
 import torch
 
 from . import build as _build
@@ -28,7 +29,8 @@ _lib = None
 class RobotDesc(C.Structure):
     _fields_ = [("dh", (C.c_float * 4) * 8), ("limits", (C.c_float * 2) * 7), ("n_spheres", C.c_int),
                 ("sphere_frame", C.c_int * MAX_SPHERES), ("sphere_offset", (C.c_float * 3) * MAX_SPHERES),
-                ("sphere_radius", C.c_float * MAX_SPHERES)]
+                ("sphere_radius", C.c_float * MAX_SPHERES), ("self_ref", C.c_float * 7),
+                ("self_margin", C.c_float)]
 
 
 class Grid(C.Structure):
@@ -43,8 +45,11 @@ class Scene(C.Structure):
     _fields_ = [("esdf_dev", C.c_void_p), ("grid", Grid), ("lipschitz", C.c_float)]
 
 
+COST_FIELDS = ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l", "w_self", "eta_self")
+
+
 class CostParams(C.Structure):
-    _fields_ = [(k, C.c_float) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l")]
+    _fields_ = [(k, C.c_float) for k in COST_FIELDS]
 
 
 class OptParams(C.Structure):
@@ -171,6 +176,7 @@ _SIGS = {
     "dseed_nn_im2col1d_bf16": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                 C.c_void_p, C.c_void_p], C.c_int),
     "dseed_nn_upsample2_bf16": ([C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p], C.c_int),
+    "dseed_robot_self_pairs": ([C.c_void_p, C.POINTER(C.c_ulonglong), C.POINTER(C.c_int)], C.c_int),
     "dseed_plan_batch_static": ([C.c_void_p, C.POINTER(PlanDesc), C.POINTER(Problems), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
 }
@@ -254,10 +260,25 @@ class Robot:
             for c in range(3):
                 d.sphere_offset[k][c] = float(robot.sph_o[k][c])
             d.sphere_radius[k] = float(robot.sph_r[k])
+        ref = np.asarray(getattr(robot, "self_ref", np.zeros(7)), np.float64).reshape(7)
+        for j in range(7):
+            d.self_ref[j] = float(ref[j])
+        d.self_margin = float(getattr(robot, "self_margin", 0.0))
         h = C.c_void_p()
         _check(load().dseed_robot_create(C.byref(d), C.byref(h)), "dseed_robot_create")
         self.handle = h
         self.n_spheres = ns
+
+    def self_pairs(self) -> np.ndarray:
+        """Checked self-collision pairs as a symmetric [ns][ns] uint8 matrix (caller's sphere order)."""
+        mask = (C.c_ulonglong * MAX_SPHERES)()
+        n = C.c_int()
+        _check(load().dseed_robot_self_pairs(self.handle, mask, C.byref(n)), "dseed_robot_self_pairs")
+        out = np.zeros((self.n_spheres, self.n_spheres), np.uint8)
+        for i in range(self.n_spheres):
+            for j in range(self.n_spheres):
+                out[i, j] = (mask[i] >> j) & 1
+        return out
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:
@@ -278,7 +299,7 @@ def plan_desc(P: int, S: int, T: int, cost, opt=None, delta_t: float = 0.005,
               delta_r: float = 2.86 * math.pi / 180.0) -> PlanDesc:
     d = PlanDesc()
     d.P, d.S, d.T = int(P), int(S), int(T)
-    for k, v in zip(("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l"), cost.as_array()):
+    for k, v in zip(COST_FIELDS, cost.as_array()):
         setattr(d.cost, k, float(v))
     if opt is not None:
         d.opt.iters, d.opt.m = int(opt.iters), int(opt.m)

@@ -15,6 +15,8 @@
 
 struct DseedRobot {
     dseed::KRobot k;
+    unsigned long long self_mask[DSEED_MAX_SPHERES];   // checked pairs in the caller's sphere order
+    int n_self_pairs;
 };
 
 namespace {
@@ -47,10 +49,12 @@ int check_desc(const DseedPlanDesc *d, bool need_opt) {
     if (d->T < 1 || d->T > DSEED_MAX_T) return fail(DSEED_EINVAL, "T = %d outside 1..%d", d->T, DSEED_MAX_T);
     if ((long long)d->P * d->S > (1LL << 31) - 1) return fail(DSEED_EINVAL, "P * S too large");
     const DseedCostParams &c = d->cost;
-    const float cv[] = {c.w_c, c.eta, c.dt, c.w_v, c.w_a, c.w_j, c.w_p, c.w_R, c.w_l, d->delta_t, d->delta_r};
+    const float cv[] = {c.w_c, c.eta, c.dt, c.w_v, c.w_a, c.w_j, c.w_p, c.w_R, c.w_l, c.w_self, c.eta_self,
+                        d->delta_t, d->delta_r};
     for (float v : cv)
         if (!finite(v)) return fail(DSEED_EINVAL, "non-finite cost or success parameter");
     if (!(c.dt > 0.f)) return fail(DSEED_EINVAL, "dt must be > 0");
+    if (c.w_self < 0.f || c.eta_self < 0.f) return fail(DSEED_EINVAL, "w_self and eta_self must be >= 0");
     if (need_opt) {
         const DseedOptParams &o = d->opt;
         if (o.iters < 1) return fail(DSEED_EINVAL, "iters = %d < 1", o.iters);
@@ -84,6 +88,8 @@ dseed::KCost make_cost(const DseedCostParams &c) {
     k.w_p = c.w_p;
     k.w_R = c.w_R;
     k.w_l = c.w_l;
+    k.w_s = c.w_self;
+    k.eta_s = c.eta_self;
     return k;
 }
 
@@ -171,6 +177,76 @@ PlanLayout plan_layout(const DseedPlanDesc *d) {
     return l;
 }
 
+// Frames 1..8 of the modified-DH chain at q (double precision, host): R row-major, p.
+void host_fk(const DseedRobotDesc *d, const float *q, double R[9][9], double P[9][3]) {
+    double Rc[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1}, pc[3] = {0, 0, 0};
+    for (int i = 0; i < 8; ++i) {
+        const double a = d->dh[i][0], dd = d->dh[i][1], al = d->dh[i][2];
+        const double th = (i < 7 ? (double)q[i] : 0.0) + d->dh[i][3];
+        const double ca = std::cos(al), sa = std::sin(al), ct = std::cos(th), st = std::sin(th);
+        // p += a x_prev; R = R RotX(alpha) RotZ(theta); p += d z_new
+        for (int r = 0; r < 3; ++r) pc[r] += a * Rc[3 * r];
+        for (int r = 0; r < 3; ++r) {
+            const double x = Rc[3 * r], y = Rc[3 * r + 1], z = Rc[3 * r + 2];
+            const double y1 = ca * y + sa * z, z1 = -sa * y + ca * z;
+            Rc[3 * r] = ct * x + st * y1;
+            Rc[3 * r + 1] = -st * x + ct * y1;
+            Rc[3 * r + 2] = z1;
+        }
+        for (int r = 0; r < 3; ++r) pc[r] += dd * Rc[3 * r + 2];
+        for (int e = 0; e < 9; ++e) R[i + 1][e] = Rc[e];
+        for (int e = 0; e < 3; ++e) P[i + 1][e] = pc[e];
+    }
+}
+
+// The robot's self-collision pairs (rule in dseed.h): spheres on frames at least
+// two apart whose surfaces are at least self_margin apart at self_ref.
+void self_pairs(const DseedRobotDesc *d, DseedRobot *r) {
+    double R[9][9], P[9][3];
+    host_fk(d, d->self_ref, R, P);
+    const int ns = d->n_spheres;
+    double c[DSEED_MAX_SPHERES][3];
+    for (int k = 0; k < ns; ++k) {
+        const int L = d->sphere_frame[k];
+        for (int row = 0; row < 3; ++row)
+            c[k][row] = R[L][3 * row] * d->sphere_offset[k][0] + R[L][3 * row + 1] * d->sphere_offset[k][1] +
+                        R[L][3 * row + 2] * d->sphere_offset[k][2] + P[L][row];
+    }
+    std::memset(r->self_mask, 0, sizeof(r->self_mask));
+    r->n_self_pairs = 0;
+    for (int i = 0; i < ns; ++i)
+        for (int j = i + 1; j < ns; ++j) {
+            const int df = d->sphere_frame[i] - d->sphere_frame[j];
+            if (df > -2 && df < 2) continue;
+            const double dx = c[i][0] - c[j][0], dy = c[i][1] - c[j][1], dz = c[i][2] - c[j][2];
+            if (std::sqrt(dx * dx + dy * dy + dz * dz) - d->sphere_radius[i] - d->sphere_radius[j] >=
+                (double)d->self_margin) {
+                r->self_mask[i] |= 1ull << j;
+                r->self_mask[j] |= 1ull << i;
+                ++r->n_self_pairs;
+            }
+        }
+    // the kernels' form: sorted sphere indices, and per frame the earlier frames with pairs
+    dseed::KRobot &k = r->k;
+    int sorted_of[DSEED_MAX_SPHERES];
+    for (int q = 0; q < ns; ++q) sorted_of[k.sph_orig[q]] = q;
+    for (int q = 0; q < ns; ++q) {
+        const unsigned long long m = r->self_mask[k.sph_orig[q]];
+        unsigned long long sm = 0;
+        for (int j = 0; j < ns; ++j)
+            if ((m >> j) & 1ull) sm |= 1ull << sorted_of[j];
+        k.self_mask[q] = sm;
+    }
+    for (int L = 1; L <= 8; ++L) {
+        unsigned fm = 0;
+        for (int a = 1; a <= L - 2; ++a)
+            for (int q = k.frame_begin[L - 1]; q < k.frame_begin[L]; ++q)
+                for (int j = k.frame_begin[a - 1]; j < k.frame_begin[a]; ++j)
+                    if ((k.self_mask[q] >> j) & 1ull) fm |= 1u << (a - 1);
+        k.self_frames[L - 1] = fm;
+    }
+}
+
 }  // namespace
 
 namespace dseed {
@@ -227,6 +303,9 @@ int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
         for (int c = 0; c < 3; ++c)
             if (!finite(desc->sphere_offset[k][c])) return fail(DSEED_EINVAL, "sphere %d: non-finite offset", k);
     }
+    for (int j = 0; j < 7; ++j)
+        if (!finite(desc->self_ref[j])) return fail(DSEED_EINVAL, "non-finite self_ref entry %d", j);
+    if (!finite(desc->self_margin)) return fail(DSEED_EINVAL, "non-finite self_margin");
     DseedRobot *r = new (std::nothrow) DseedRobot;
     if (!r) return fail(DSEED_ENOMEM, "host allocation of the robot failed");
     std::memset(&r->k, 0, sizeof(r->k));
@@ -285,7 +364,15 @@ int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
     }
     k.cf8 = (float)std::cos((double)desc->dh[7][3]);
     k.sf8 = (float)std::sin((double)desc->dh[7][3]);
+    self_pairs(desc, r);
     *out = r;
+    return DSEED_OK;
+}
+
+int dseed_robot_self_pairs(const DseedRobot *robot, unsigned long long *mask_host, int *n_pairs) {
+    if (!robot || !mask_host) return fail(DSEED_EINVAL, "robot or mask is NULL");
+    for (int i = 0; i < robot->k.n_spheres; ++i) mask_host[i] = robot->self_mask[i];
+    if (n_pairs) *n_pairs = robot->n_self_pairs;
     return DSEED_OK;
 }
 

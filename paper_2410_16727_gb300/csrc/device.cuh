@@ -211,10 +211,24 @@ struct WaypointAcc {
 #define DSEED_FRAME_LOOP _Pragma("unroll 1")
 #endif
 
-template <int MODE>
+// Self-collision scratch of one lane, in its warp's shared slice (element e of
+// lane l at sbuf[e * 32 + l]): the transforms (R row-major, p) of frames 1..6
+// for the later frames' pair tests, then per-frame deposits (force, moment) of
+// the pair reactions, applied to the joints that move that frame.
+constexpr int kSelfFrames = 6;
+constexpr int kSelfFloats = kSelfFrames * 12 + kSelfFrames * 6;   // per lane
+
+__device__ __forceinline__ unsigned long long frame_bits(const KRobot &rb, int a) {
+    const int b = rb.frame_begin[a - 1], e = rb.frame_begin[a];
+    const unsigned long long hi = e >= 64 ? ~0ull : ((1ull << e) - 1ull);
+    const unsigned long long lo = b >= 64 ? ~0ull : ((1ull << b) - 1ull);
+    return hi & ~lo;
+}
+
+template <int MODE, bool SELF = false>
 __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc, const SceneView &sv,
                                                const float (&q)[7], bool last, const Goal &G,
-                                               WaypointAcc &acc, float (&gq)[7]) {
+                                               WaypointAcc &acc, float (&gq)[7], float *sbuf = nullptr) {
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
     constexpr bool KEEP = MODE == MODE_GRAD && !DSEED_ADJOINT_RECOMPUTE;
@@ -244,6 +258,81 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                 wj[ii][0] = w0; wj[ii][1] = w1; wj[ii][2] = w2;
             }
             bj[i] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
+        }
+        if (SELF) {
+            // C_self against frames a <= L - 2: for a checked pair (k on frame L, j on
+            // frame a) the hinge w_s max(0, r_k + r_j + eta_s - |c_k - c_j|) pushes
+            // sphere k with g = dC/dc_k = -w_s (c_k - c_j) / |c_k - c_j| (entered now,
+            // as for the world spheres of frame L) and sphere j with -g; the joints
+            // that move both see no net effect, so -g is deposited at c_k on frame a
+            // and cancels g for the joints that move frame a (added in the second pass)
+            const int lane = threadIdx.x & 31;
+            if (L == 1)
+                for (int e = 0; e < kSelfFrames * 6; ++e) sbuf[(kSelfFrames * 12 + e) * 32 + lane] = 0.f;
+            const unsigned fm = rb.self_frames[L - 1];
+            if (fm) {
+                const float4 fbL = rb.fbound[L - 1];
+                const float bx = fmaf(R[0], fbL.x, fmaf(R[1], fbL.y, fmaf(R[2], fbL.z, p[0])));
+                const float by = fmaf(R[3], fbL.x, fmaf(R[4], fbL.y, fmaf(R[5], fbL.z, p[1])));
+                const float bz = fmaf(R[6], fbL.x, fmaf(R[7], fbL.y, fmaf(R[8], fbL.z, p[2])));
+                for (int a = 1; a <= L - 2; ++a) {
+                    if (!((fm >> (a - 1)) & 1u)) continue;
+                    float Ra[12];
+#pragma unroll
+                    for (int e = 0; e < 12; ++e) Ra[e] = sbuf[((a - 1) * 12 + e) * 32 + lane];
+                    if (MODE != MODE_EVAL) {
+                        // frame-level bound: every sphere lies within fbound.w (radius included) of
+                        // its frame's bounding centre, so |c_k - c_j| - r_k - r_j >= dd - wL - wa
+                        const float4 fba = rb.fbound[a - 1];
+                        const float ax = fmaf(Ra[0], fba.x, fmaf(Ra[1], fba.y, fmaf(Ra[2], fba.z, Ra[9])));
+                        const float ay = fmaf(Ra[3], fba.x, fmaf(Ra[4], fba.y, fmaf(Ra[5], fba.z, Ra[10])));
+                        const float az = fmaf(Ra[6], fba.x, fmaf(Ra[7], fba.y, fmaf(Ra[8], fba.z, Ra[11])));
+                        const float dd = sqrtf((bx - ax) * (bx - ax) + (by - ay) * (by - ay) + (bz - az) * (bz - az));
+                        if (dd - fbL.w - fba.w >= kc.eta_s + 1e-4f) continue;
+                    }
+                    const unsigned long long abits = frame_bits(rb, a);
+                    for (int k = rb.frame_begin[L - 1]; k < rb.frame_begin[L]; ++k) {
+                        unsigned long long sel = rb.self_mask[k] & abits;
+                        if (!sel) continue;
+                        const float4 sk = rb.sph[k];
+                        const float ckx = fmaf(R[0], sk.x, fmaf(R[1], sk.y, fmaf(R[2], sk.z, p[0])));
+                        const float cky = fmaf(R[3], sk.x, fmaf(R[4], sk.y, fmaf(R[5], sk.z, p[1])));
+                        const float ckz = fmaf(R[6], sk.x, fmaf(R[7], sk.y, fmaf(R[8], sk.z, p[2])));
+                        while (sel) {
+                            const int j = __ffsll((long long)sel) - 1;
+                            sel &= sel - 1ull;
+                            const float4 sj = rb.sph[j];
+                            const float cjx = fmaf(Ra[0], sj.x, fmaf(Ra[1], sj.y, fmaf(Ra[2], sj.z, Ra[9])));
+                            const float cjy = fmaf(Ra[3], sj.x, fmaf(Ra[4], sj.y, fmaf(Ra[5], sj.z, Ra[10])));
+                            const float cjz = fmaf(Ra[6], sj.x, fmaf(Ra[7], sj.y, fmaf(Ra[8], sj.z, Ra[11])));
+                            const float dx = ckx - cjx, dy = cky - cjy, dz = ckz - cjz;
+                            const float dist = sqrtf(dx * dx + dy * dy + dz * dz);
+                            if (MODE == MODE_EVAL) acc.min_clear = fminf(acc.min_clear, dist - sk.w - sj.w);
+                            const float h = sk.w + sj.w + kc.eta_s - dist;
+                            if (h > 0.0f) {
+                                acc.c_world = fmaf(kc.w_s, h, acc.c_world);
+                                if (MODE == MODE_GRAD && dist > 0.0f) {
+                                    const float inv = kc.w_s / dist;
+                                    const float gx = -dx * inv, gy = -dy * inv, gz = -dz * inv;
+                                    const float mx = cky * gz - ckz * gy, my = ckz * gx - ckx * gz,
+                                                mz = ckx * gy - cky * gx;
+                                    Fx += gx; Fy += gy; Fz += gz;
+                                    Mx += mx; My += my; Mz += mz;
+                                    float *dep = sbuf + (kSelfFrames * 12 + (a - 1) * 6) * 32 + lane;
+                                    dep[0] -= gx; dep[32] -= gy; dep[64] -= gz;
+                                    dep[96] -= mx; dep[128] -= my; dep[160] -= mz;
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            if (L <= kSelfFrames) {
+#pragma unroll
+                for (int e = 0; e < 9; ++e) sbuf[((L - 1) * 12 + e) * 32 + lane] = R[e];
+#pragma unroll
+                for (int e = 0; e < 3; ++e) sbuf[((L - 1) * 12 + 9 + e) * 32 + lane] = p[e];
+            }
         }
         // frame L in voxel coordinates: u = Rv o + pv for an offset o
         float Rv[9], pv[3];
@@ -362,6 +451,15 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             // 42 values per waypoint live across the sphere loop
             float R2[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
             float p2[3] = {0.f, 0.f, 0.f};
+            // self-collision reactions deposited on frames 1..6: joint i moves frames
+            // >= i + 1, so it takes the deposits of frames a >= i + 1 (a suffix sum)
+            float SD[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+            if (SELF) {
+                const int lane = threadIdx.x & 31;
+                for (int a = 0; a < kSelfFrames; ++a)
+#pragma unroll
+                    for (int e = 0; e < 6; ++e) SD[e] += sbuf[(kSelfFrames * 12 + a * 6 + e) * 32 + lane];
+            }
 #pragma unroll
             for (int i = 0; i < 7; ++i) {
                 dh_step(R2, p2, rb.a[i], rb.d[i], rb.ca[i], rb.sa[i], cs[i], sn[i]);
@@ -370,6 +468,14 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                 const float w1 = z2 * p2[0] - z0 * p2[2];
                 const float w2 = z0 * p2[1] - z1 * p2[0];
                 gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i];
+                if (SELF) {
+                    gq[i] += (z0 * SD[3] + z1 * SD[4] + z2 * SD[5]) - (w0 * SD[0] + w1 * SD[1] + w2 * SD[2]);
+                    if (i < kSelfFrames) {
+                        const int lane = threadIdx.x & 31;
+#pragma unroll
+                        for (int e = 0; e < 6; ++e) SD[e] -= sbuf[(kSelfFrames * 12 + i * 6 + e) * 32 + lane];
+                    }
+                }
             }
         }
     }
@@ -387,7 +493,13 @@ __host__ __device__ constexpr int warp_smem_floats(int T) { return 4 * (T + kPad
 
 struct WarpSmem {
     float *xs, *es, *gs, *xa, *ga, *dd, *v;
+    float *self;      // [kSelfFloats][32] self-collision scratch (SELF kernels only)
 };
+
+// Per-warp shared floats, with the self-collision scratch when SELF.
+__host__ __device__ constexpr int warp_smem_floats(int T, bool self) {
+    return warp_smem_floats(T) + (self ? kSelfFloats * 32 : 0);
+}
 
 __device__ __forceinline__ WarpSmem carve(float *base, int T) {
     WarpSmem w;
@@ -398,6 +510,7 @@ __device__ __forceinline__ WarpSmem carve(float *base, int T) {
     w.ga = w.xa + T * 7;
     w.dd = w.ga + T * 7;
     w.v = w.dd + T * 7;
+    w.self = w.v + 32;
     return w;
 }
 
@@ -410,7 +523,7 @@ struct EvalOut {
 // Cost (MODE_COST), cost and gradient into ws.gs (MODE_GRAD), or cost and
 // success metrics (MODE_EVAL) of the trajectory held in ws.xs.  Warp-uniform
 // result.  ws.es rows T..T+2 must be zero (MODE_GRAD).
-template <int TPL, int MODE>
+template <int TPL, int MODE, bool SELF = false>
 __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, const SceneView &sv,
                                              int T, const Goal &G, const WarpSmem &ws, bool want_terms) {
     const int lane = threadIdx.x & 31;
@@ -430,7 +543,7 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
 #pragma unroll
             for (int j = 0; j < 7; ++j) q[j] = y[j];
             WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
-            waypoint_terms<MODE>(rb, kc, sv, q, t0 == T - 1, G, acc, gq[u]);
+            waypoint_terms<MODE, SELF>(rb, kc, sv, q, t0 == T - 1, G, acc, gq[u], ws.self);
             c_world += acc.c_world;
             c_goal += acc.c_goal;
             if (MODE == MODE_EVAL) {

@@ -25,10 +25,15 @@ struct KRobot {
     float cf8, sf8;                          // cos / sin of the flange frame's fixed theta offset
     float4 sph[DSEED_MAX_SPHERES];           // offset xyz, radius (sorted by frame)
     int sph_orig[DSEED_MAX_SPHERES];         // index in the caller's description
+    // self-collision: bit j of self_mask[k] = the (sorted) pair (k, j) is checked;
+    // bit a - 1 of self_frames[L - 1] = frame a <= L - 2 has a checked pair with frame L
+    unsigned long long self_mask[DSEED_MAX_SPHERES];
+    unsigned self_frames[8];
 };
 
 struct KCost {
     float w_c, eta, inv_dt, w_v, w_a, w_j, w_p, w_R, w_l;
+    float w_s, eta_s;                        // self-collision hinge (w_s = 0: off)
 };
 
 struct KOpt {

@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(128) k_fk(const __grid_constant__ KRobot rb, c
 // One warp per trajectory.  A problem whose scene index is out of range, or
 // whose scene descriptor is unusable, gets a NaN cost, NaN gradient and no
 // success (and no memory outside the inputs is touched).
-template <int TPL, int MODE>
+template <int TPL, int MODE, bool SELF>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_eval(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KBatch kb,
            const float *__restrict__ x, const float *__restrict__ grad_scale, float *__restrict__ cost,
@@ -65,7 +65,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     if (b >= B) return;
     const int T = kb.T, n = 7 * T;
     const int p = (int)(b / kb.S);
-    WarpSmem ws = carve(smem + wid * warp_smem_floats(T), T);
+    WarpSmem ws = carve(smem + wid * warp_smem_floats(T, SELF), T);
     const int si = kb.scene_of_problem[p];
     const bool in_table = si >= 0 && si < kb.n_scenes;
     if (!in_table || !load_scene(kb.scenes, si).ok) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const Goal G = make_goal(kb.goal + (size_t)p * 7);
     const SceneView sv = load_scene(kb.scenes, si);
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE>(rb, kc, sv, T, G, ws, terms != nullptr);
+    const EvalOut o = warp_eval<TPL, MODE, SELF>(rb, kc, sv, T, G, ws, terms != nullptr);
     __syncwarp();
     if (lane == 0) {
         if (cost) cost[b] = o.cost;
@@ -114,7 +114,9 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     }
 }
 
-static size_t eval_smem_bytes(int T) { return (size_t)kWarpsPerBlock * warp_smem_floats(T) * sizeof(float); }
+static size_t eval_smem_bytes(int T, bool self) {
+    return (size_t)kWarpsPerBlock * warp_smem_floats(T, self) * sizeof(float);
+}
 
 template <int MODE>
 static int launch_eval_mode(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x,
@@ -123,7 +125,8 @@ static int launch_eval_mode(const KRobot &rb, const KCost &kc, const KBatch &kb,
     const long long B = (long long)kb.P * kb.S;
     if (B == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((B + kWarpsPerBlock - 1) / kWarpsPerBlock);
-    const size_t smem = eval_smem_bytes(kb.T);
+    const bool self = kc.w_s > 0.f;
+    const size_t smem = eval_smem_bytes(kb.T, self);
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -132,9 +135,14 @@ static int launch_eval_mode(const KRobot &rb, const KCost &kc, const KBatch &kb,
         kern<<<blocks, kWarpsPerBlock * 32, smem, st>>>(rb, kc, kb, x, grad_scale, cost, terms, grad, success, metrics);
         return (int)cudaGetLastError();
     };
-    if (kb.T <= 32) return go(k_eval<1, MODE>);
-    if (kb.T <= 64) return go(k_eval<2, MODE>);
-    return go(k_eval<4, MODE>);
+    if (self) {
+        if (kb.T <= 32) return go(k_eval<1, MODE, true>);
+        if (kb.T <= 64) return go(k_eval<2, MODE, true>);
+        return go(k_eval<4, MODE, true>);
+    }
+    if (kb.T <= 32) return go(k_eval<1, MODE, false>);
+    if (kb.T <= 64) return go(k_eval<2, MODE, false>);
+    return go(k_eval<4, MODE, false>);
 }
 
 int launch_cost(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x, float *cost, float *terms,

@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 // update) -> success test of the accepted point -> outputs.  best_key[p] holds
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
 // their bit patterns order like the values); it must start at ~0.
-template <int TPL, int MH>
-__global__ void __launch_bounds__(kPlanWarps * 32, DSEED_PLAN_MINBLOCKS)
+template <int TPL, int MH, bool SELF>
+__global__ void __launch_bounds__(kPlanWarps * 32, SELF ? 2 : DSEED_PLAN_MINBLOCKS)
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
            float *__restrict__ hist_y, unsigned long long *__restrict__ best_key, float *traj,
@@ -109,7 +109,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32, DSEED_PLAN_MINBLOCKS)
     if (b >= B) return;
     const int T = kb.T, n = 7 * T, m = ko.m;
     const int p = (int)(b / kb.S);
-    WarpSmem ws = carve(smem + wid * warp_smem_floats(T), T);
+    WarpSmem ws = carve(smem + wid * warp_smem_floats(T, SELF), T);
     float *xt = ws.xs + kPad * 7;
     const int si = kb.scene_of_problem[p];
     const bool in_table = si >= 0 && si < kb.n_scenes;
@@ -138,14 +138,14 @@ __global__ void __launch_bounds__(kPlanWarps * 32, DSEED_PLAN_MINBLOCKS)
     LbUni st{CUDART_INF_F, 1.0f, 0.0f, 0, -1, 1, 0};
     __syncwarp();
     for (int it = 0; it < ko.iters; ++it) {
-        const EvalOut o = warp_eval<TPL, MODE_GRAD>(rb, kc, sv, T, G, ws, false);
+        const EvalOut o = warp_eval<TPL, MODE_GRAD, SELF>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
         lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
     }
     // success test of the accepted point
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE_EVAL>(rb, kc, sv, T, G, ws, false);
+    const EvalOut o = warp_eval<TPL, MODE_EVAL, SELF>(rb, kc, sv, T, G, ws, false);
     for (int e = lane; e < n; e += 32) traj[b * n + e] = ws.xa[e];
     const bool free = o.min_clear >= 0.0f;
     const bool ok = free && o.pos_err < kb.delta_t && o.rot_err < kb.delta_r && o.lim_viol == 0.0f;
@@ -170,7 +170,9 @@ __global__ void k_best(int P, const unsigned long long *__restrict__ key, int *_
     if (p < P) best[p] = key[p] == ~0ull ? -1 : (int)(key[p] & 0xffffffffull);
 }
 
-static size_t plan_smem_bytes(int T) { return (size_t)kPlanWarps * warp_smem_floats(T) * sizeof(float); }
+static size_t plan_smem_bytes(int T, bool self = false) {
+    return (size_t)kPlanWarps * warp_smem_floats(T, self) * sizeof(float);
+}
 
 template <typename K>
 static int set_smem(K kern, size_t smem) {
@@ -210,7 +212,8 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
     if (e != cudaSuccess) return (int)e;
     const long long B = (long long)kb.P * kb.S;
     const unsigned blocks = (unsigned)((B + kPlanWarps - 1) / kPlanWarps);
-    const size_t smem = plan_smem_bytes(kb.T);
+    const bool self = kc.w_s > 0.f;
+    const size_t smem = plan_smem_bytes(kb.T, self);
     auto go = [&](auto kern) {
         int r = set_smem(kern, smem);
         if (r) return r;
@@ -219,9 +222,15 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
         return (int)cudaGetLastError();
     };
     int r;
-    if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5>) : go(k_plan<1, 0>);
-    else if (kb.T <= 64) r = go(k_plan<2, 0>);
-    else r = go(k_plan<4, 0>);
+    if (self) {
+        if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5, true>) : go(k_plan<1, 0, true>);
+        else if (kb.T <= 64) r = go(k_plan<2, 0, true>);
+        else r = go(k_plan<4, 0, true>);
+    } else {
+        if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5, false>) : go(k_plan<1, 0, false>);
+        else if (kb.T <= 64) r = go(k_plan<2, 0, false>);
+        else r = go(k_plan<4, 0, false>);
+    }
     if (r) return r;
     k_best<<<(kb.P + 127) / 128, 128, 0, st>>>(kb.P, best_key, best);
     return (int)cudaGetLastError();

@@ -52,6 +52,11 @@ FRANKA_LIMITS = np.array([
     [-2.8973, 2.8973],
 ], dtype=np.float64)
 
+# The arm's "ready" configuration (manufacturer's home pose), used as the reference
+# pose of the self-collision pair rule.
+FRANKA_READY = np.array([0.0, -math.pi / 4, 0.0, -3 * math.pi / 4, 0.0, math.pi / 2, math.pi / 4],
+                        dtype=np.float64)
+
 # Collision-sphere layout: for each frame 1..8, how many spheres, and the segment
 # (start, end) in that frame's coordinates along which they are spread.  The
 # segments follow the link bodies: each runs to the next joint origin as read off
@@ -77,6 +82,10 @@ class Robot:
     sph_frame: np.ndarray   # [Ns] int32: frame index 1..8 the sphere is fixed to
     sph_o: np.ndarray       # [Ns][3] float32: offset in that frame (m)
     sph_r: np.ndarray       # [Ns] float32: radius (m)
+    # self-collision pair rule: spheres on frames at least two apart whose
+    # surfaces are at least self_margin apart at the reference pose self_ref
+    self_ref: np.ndarray = dataclasses.field(default_factory=lambda: FRANKA_READY.astype(np.float32))
+    self_margin: float = 0.02
 
     @property
     def n_spheres(self) -> int:
@@ -124,10 +133,12 @@ class CostParams:
     w_p: float = 1e4        # goal position weight
     w_R: float = 1e3        # goal orientation weight
     w_l: float = 1e3        # joint-limit weight
+    w_self: float = 0.0     # self-collision hinge weight (0: the self term is off)
+    eta_self: float = 0.01  # self-collision margin (m)
 
     def as_array(self) -> np.ndarray:
         return np.array([self.w_c, self.eta, self.dt, self.w_v, self.w_a, self.w_j,
-                         self.w_p, self.w_R, self.w_l], dtype=np.float64)
+                         self.w_p, self.w_R, self.w_l, self.w_self, self.eta_self], dtype=np.float64)
 
 
 @dataclasses.dataclass

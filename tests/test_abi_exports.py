@@ -43,7 +43,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_library_loads_and_reports_version(libpath):
     lib = ctypes.CDLL(libpath)
     lib.dseed_abi_version.restype = ctypes.c_int
-    assert lib.dseed_abi_version() == 1
+    assert lib.dseed_abi_version() == 2
     lib.dseed_last_error.restype = ctypes.c_char_p
     assert lib.dseed_last_error() is not None
 

@@ -1,0 +1,122 @@
+"""GPU parity of the self-collision term (C_self) against the FP64 oracle:
+the checked-pair set, a two-sphere closed form, cost and gradient on
+trajectories with self contact (one and two waypoints per lane), the success
+metrics, and plans; the serving loop refuses the term."""
+import dataclasses
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from golden.read import read
+from gpu_helpers import rel_l2, to_np
+from paper_2410_16727_gb300 import api, binding as B, inputs as I
+
+pytestmark = pytest.mark.gpu
+
+COST = dataclasses.replace(I.CostParams(), w_self=100.0, eta_self=0.01)
+
+
+def _cuda(a):
+    return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    spec = I.WORKLOADS["tiny"]
+    cub, grids = I.make_scenes(spec)
+    orc = oracle.Oracle(I.make_robot(), COST, grids, cub, T=32)
+    wl = I.build_workload(spec, cub, grids, orc.clearance, orc.flange_pose, n_problems=8)
+    return wl, orc
+
+
+def _gpu(wl, T=None, S=None):
+    planner = api.Planner(wl.robot, COST, wl.opt)
+    planner.set_scenes(wl.cuboids, wl.grids)
+    batch = planner.batch(wl.q_start, wl.goal, wl.scene_of_problem, S or wl.S, T or wl.T)
+    return planner, batch
+
+
+def test_pair_set_matches_oracle(gpu_lib, tiny):
+    wl, orc = tiny
+    mask = B.Robot(wl.robot).self_pairs()
+    assert np.array_equal(mask, orc.self_mask)
+
+
+def test_two_sphere_closed_form(gpu_lib):
+    gold = read("franka_fk.txt")
+    r = 0.35
+    robot = dataclasses.replace(I.make_robot(), sph_frame=np.array([1, 8], np.int32),
+                                sph_o=np.zeros((2, 3), np.float32), sph_r=np.array([r, r], np.float32),
+                                self_margin=-10.0)
+    only = I.CostParams(w_c=0.0, w_v=0.0, w_a=0.0, w_j=0.0, w_p=0.0, w_R=0.0, w_l=0.0, w_self=100.0)
+    planner = api.Planner(robot, only)
+    spec = I.WORKLOADS["tiny"]
+    planner.set_scenes([np.zeros((0, 6), np.float32)], [spec.grid])
+    q0 = np.zeros((1, 7), np.float32)
+    batch = planner.batch(q0, np.array([[0, 0, 0, 1, 0, 0, 0]], np.float32), np.zeros(1, np.int32), 1, 1)
+    c, g = B.cost_grad(planner.robot, batch.desc, batch.pr, _cuda(q0.reshape(1, 1, 1, 7)))
+    d = float(np.linalg.norm(gold["zero_flange_p"] - gold["zero_origin_1"]))
+    want = only.w_self * (2 * float(np.float32(r)) + only.eta_self - d)
+    assert abs(float(c[0, 0]) - want) <= 1e-4 * want
+    assert abs(float(g[0, 0, 0, 0])) <= 1e-4
+
+
+@pytest.mark.parametrize("T", [32, 48])
+def test_cost_and_gradient_match_oracle(gpu_lib, tiny, T):
+    wl, orc = tiny
+    rng = np.random.default_rng(T)
+    planner, batch = _gpu(wl, T=T, S=16)
+    x = np.stack([I.random_trajectories(rng, wl.q_start[p], 16, T, wl.robot.limits, spread=1.5)
+                  for p in range(wl.P)]).astype(np.float32)
+    c, g = B.cost_grad(planner.robot, batch.desc, batch.pr, _cuda(x))
+    c, g = to_np(c), to_np(g)
+    n_self = 0
+    for p in range(wl.P):
+        wc, wg, terms = orc.cost(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], x[p], grad=True,
+                                 terms=True)
+        # the oracle's collision term with the self term off, to count trajectories in self contact
+        for s in range(16):
+            assert abs(c[p, s] - wc[s]) <= 1e-4 * max(abs(wc[s]), 1e-6), (p, s, c[p, s], wc[s])
+            assert rel_l2(g[p, s], wg[s]) <= 1e-3, (p, s)
+        n_self += int((terms[:, 0] > 0).sum())
+    assert n_self > 16
+
+
+def test_evaluate_matches_oracle(gpu_lib, tiny):
+    wl, orc = tiny
+    rng = np.random.default_rng(5)
+    planner, batch = _gpu(wl, S=8)
+    x = np.stack([I.random_trajectories(rng, wl.q_start[p], 8, wl.T, wl.robot.limits, spread=1.5)
+                  for p in range(wl.P)]).astype(np.float32)
+    ok, met = B.evaluate(planner.robot, batch.desc, batch.pr, _cuda(x))
+    met = to_np(met)
+    for p in range(wl.P):
+        wok, wmet = orc.evaluate(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], x[p])
+        assert np.abs(met[p, :, 0] - wmet[:, 0]).max() <= 1e-4          # min clearance incl. self pairs
+        far = np.abs(wmet[:, 0]) > 1e-3
+        assert np.array_equal(to_np(ok)[p][far].astype(bool), wok[far])
+
+
+def test_plan_agrees_with_oracle(gpu_lib, tiny):
+    wl, orc = tiny
+    planner, batch = _gpu(wl)
+    out = planner.plan(batch, wl.seeds)
+    ok = to_np(out["success"]).astype(bool)
+    ref = orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
+    agree = (ok == ref["success"]).mean()
+    assert agree >= 0.98, agree
+    both = ok & ref["success"]
+    if both.any():
+        rel = np.abs(to_np(out["cost"])[both] - ref["cost"][both]) / ref["cost"][both]
+        assert np.median(rel) < 1e-2
+    # the plans themselves are free of self-collision where they succeed
+    assert (to_np(out["metrics"])[ok][:, 0] >= 0).all() if "metrics" in out else True
+
+
+def test_server_refuses_self_term(gpu_lib, tiny):
+    wl, _ = tiny
+    from paper_2410_16727_gb300 import serving as SV
+    with pytest.raises(B.DseedError, match="self-collision"):
+        SV.Server(wl.robot, 1 << 26, cost=COST)
