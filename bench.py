@@ -28,6 +28,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, HERE)
 
+from paper_2410_16727_gb300 import dist as D  # noqa: E402
 from paper_2410_16727_gb300 import inputs as I  # noqa: E402
 
 METRIC = "seed-timestep cost+grad evals/s"
@@ -187,11 +188,7 @@ def run_gpu(args, rank: int, world: int):
     esdf_ms = [e[0].elapsed_time(e[1]) for e in evs]
     plan_ms = [e[1].elapsed_time(e[2]) for e in evs]
     step_ms = [a + b for a, b in zip(esdf_ms, plan_ms)]
-    ms = sum(step_ms) / len(step_ms)
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = D.max_over_ranks(sum(step_ms) / len(step_ms), dev)
     success_rate = float(out["success"].float().mean())
     solved = float((out["best"] >= 0).float().mean())
 
@@ -237,17 +234,13 @@ def run_gpu(args, rank: int, world: int):
         b.record(stream)
         b.synchronize()
         e_ms.append(a.elapsed_time(b))
-    e2e_ms = sum(e_ms) / len(e_ms) if e_ms else float("nan")
-    if world > 1:
-        t = torch.tensor([e2e_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = D.max_over_ranks(sum(e_ms) / len(e_ms) if e_ms else float("nan"), dev)
 
     plan_avg = sum(plan_ms) / len(plan_ms)
     esdf_avg = sum(esdf_ms) / len(esdf_ms)
     achieved = FLOP_PER_ST * st_evals / (plan_avg * 1e-3) / 1e12
     res = dict(
-        metric=METRIC, value=st_evals * world / (ms * 1e-3), unit=UNIT, n_gpus=world, steps=args.steps,
+        metric=METRIC, value=D.job_throughput(st_evals, ms, world), unit=UNIT, n_gpus=world, steps=args.steps,
         warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
         dtype="f32", data="synthetic",
         config={"workload": f"{spec.name}: {P} problems x {S} seeds x {T} waypoints, {iters} L-BFGS iterations, "
@@ -259,7 +252,7 @@ def run_gpu(args, rank: int, world: int):
         success_rate=success_rate, problems_solved=solved,
         wall_s_timed=wall,
         gpu_launches=(len(cub) + 255) // 256 + 2,
-        e2e={"value": st_evals * world / (e2e_ms * 1e-3) if e_ms else None, "unit": UNIT,
+        e2e={"value": D.job_throughput(st_evals, e2e_ms, world) if e_ms else None, "unit": UNIT,
              "ms_per_step": e2e_ms if e_ms else None,
              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
