@@ -368,9 +368,12 @@ def run_learned(args) -> dict:
         plain[it] = {"iters": it, "solved": round(sv, 4), "seed_success": round(ss, 4), "ms": round(dt * 1e3, 2)}
     out["heldout"] = {"problems": P, "scenes": 64, "plain_seeds": 64, "plain": list(plain.values())}
     learned = []
+    diff_only = []
     for S, d, it in ((64, 10, 20), (12, 5, 20), (12, 5, 10)):
         L.propose(net, robot, te, S, steps=d)                                  # warm-up
         seeds, t_d = timed(lambda: L.propose(net, robot, te, S, steps=d))
+        if it == 20:
+            diff_only.append({"samples": S, "ddim_steps": d, **L.diffusion_only(planner, te, seeds)})
         o, t_p = timed(lambda: L.solve(planner, te, seeds, it, chunk=P))
         sv, ss = score(o)
         total = (t_d + t_p) * 1e3
@@ -383,6 +386,7 @@ def run_learned(args) -> dict:
                         "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
                                                 if eq else None)})
     out["heldout"]["learned"] = learned
+    out["heldout"]["diffusion_only"] = diff_only
     # the (12, 5) proposal for all 512 problems as one CUDA-graph replay, without and
     # with cost-gradient guidance (Eq. 5, k = 60, n = 20)
     occ_all = te.occ[te.scene_of_problem.long()]

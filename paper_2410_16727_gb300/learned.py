@@ -171,12 +171,16 @@ class Dataset:
 
 
 def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int = 64, iters: int = 100,
-                  alpha: float = 4.0, nonlinear_rad: float = 0.3, seed: int = 0, chunk: int = 256) -> Dataset:
+                  alpha: float = 4.0, nonlinear_rad: float = 0.3, seed: int = 0, chunk: int = 256,
+                  reverse: bool = True) -> Dataset:
     """Solve every problem with S random seeds; keep the best successful
     trajectory of each solved problem.  A solution that leaves the straight
     start-goal joint line by more than `nonlinear_rad` counts as non-linear
     and gets weight 1 + alpha (the paper up-weights solutions a linear seed
-    does not reach, Eq. 2)."""
+    does not reach, Eq. 2).  With reverse, every solution is also added run
+    backwards (App. A.4 swaps start and goal): start = its last waypoint,
+    goal = the original start configuration and its flange pose, waypoints
+    y_{T-1}, ..., y_1, q_start."""
     T = 32
     P = ps.q_start.shape[0]
     opt = I.OptParams(iters=iters)
@@ -194,14 +198,23 @@ def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int =
     keep = torch.cat(keeps)
     traj = torch.cat(trajs)                                        # [M][T][7]
     qs, qg = ps.q_start[keep], ps.q_goal[keep]
+    goal = ps.goal[keep]
+    scene = ps.scene_of_problem[keep]
+    if reverse:
+        rq_s = traj[:, -1].contiguous()
+        rtraj = torch.cat([traj[:, :-1].flip(1), qs[:, None]], 1)
+        rgoal = planner.fk(qs)
+        traj = torch.cat([traj, rtraj])
+        qs, qg = torch.cat([qs, rq_s]), torch.cat([qg, ps.q_start[keep]])
+        goal = torch.cat([goal, rgoal])
+        scene = torch.cat([scene, scene])
     tt = torch.arange(1, T + 1, device=planner.device, dtype=torch.float32)[None, :, None] / T
     lin = qs[:, None, :] + tt * (qg - qs)[:, None, :]
     dev = (traj - lin).abs().amax(dim=(1, 2))
     weight = 1.0 + alpha * (dev > nonlinear_rad).float()
     qs_n, qg_n = normalise(robot, qs.contiguous()), normalise(robot, qg.contiguous())
     x0 = to_residual(normalise(robot, traj.contiguous()), linear_path(qs_n, qg_n, T))
-    return Dataset(x0, qs_n, qg_n, ps.goal[keep].contiguous(), ps.scene_of_problem[keep].long(), ps.occ,
-                   weight.contiguous())
+    return Dataset(x0, qs_n, qg_n, goal.contiguous(), scene.long(), ps.occ, weight.contiguous())
 
 
 class GraphStep:
@@ -465,6 +478,21 @@ def propose(net: DN.Denoiser, robot: I.Robot, ps: ProblemSet, S: int, steps: int
     """DDIM proposals for every problem of a problem set: [P][S][T][7]."""
     occ = ps.occ[ps.scene_of_problem.long()]
     return propose_for(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, S, steps, seed, bf16)
+
+
+def diffusion_only(planner: api.Planner, ps: ProblemSet, seeds: torch.Tensor) -> dict:
+    """Planning with the proposals alone (the paper's diffusion-only mode, App.
+    Table 8): per problem the proposal with the smallest translation error is
+    the plan; solved when that trajectory passes the success test (no
+    optimiser iterations)."""
+    P, S, T = seeds.shape[0], seeds.shape[1], seeds.shape[2]
+    b = api.Batch(ps.q_start, ps.goal, ps.scene_of_problem, ps.table, S, T, planner.cost, None, planner.device)
+    ok, met = B.evaluate(planner.robot, b.desc, b.pr, seeds.contiguous())
+    pick = met[..., 1].argmin(dim=1)
+    rows = torch.arange(P, device=seeds.device)
+    return dict(problems_solved=float(ok[rows, pick].float().mean()),
+                pos_err_median_mm=float(met[rows, pick, 1].median() * 1e3),
+                seed_success=float(ok.float().mean()))
 
 
 def evaluate(planner: api.Planner, ps: ProblemSet, seeds, iters: int) -> dict:

@@ -120,3 +120,28 @@ def test_cost_guided_sampling(trained):
                            rows, 5, True, True, (planner, te.table, te.scene_of_problem[:g], L.Guidance()))
     assert float((got - want).abs().max()) <= 1e-4
     pg.check()
+
+
+def test_reversed_samples_decode_to_valid_trajectories(trained):
+    """Start/goal reversal (App. A.4): a reversed sample decodes back to the
+    original trajectory run backwards, ending exactly at the original start,
+    whose flange pose is its goal."""
+    robot, planner, tr, data, net, losses, te = trained
+    M = data.x0.shape[0] // 2
+    lin = L.linear_path(data.qs, data.qg, 32)
+    q = L.normalise(robot, L.from_residual(data.x0, lin), inverse=True)
+    fwd, rev = q[:M], q[M:]
+    assert float((rev[:, :-1] - fwd[:, :-1].flip(1)).abs().max()) < 1e-4
+    qs_fwd = L.normalise(robot, data.qs[:M], inverse=True)
+    assert float((rev[:, -1] - qs_fwd).abs().max()) < 1e-4
+    pose = planner.fk(qs_fwd)
+    assert float((pose[:, :3] - data.goal[M:, :3]).abs().max()) < 1e-5
+
+
+def test_diffusion_only_planning(trained):
+    robot, planner, tr, data, net, losses, te = trained
+    seeds = L.propose(net, robot, te, 16, steps=10)
+    d = L.diffusion_only(planner, te, seeds)
+    assert 0.0 <= d["problems_solved"] <= 1.0
+    # the optimiser refines what diffusion alone proposes
+    assert L.evaluate(planner, te, seeds, 20)["problems_solved"] >= d["problems_solved"]
