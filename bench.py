@@ -313,6 +313,58 @@ def run_serving(args, rank: int) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------- tensor-core roofline
+
+def conv_tc_roofline() -> dict:
+    """The denoiser's widest layer as the DDIM sampler runs it for 32768
+    trajectories: a 256 -> 256-channel, 5-tap convolution over 262144 rows (8
+    waypoints each) with the fused group norm / Mish / FiLM epilogue, timed alone
+    with CUDA events (inputs larger than L2); achieved = 2 M N K / time against
+    the measured BF16 dense peak (burst figure: a kernel timed alone)."""
+    import torch
+    from paper_2410_16727_gb300 import binding as B
+
+    N, L, C, k = 32768, 8, 256, 5
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    x = torch.randn((N, L, C), device="cuda", generator=g).to(torch.bfloat16)
+    w = (torch.randn((C, k, C), device="cuda", generator=g) / (k * C) ** 0.5).to(torch.bfloat16)
+    bias, beta = torch.zeros(C, device="cuda"), torch.zeros(C, device="cuda")
+    gamma = torch.ones(C, device="cuda")
+    film = torch.randn((512, 2 * C), device="cuda", generator=g)
+    rows = torch.arange(512, device="cuda", dtype=torch.int32).repeat_interleave(64)
+    res = torch.randn((N * L, C), device="cuda", generator=g).to(torch.bfloat16)
+    out = torch.empty((N * L, C), dtype=torch.bfloat16, device="cuda")
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+
+    def run():
+        B.conv_tc(x, w, out, n_samples=N, L=L, taps=k, pad=k // 2, cout=C, bias=bias, epilogue=B.EPI_GN,
+                  rows_per_sample=L, gamma=gamma, beta=beta, film=film, sample_problem=rows, res=res, err=err)
+
+    for _ in range(3):
+        run()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(20)]
+    for a, b in evs:
+        a.record()
+        run()
+        b.record()
+    torch.cuda.synchronize()
+    if int(err.item()) != 0:
+        raise RuntimeError("conv_tc reported a pipeline wait that gave up")
+    ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    flop = 2.0 * N * L * C * (k * C)
+    achieved = flop / (ms * 1e-3) / 1e12
+    peak, src = None, "MEASURED_PEAKS.json bf16_tflops (burst)"
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        peak, src = 1900.0, "fallback 1.9 PFLOP/s bf16 burst"
+    return {"bound": "tensor", "kernel": "k_conv_tc<256, GN> (5-tap 256->256, 262144 rows, fused epilogue)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "ms": ms,
+            "peak_source": src, "traffic": None}
+
+
 # ---------------------------------------------------------------------------- learned proposal
 
 def run_learned(args) -> dict:
@@ -411,6 +463,8 @@ def run_learned(args) -> dict:
                                                     if eq else None)})
         del gall
     out["heldout"]["learned_graph"] = graphed
+
+    out["roofline_tc"] = conv_tc_roofline()
 
     # serving: the held-out problems as Poisson arrivals
     budget = 16 * 10 ** 9
