@@ -40,8 +40,8 @@ FLOP_PER_ST = 5800.0
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one k_plan launch per problem of the batched workload
 # (64 seeds x 32 waypoints x 100 iterations, 128^3 shelf ESDF): ncu capture of the
-# 32-problem case, 36.10 MB per launch, scaled by the problems processed.
-K_PLAN_DRAM_BYTES_PER_PROBLEM = 36.10e6 / 32
+# 32-problem case, 35.97 MB per launch, scaled by the problems processed.
+K_PLAN_DRAM_BYTES_PER_PROBLEM = 35.97e6 / 32
 
 
 def parse():
