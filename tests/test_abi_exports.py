@@ -70,3 +70,56 @@ def test_host_argument_checks_without_gpu(libpath):
         BD.Robot(r)
     h = BD.Robot(I.make_robot())
     assert h.n_spheres == 50
+
+
+def test_conv_tc_descriptor_checks_without_gpu(libpath):
+    """The tensor-core convolution validates its descriptor on the host: bad
+    shapes or alignment return EINVAL before anything reaches a device."""
+    from paper_2410_16727_gb300 import binding as BD
+    BD._lib = None
+    lib = BD.load()
+    fake = 1 << 20                                   # aligned, never dereferenced
+
+    def desc(**kw):
+        d = BD.ConvTc()
+        d.a0_dev, d.c0, d.n_samples, d.L, d.taps, d.pad = fake, 64, 16, 32, 5, 2
+        d.w_dev, d.cout, d.cout_pad, d.out_dev, d.out_ld, d.epilogue = fake, 64, 64, fake, 64, BD.EPI_BF16
+        for k, v in kw.items():
+            setattr(d, k, v)
+        return d
+
+    def rc(d):
+        return lib.dseed_nn_conv_tc(ctypes.byref(d), None)
+
+    assert rc(desc(c0=48)) == -1 and "multiples of 64" in BD.last_error()
+    assert rc(desc(cout_pad=32, cout=32, out_ld=32)) == -1
+    assert rc(desc(L=24)) == -1
+    assert rc(desc(taps=9)) == -1
+    assert rc(desc(pad=5)) == -1
+    assert rc(desc(a0_dev=fake + 4)) == -1 and "aligned" in BD.last_error()
+    assert rc(desc(epilogue=BD.EPI_GN)) == -1                       # no bias / gamma / beta
+    assert rc(desc(epilogue=BD.EPI_GN, bias_dev=fake, gamma_dev=fake, beta_dev=fake, rows_per_sample=3)) == -1
+    assert rc(desc(epilogue=BD.EPI_GN, bias_dev=fake, gamma_dev=fake, beta_dev=fake, rows_per_sample=32,
+                   cout=48, out_ld=64)) == -1
+    assert lib.dseed_nn_im2col1d_bf16(fake, 4, 8, 7, 3, 1, 1, 8, 24, fake, None) == -1   # C not a multiple of 8
+
+
+def test_robot_self_pairs_match_the_oracle_without_gpu(libpath):
+    """The self-collision pair set is computed on the host when the robot is
+    created; it equals the oracle's set, which is computed independently."""
+    import numpy as np
+
+    import oracle
+    from paper_2410_16727_gb300 import binding as BD
+    from paper_2410_16727_gb300 import inputs as I
+    BD._lib = None
+    robot = I.make_robot()
+    mask = BD.Robot(robot).self_pairs()
+    spec = I.WORKLOADS["tiny"]
+    orc = oracle.Oracle(robot, I.CostParams(), [spec.grid], [np.zeros((0, 6), np.float32)], T=1)
+    assert np.array_equal(mask, orc.self_mask)
+    assert int(mask.sum()) // 2 == orc.n_self_pairs == 767
+    bad = I.make_robot()
+    bad.self_margin = float("nan")
+    with pytest.raises(BD.DseedError, match="self_margin"):
+        BD.Robot(bad)
