@@ -37,7 +37,7 @@ def _worker(rank, world, port, out):
 
 def test_two_ranks_combine_like_the_benchmark():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:      # no fork of this (threaded) process
         out = m.dict()
         mp.start_processes(_worker, args=(world, _free_port(), out), nprocs=world, join=True, start_method="spawn")
         res = dict(out)
