@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=10000)
+    ap.add_argument("--serve-round-iters", type=int, default=10, help="L-BFGS iterations per serving round")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
     ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
     ap.add_argument("--learned-steps", type=int, default=6000, help="denoiser training steps (batch 256)")
@@ -286,10 +287,10 @@ def run_serving(args, rank: int) -> dict:
     sw = SV.build_serving_workload(n, cf, pf, n_scenes=64, seed=rank)
     budget = 120 * 10 ** 9
     out = {"workload": f"{n} requests, S in {{4,16,64,256}}, T in {{32,48,64}}, 64 scenes 64^3-192^3 at 1-2 cm, "
-                       f"100 iterations, 120 GB budget, rounds of 10 iterations"}
+                       f"100 iterations, 120 GB budget, rounds of {args.serve_round_iters} iterations"}
 
     def fresh():
-        sv = SV.Server(sw.robot, budget, max_requests=4096, round_iters=10)
+        sv = SV.Server(sw.robot, budget, max_requests=4096, round_iters=args.serve_round_iters)
         for s, (c, g) in enumerate(zip(sw.cuboids, sw.grids)):
             sv.add_scene(s, c, g)
         torch.cuda.synchronize()

@@ -62,6 +62,7 @@ int dseed_nn_gemm_f32(int trans_a, int trans_b, int M, int N, int K, float alpha
                       const float *B_dev, int ldb, float beta, float *C_dev, int ldc, const float *bias_dev,
                       cudaStream_t stream) {
     NEED(M >= 0 && N >= 0 && K >= 0, "gemm: negative size");
+    NEED(N <= 65535 * 64, "gemm: N above 4194240 (column tiles in the grid's y)");
     NEED((M == 0 || N == 0) || (C_dev && (K == 0 || (A_dev && B_dev))), "gemm: NULL operand");
     return cu(dseed::nn_gemm_f32(trans_a, trans_b, M, N, K, alpha, A_dev, lda, B_dev, ldb, beta, C_dev, ldc, bias_dev,
                                  stream), "gemm_f32");
@@ -70,6 +71,7 @@ int dseed_nn_gemm_f32(int trans_a, int trans_b, int M, int N, int K, float alpha
 int dseed_nn_gemm_bf16(int M, int N, int K, const void *A_dev, const void *W_dev, float *C_dev,
                        const float *bias_dev, cudaStream_t stream) {
     NEED(M >= 0 && N >= 0 && K >= 0 && K % 16 == 0, "gemm_bf16: sizes must be >= 0 and K a multiple of 16");
+    NEED(N <= 65535 * 64, "gemm_bf16: N above 4194240 (column tiles in the grid's y)");
     NEED((M == 0 || N == 0) || (A_dev && W_dev && C_dev), "gemm_bf16: NULL operand");
     return cu(dseed::nn_gemm_bf16(M, N, K, A_dev, W_dev, C_dev, bias_dev, stream), "gemm_bf16");
 }
@@ -90,6 +92,7 @@ int dseed_nn_col2im1d(const float *cols_dev, int N, int L, int C, int k, int s, 
 
 int dseed_nn_colsum(const float *y_dev, int R, int C, float *out_dev, int accumulate, cudaStream_t stream) {
     NEED(R >= 0 && C >= 1 && y_dev && out_dev, "colsum: bad arguments");
+    NEED(C <= 65535 * 32, "colsum: C above 2097120 (column blocks in the grid's y)");
     return cu(dseed::nn_colsum(y_dev, R, C, out_dev, accumulate, stream), "colsum");
 }
 

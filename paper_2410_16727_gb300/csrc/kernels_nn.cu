@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alp
     __shared__ float As[GK][GB + 4];
     __shared__ float Bs[GK][GB + 4];
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
-    const int m0 = blockIdx.y * GB, n0 = blockIdx.x * GB;
+    const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;     // row tiles in x: up to 2^31 - 1 of them
     const int kb = SPLIT ? blockIdx.z * kchunk : 0;
     const int ke = SPLIT ? min(K, kb + kchunk) : K;
     float acc[4][4] = {};
@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(256) k_gemm_bf16(int M, int N, int K, const __
     __shared__ __nv_bfloat16 Ws[TN][TK + 8];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int wm = warp >> 1, wn = warp & 1;            // 4 x 2 warps
-    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    const int m0 = blockIdx.x * TM, n0 = blockIdx.y * TN;
     float acc[2][4][4] = {};
     for (int k0 = 0; k0 < K; k0 += TK) {
         // 16-byte chunks (8 bf16); K % 8 == 0 (caller pads K to 16)
@@ -267,8 +267,8 @@ __global__ void k_col2im1d(const float *__restrict__ cols, int N, int L, int C, 
 // columns x 8 row lanes, grid.y = row chunks, partial sums added atomically
 __global__ void k_colsum(const float *__restrict__ y, int R, int C, int rows_per, float *__restrict__ out) {
     __shared__ float s[8][33];
-    const int c = blockIdx.x * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
-    const int r0 = blockIdx.y * rows_per, r1 = min(R, r0 + rows_per);
+    const int c = blockIdx.y * 32 + (threadIdx.x & 31), ty = threadIdx.x >> 5;
+    const int r0 = blockIdx.x * rows_per, r1 = min(R, r0 + rows_per);
     float acc = 0.f;
     if (c < C)
         for (int r = r0 + ty; r < r1; r += 8) acc += y[(size_t)r * C + c];
@@ -590,10 +590,10 @@ int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A
         splits = min(splits, K / 256);
         const int kchunk = ((K + splits - 1) / splits + GK - 1) / GK * GK;
         splits = (K + kchunk - 1) / kchunk;
-        dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB, splits);
+        dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB, splits);
         gemm_go<true>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk, st);
     } else {
-        dim3 grid((N + GB - 1) / GB, (M + GB - 1) / GB);
+        dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB);
         gemm_go<false>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, K, st);
     }
     return (int)cudaGetLastError();
@@ -601,7 +601,7 @@ int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A
 
 int nn_gemm_bf16(int M, int N, int K, const void *A, const void *W, float *C, const float *bias, cudaStream_t st) {
     if (M == 0 || N == 0) return cudaSuccess;
-    dim3 grid((N + TN - 1) / TN, (M + TM - 1) / TM);
+    dim3 grid((M + TM - 1) / TM, (N + TN - 1) / TN);
     k_gemm_bf16<<<grid, 256, 0, st>>>(M, N, K, (const __nv_bfloat16 *)A, (const __nv_bfloat16 *)W, C, bias);
     return (int)cudaGetLastError();
 }
@@ -643,7 +643,7 @@ int nn_colsum(const float *y, int R, int C, float *out, int accumulate, cudaStre
     }
     if (R == 0) return cudaSuccess;
     const int rows_per = 256;
-    dim3 grid((C + 31) / 32, (R + rows_per - 1) / rows_per);
+    dim3 grid((R + rows_per - 1) / rows_per, (C + 31) / 32);
     k_colsum<<<grid, 256, 0, st>>>(y, R, C, rows_per, out);
     return (int)cudaGetLastError();
 }

@@ -97,6 +97,28 @@ def test_tensor_core_unet_matches_oracle(gpu_lib, net):
         assert _rel(got[n], want[n]) <= 6e-2, n
 
 
+def test_tensor_core_unet_full_size_sampled(gpu_lib, net):
+    """The launch size of the sampler (512 problems x 64 samples = 32768
+    trajectories: 8192 tiles at the first level, many per persistent CTA):
+    sampled trajectories against the FP64 oracle, and the result of one
+    trajectory does not depend on the batch it runs in."""
+    N = 32768
+    inp = _inputs(net.spec, 64, seed=21)
+    rng = np.random.default_rng(22)
+    pick = rng.integers(0, 64, N)                       # every sample is one of 64 reference inputs
+    big = {k: v[pick] for k, v in inp.items()}
+    args = [_cuda(big[k]) for k in ("x0", "k", "qs", "qg", "goal", "occ")]
+    got = net.infer_tc(*args).cpu().numpy()
+    small = net.infer_tc(*[_cuda(inp[k]) for k in ("x0", "k", "qs", "qg", "goal", "occ")]).cpu().numpy()
+    for n in rng.choice(N, 64, replace=False):
+        np.testing.assert_array_equal(got[n], small[pick[n]])
+    ref_ids = np.unique(pick[rng.choice(N, 8, replace=False)])
+    want = DO.predict(net.spec, net.params.cpu().numpy(), inp["x0"][ref_ids], inp["k"][ref_ids], inp["qs"][ref_ids],
+                      inp["qg"][ref_ids], inp["goal"][ref_ids], inp["occ"][ref_ids])
+    for i, r in enumerate(ref_ids):
+        assert _rel(small[r], want[i]) <= 6e-2
+
+
 def test_ddim_sampling_paths_agree(gpu_lib, net):
     """DDIM with shared per-problem conditions: the tensor-core path and the
     FP32 path give the same trajectories up to BF16 rounding."""
@@ -142,6 +164,19 @@ def test_gemm_kernels_against_float64():
         out = _cuda(base.copy())
         B.nn("colsum", _cuda(y), R, Cn, out, 1)
         assert _rel(out.cpu().numpy(), y.astype(np.float64).sum(0) + base) <= 1e-5
+    # more row tiles than a grid's y dimension holds (65535): rows run along x
+    M, N, K = 65535 * 64 + 1000, 8, 16
+    A = rng.normal(size=(M, K)).astype(np.float32)
+    Bm = rng.normal(size=(N, K)).astype(np.float32)
+    C = torch.empty((M, N), device="cuda")
+    B.nn("gemm_f32", 0, 1, M, N, K, 1.0, _cuda(A), K, _cuda(Bm), K, 0.0, C, N, None)
+    rows = rng.choice(M, 256, replace=False)
+    rows[0] = M - 1
+    assert _rel(C[rows].cpu().numpy(), A[rows].astype(np.float64) @ Bm.T.astype(np.float64)) <= 1e-5
+    y = rng.normal(size=(65535 * 256 + 77, 2)).astype(np.float32)
+    out = torch.empty(2, device="cuda")
+    B.nn("colsum", _cuda(y), y.shape[0], 2, out, 0)
+    assert _rel(out.cpu().numpy(), y.astype(np.float64).sum(0)) <= 1e-4
     for (M, N, K) in [(300, 70, 48), (17, 129, 16), (1024, 256, 1280)]:
         A = rng.normal(size=(M, K)).astype(np.float32)
         W = rng.normal(size=(N, K)).astype(np.float32)
