@@ -146,8 +146,6 @@ def run_gpu(args, rank: int, world: int):
     # resident device inputs and outputs
     batch = planner.batch(wl.q_start, wl.goal, wl.scene_of_problem, S, T)
     seeds = torch.as_tensor(wl.seeds).to(dev)
-    cub_dev = [torch.as_tensor(c).to(dev) for c in cub]
-    esdfs = planner.esdfs
     ws = planner.workspace(batch)
     out = dict(traj=torch.empty((P, S, T, 7), device=dev), cost=torch.empty((P, S), device=dev),
                success=torch.empty((P, S), dtype=torch.uint8, device=dev),
@@ -159,7 +157,7 @@ def run_gpu(args, rank: int, world: int):
     def step(ev=None):
         if ev:
             ev[0].record(stream)
-        B.scene_build_esdf_batch(cub_dev, grids, esdfs)
+        planner.rebuild_scenes()
         if ev:
             ev[1].record(stream)
         B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
@@ -196,7 +194,7 @@ def run_gpu(args, rank: int, world: int):
     # end to end through the public API with host buffers: H2D of the step's
     # inputs (cuboids, starts, goals, scene ids, seeds) from pinned memory, the
     # step, D2H of trajectories, costs, success flags and best seeds
-    h_cub = [torch.as_tensor(c).pin_memory() for c in cub]
+    h_cub = planner.cub_packed.cpu().pin_memory()      # every scene's cuboids, packed
     h_q = torch.as_tensor(wl.q_start).pin_memory()
     h_goal = torch.as_tensor(wl.goal).pin_memory()
     h_sc = torch.as_tensor(wl.scene_of_problem).pin_memory()
@@ -205,18 +203,15 @@ def run_gpu(args, rank: int, world: int):
     d_q = batch.q_start
     d_goal = batch.goal
     d_sc = batch.scene_of_problem
-    h2d = sum(t.numel() * t.element_size() for t in h_cub) + sum(
-        t.numel() * t.element_size() for t in (h_q, h_goal, h_sc, h_seeds))
+    h2d = sum(t.numel() * t.element_size() for t in (h_cub, h_q, h_goal, h_sc, h_seeds))
     d2h = sum(t.numel() * t.element_size() for t in h_out.values())
 
     def e2e_step():
-        for hc, dc in zip(h_cub, cub_dev):
-            dc.copy_(hc, non_blocking=True)
         d_q.copy_(h_q, non_blocking=True)
         d_goal.copy_(h_goal, non_blocking=True)
         d_sc.copy_(h_sc, non_blocking=True)
         seeds.copy_(h_seeds, non_blocking=True)
-        B.scene_build_esdf_batch(cub_dev, grids, esdfs)
+        planner.rebuild_scenes(h_cub)                    # one copy of all cuboids, then the ESDF build
         B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
         for k, v in h_out.items():
             v.copy_(out[k], non_blocking=True)

@@ -77,12 +77,31 @@ class Planner:
 
     # -- scenes ---------------------------------------------------------------
     def set_scenes(self, cuboids: Sequence, grids: Sequence, out: Optional[List[torch.Tensor]] = None):
-        """Build (or rebuild in place, when `out` is given) one ESDF per scene on the device."""
-        cts = [_to(c, torch.float32, self.device).reshape(-1, 6) for c in cuboids]
-        esdfs = B.scene_build_esdf_batch(cts, grids, out)
-        self.esdfs, self.grids = esdfs, list(grids)
-        self.table = B.SceneTable(esdfs, grids, self.device)
-        return esdfs
+        """Build (or rebuild in place, when `out` is given) one ESDF per scene on the device.
+        The scenes' cuboids are kept in one packed device buffer, so that
+        rebuild_scenes() can refresh them from host memory with one copy."""
+        rows = [np.asarray(c, np.float32).reshape(-1, 6) if not isinstance(c, torch.Tensor)
+                else c.detach().reshape(-1, 6).to(torch.float32).cpu().numpy() for c in cuboids]
+        counts = [r.shape[0] for r in rows]
+        packed = np.concatenate(rows) if sum(counts) else np.zeros((0, 6), np.float32)
+        self.cub_packed = torch.as_tensor(np.ascontiguousarray(packed)).to(self.device)
+        offs = np.concatenate([[0], np.cumsum(counts)]).astype(int)
+        cts = [self.cub_packed[offs[i]:offs[i + 1]] for i in range(len(rows))]
+        if out is None:
+            out = [torch.empty((g.n[2], g.n[1], g.n[0]), dtype=torch.float32, device=self.device) for g in grids]
+        self.esdf_batch = B.EsdfBatch(cts, grids, out)
+        self.esdf_batch.run()
+        self.esdfs, self.grids = list(out), list(grids)
+        self.table = B.SceneTable(self.esdfs, grids, self.device)
+        return self.esdfs
+
+    def rebuild_scenes(self, packed_host: Optional[torch.Tensor] = None):
+        """Rebuild every ESDF of the current scene set; with packed_host (the
+        scenes' cuboids concatenated in set_scenes order, [sum n][6], pinned
+        for an asynchronous copy), first refresh the cuboids with one copy."""
+        if packed_host is not None:
+            self.cub_packed.copy_(packed_host.view(self.cub_packed.shape), non_blocking=True)
+        self.esdf_batch.run()
 
     # -- kinematics -----------------------------------------------------------
     def fk(self, q, spheres: bool = False):

@@ -376,6 +376,28 @@ def scene_build_esdf_batch(cuboids: Sequence[torch.Tensor], grids: Sequence,
     return res
 
 
+class EsdfBatch:
+    """A prepared dseed_scene_build_esdf_batch call: the job records for fixed
+    cuboid and ESDF tensors are built once, so a rebuild (new cuboid values in
+    the same tensors) costs one C call."""
+
+    def __init__(self, cuboids: Sequence[torch.Tensor], grids: Sequence, outs: Sequence[torch.Tensor]):
+        self.jobs = (EsdfJob * len(cuboids))()
+        self.keep = (list(cuboids), list(outs))
+        for q, (c, g, out) in enumerate(zip(cuboids, grids, outs)):
+            gg = make_grid(g)
+            n = int(c.shape[0])
+            self.jobs[q].cuboids_dev = _dev(c, torch.float32, f"cuboids[{q}]", (n, 6)) if n > 0 else None
+            self.jobs[q].n = n
+            self.jobs[q].grid = gg
+            self.jobs[q].esdf_dev = _dev(out, torch.float32, f"esdf[{q}]", (gg.nz, gg.ny, gg.nx))
+        self.n = len(cuboids)
+
+    def run(self):
+        _check(load().dseed_scene_build_esdf_batch(C.cast(self.jobs, C.c_void_p), self.n, _stream()),
+               "dseed_scene_build_esdf_batch")
+
+
 def fk(robot: Robot, q: torch.Tensor, spheres: bool = False):
     """Flange poses [N][7] (and sphere centres [N][Ns][3]) of q [N][7]."""
     N = int(q.shape[0])
