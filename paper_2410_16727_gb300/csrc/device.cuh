@@ -756,19 +756,28 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
         } else {
             int k = st.newest;
             for (int c = 0; c < h; ++c) {
+                // both vectors of the pair in one round of loads (y is not needed
+                // until the reduction of s^T q is in, but its latency overlaps it)
                 const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+                constexpr bool kPair = NPL <= 14;          // registers to spare for y
+                float yk[kPair ? NPL : 1];
                 float dot = 0.f;
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
                     const int e = lane + 32 * i;
-                    if (e < n) dot = fmaf(Sk[e], qv[i], dot);
+                    if (kPair) yk[kPair ? i : 0] = 0.f;
+                    if (e < n) {
+                        dot = fmaf(Sk[e], qv[i], dot);
+                        if (kPair) yk[kPair ? i : 0] = Yk[e];
+                    }
                 }
                 const float a = ws.v[k] * warp_sum(dot);
                 if (lane == 0) ws.v[16 + c] = a;
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
                     const int e = lane + 32 * i;
-                    if (e < n) qv[i] = fmaf(-a, Yk[e], qv[i]);
+                    if (kPair) qv[i] = fmaf(-a, yk[kPair ? i : 0], qv[i]);
+                    else if (e < n) qv[i] = fmaf(-a, Yk[e], qv[i]);
                 }
                 k = ring_prev(k, m);
             }
@@ -780,17 +789,24 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
             for (int c = h - 1; c >= 0; --c) {
                 k = ring_next(k, m);
                 const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
+                constexpr bool kPair = NPL <= 14;
+                float sk[kPair ? NPL : 1];
                 float dot = 0.f;
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
                     const int e = lane + 32 * i;
-                    if (e < n) dot = fmaf(Yk[e], qv[i], dot);
+                    if (kPair) sk[kPair ? i : 0] = 0.f;
+                    if (e < n) {
+                        dot = fmaf(Yk[e], qv[i], dot);
+                        if (kPair) sk[kPair ? i : 0] = Sk[e];
+                    }
                 }
                 const float cf = ws.v[16 + c] - ws.v[k] * warp_sum(dot);
 #pragma unroll
                 for (int i = 0; i < NPL; ++i) {
                     const int e = lane + 32 * i;
-                    if (e < n) qv[i] = fmaf(cf, Sk[e], qv[i]);
+                    if (kPair) qv[i] = fmaf(cf, sk[kPair ? i : 0], qv[i]);
+                    else if (e < n) qv[i] = fmaf(cf, Sk[e], qv[i]);
                 }
             }
         }
