@@ -225,22 +225,32 @@ __device__ __forceinline__ unsigned long long frame_bits(const KRobot &rb, int a
     return hi & ~lo;
 }
 
+// Per-lane scratch of the frame loop (element e of lane l at fsc[e * 32], fsc
+// already offset by l): sin and cos of the joint angles [0, 14) and the adjoint
+// prefixes b_i [14, 21).  The loop runs rolled, so these are indexed by the
+// frame number; in shared memory they stay out of the L1 cache that the ESDF
+// gathers use.
+constexpr int kFrameScratch = 21;
+
 template <int MODE, bool SELF = false>
 __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc, const SceneView &sv,
-                                               const float (&q)[7], bool last, const Goal &G,
-                                               WaypointAcc &acc, float (&gq)[7], float *sbuf = nullptr) {
+                                               const float *q, bool last, const Goal &G, WaypointAcc &acc,
+                                               float (&gq)[7], float *fsc, float *sbuf = nullptr) {
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
     constexpr bool KEEP = MODE == MODE_GRAD && !DSEED_ADJOINT_RECOMPUTE;
-    float zj[KEEP ? 7 : 1][3], wj[KEEP ? 7 : 1][3], bj[7], sn[7], cs[7];
+    float zj[KEEP ? 7 : 1][3], wj[KEEP ? 7 : 1][3];
+    float *const sn = fsc, *const cs = fsc + 7 * 32, *const bj = fsc + 14 * 32;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
     DSEED_FRAME_LOOP
     for (int L = 1; L <= 8; ++L) {
         float st, ct;
         if (L <= 7) {
-            sincosf(q[L <= 7 ? L - 1 : 0] + rb.off[L - 1], &st, &ct);
-            sn[L <= 7 ? L - 1 : 0] = st;
-            cs[L <= 7 ? L - 1 : 0] = ct;
+            sincosf(q[L - 1] + rb.off[L - 1], &st, &ct);
+            if (MODE == MODE_GRAD) {
+                sn[(L - 1) * 32] = st;
+                cs[(L - 1) * 32] = ct;
+            }
         } else {
             st = rb.sf8;
             ct = rb.cf8;
@@ -257,7 +267,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                 zj[ii][0] = z0; zj[ii][1] = z1; zj[ii][2] = z2;
                 wj[ii][0] = w0; wj[ii][1] = w1; wj[ii][2] = w2;
             }
-            bj[i] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
+            bj[i * 32] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
         }
         if (SELF) {
             // C_self against frames a <= L - 2: for a checked pair (k on frame L, j on
@@ -443,7 +453,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             for (int i = 0; i < 7; ++i) {
                 const int ii = KEEP ? i : 0;
                 gq[i] += (zj[ii][0] * Mx + zj[ii][1] * My + zj[ii][2] * Mz)
-                         - (wj[ii][0] * Fx + wj[ii][1] * Fy + wj[ii][2] * Fz) - bj[i];
+                         - (wj[ii][0] * Fx + wj[ii][1] * Fy + wj[ii][2] * Fz) - bj[i * 32];
             }
         } else {
             // second pass: rebuild the joint axes z_i and origins p_i from the
@@ -462,12 +472,12 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             }
 #pragma unroll
             for (int i = 0; i < 7; ++i) {
-                dh_step(R2, p2, rb.a[i], rb.d[i], rb.ca[i], rb.sa[i], cs[i], sn[i]);
+                dh_step(R2, p2, rb.a[i], rb.d[i], rb.ca[i], rb.sa[i], cs[i * 32], sn[i * 32]);
                 const float z0 = R2[2], z1 = R2[5], z2 = R2[8];
                 const float w0 = z1 * p2[2] - z2 * p2[1];
                 const float w1 = z2 * p2[0] - z0 * p2[2];
                 const float w2 = z0 * p2[1] - z1 * p2[0];
-                gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i];
+                gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i * 32];
                 if (SELF) {
                     gq[i] += (z0 * SD[3] + z1 * SD[4] + z2 * SD[5]) - (w0 * SD[0] + w1 * SD[1] + w2 * SD[2]);
                     if (i < kSelfFrames) {
@@ -484,12 +494,17 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
 // ----------------------------------------------------------------- one trajectory
 // Shared-memory slice of one warp (floats):
 //   xs [(T + 3) * 7]   y_-2, y_-1, y_0 (= q_start) then the trial waypoints 1..T
-//   es [3 * (T + 3) * 7] velocity / acceleration / jerk adjoint weights, rows >= T zero
+//   es [3 * (T + 3) * 7] velocity / acceleration / jerk adjoint weights, rows >= T zero;
+//                      before they are written, the lanes' frame-loop scratch (at least
+//                      21 * 32 floats)
 //   gs [T * 7]         gradient of the trial point
 //   xa, ga, dd [T * 7] accepted point, its gradient, current search direction (optimiser)
 //   v [32]             L-BFGS scalars: rho per slot [0, 8), y^T y of the newest pair [8],
 //                      alpha_i of the two-loop [16, 24)
-__host__ __device__ constexpr int warp_smem_floats(int T) { return 4 * (T + kPad) * 7 + 4 * 7 * T + 32; }
+__host__ __device__ constexpr int es_floats(int T) {
+    return 3 * (T + kPad) * 7 > kFrameScratch * 32 ? 3 * (T + kPad) * 7 : kFrameScratch * 32;
+}
+__host__ __device__ constexpr int warp_smem_floats(int T) { return (T + kPad) * 7 + es_floats(T) + 4 * 7 * T + 32; }
 
 struct WarpSmem {
     float *xs, *es, *gs, *xa, *ga, *dd, *v;
@@ -505,7 +520,7 @@ __device__ __forceinline__ WarpSmem carve(float *base, int T) {
     WarpSmem w;
     w.xs = base;
     w.es = w.xs + (T + kPad) * 7;
-    w.gs = w.es + 3 * (T + kPad) * 7;
+    w.gs = w.es + es_floats(T);
     w.xa = w.gs + T * 7;
     w.ga = w.xa + T * 7;
     w.dd = w.ga + T * 7;
@@ -538,18 +553,27 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
 #pragma unroll
         for (int j = 0; j < 7; ++j) gq[u][j] = 0.f;
         if (t0 < T) {
-            const float *y = ws.xs + (t0 + kPad) * 7;   // y_t; y - 7 = y_{t-1}, ...
-            float q[7];
-#pragma unroll
-            for (int j = 0; j < 7; ++j) q[j] = y[j];
             WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
-            waypoint_terms<MODE, SELF>(rb, kc, sv, q, t0 == T - 1, G, acc, gq[u], ws.self);
+            waypoint_terms<MODE, SELF>(rb, kc, sv, ws.xs + (t0 + kPad) * 7, t0 == T - 1, G, acc, gq[u],
+                                       ws.es + lane, ws.self);
             c_world += acc.c_world;
             c_goal += acc.c_goal;
             if (MODE == MODE_EVAL) {
                 min_clear = fminf(min_clear, acc.min_clear);
                 if (t0 == T - 1) { pos_err = acc.pos_err; rot_err = acc.rot_err; }
             }
+        }
+    }
+    if (MODE == MODE_GRAD) {
+        // every lane is done with its frame scratch: restore the zero rows of es
+        __syncwarp();
+        for (int e = lane; e < kPad * 7 * 3; e += 32) ws.es[(e / (kPad * 7)) * R3 + T * 7 + e % (kPad * 7)] = 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < TPL; ++u) {
+        const int t0 = lane + 32 * u;
+        if (t0 < T) {
+            const float *y = ws.xs + (t0 + kPad) * 7;   // y_t; y - 7 = y_{t-1}, ...
 #pragma unroll
             for (int j = 0; j < 7; ++j) {
                 const float y0 = y[j], y1 = y[j - 7], y2 = y[j - 14], y3 = y[j - 21];
@@ -635,11 +659,12 @@ __device__ __forceinline__ int ring_next(int k, int m) { return k + 1 == m ? 0 :
 // d = -H g by the two-loop recursion, and the next trial point into xt_next
 // (may alias xt).  S, Y: this seed's history [m][n] in global memory, by ring
 // slot; rho = 1 / s^T y per slot in ws.v[0..m), y^T y of the newest pair in
-// ws.v[8].  With MH > 0 (m <= MH) the history is first loaded into registers
-// so the two loops wait on one round of loads instead of one per pair.  After
-// a rejected trial g and the history are unchanged, so the stored direction
-// ws.dd is reused (the recursion would give the same numbers).
-template <int NPL, int MH>
+// ws.v[8]; the alphas of the first loop go to ws.v[16 + c].  The history is
+// read from L2 in both loops, one round of loads per pair (s and y together),
+// which leaves the registers to more resident warps.  After a rejected trial g
+// and the history are unchanged, so the stored direction ws.dd is reused (the
+// recursion would give the same numbers).
+template <int NPL>
 __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, const float *xt,
                                              const float *gt, float ft, const WarpSmem &ws,
                                              float *__restrict__ S, float *__restrict__ Y, float *xt_next) {
@@ -705,55 +730,10 @@ __device__ __forceinline__ void lbfgs_update(const KOpt &ko, int n, LbUni &st, c
     if (new_dir) {
         // two-loop recursion: newest to oldest, then oldest to newest
         const int h = st.hist;
-        float qv[NPL], al[MH > 0 ? MH : DSEED_MAX_HISTORY];
+        float qv[NPL];
 #pragma unroll
         for (int i = 0; i < NPL; ++i) qv[i] = gv[i];
-        if (MH > 0) {
-            float Sr[MH > 0 ? MH : 1][NPL], Yr[MH > 0 ? MH : 1][NPL], rr[MH > 0 ? MH : 1];
-            int k = st.newest;
-#pragma unroll
-            for (int c = 0; c < (MH > 0 ? MH : 1); ++c) {      // c = 0 newest
-                rr[c] = 0.f;
-#pragma unroll
-                for (int i = 0; i < NPL; ++i) { Sr[c][i] = 0.f; Yr[c][i] = 0.f; }
-                if (c < h) {
-                    rr[c] = ws.v[k];
-                    const float *Sk = S + (size_t)k * n, *Yk = Y + (size_t)k * n;
-#pragma unroll
-                    for (int i = 0; i < NPL; ++i) {
-                        const int e = lane + 32 * i;
-                        if (e < n) { Sr[c][i] = Sk[e]; Yr[c][i] = Yk[e]; }
-                    }
-                    k = ring_prev(k, m);
-                }
-            }
-#pragma unroll
-            for (int c = 0; c < (MH > 0 ? MH : 1); ++c) {
-                al[c] = 0.f;
-                if (c < h) {
-                    float dot = 0.f;
-#pragma unroll
-                    for (int i = 0; i < NPL; ++i) dot = fmaf(Sr[c][i], qv[i], dot);
-                    al[c] = rr[c] * warp_sum(dot);
-#pragma unroll
-                    for (int i = 0; i < NPL; ++i) qv[i] = fmaf(-al[c], Yr[c][i], qv[i]);
-                }
-            }
-            const float gamma = h > 0 ? (1.0f / rr[0]) / ws.v[8] : ko.gamma0;
-#pragma unroll
-            for (int i = 0; i < NPL; ++i) qv[i] *= gamma;
-#pragma unroll
-            for (int c = (MH > 0 ? MH : 1) - 1; c >= 0; --c) {
-                if (c < h) {
-                    float dot = 0.f;
-#pragma unroll
-                    for (int i = 0; i < NPL; ++i) dot = fmaf(Yr[c][i], qv[i], dot);
-                    const float cf = al[c] - rr[c] * warp_sum(dot);
-#pragma unroll
-                    for (int i = 0; i < NPL; ++i) qv[i] = fmaf(cf, Sr[c][i], qv[i]);
-                }
-            }
-        } else {
+        {
             int k = st.newest;
             for (int c = 0; c < h; ++c) {
                 // both vectors of the pair in one round of loads (y is not needed

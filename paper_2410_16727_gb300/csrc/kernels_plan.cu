@@ -16,14 +16,15 @@ namespace dseed {
 #define DSEED_PLAN_WARPS 4
 #endif
 #ifndef DSEED_PLAN_MINBLOCKS
-#define DSEED_PLAN_MINBLOCKS 4
-#endif
-#ifndef DSEED_PLAN_PREFETCH_HISTORY
-#define DSEED_PLAN_PREFETCH_HISTORY 1
+#define DSEED_PLAN_MINBLOCKS 5
 #endif
 constexpr int kPlanWarps = DSEED_PLAN_WARPS;
-// history length up to which T <= 32 plans keep the L-BFGS history in registers
-constexpr int kPrefetchM = DSEED_PLAN_PREFETCH_HISTORY ? 5 : 0;
+// Resident blocks per SM that the register allocation is sized for.  A T <= 32
+// plan fits 96 registers without spills, so five blocks of four warps stay
+// resident (shared memory would allow six, but the 80-register build is
+// slower); longer horizons are held to three or fewer blocks by shared memory,
+// and the self-collision scratch leaves room for two.
+constexpr int plan_min_blocks(int tpl, bool self) { return self ? 2 : tpl == 1 ? DSEED_PLAN_MINBLOCKS : 4; }
 
 // ---------------------------------------------------------------- standalone L-BFGS
 __global__ void k_lbfgs_init(long long B, int n, int m, const float *__restrict__ x0, KLbfgsPtrs p) {
@@ -40,7 +41,7 @@ __global__ void k_lbfgs_init(long long B, int n, int m, const float *__restrict_
     }
 }
 
-template <int NPL, int MH>
+template <int NPL>
 __global__ void __launch_bounds__(kPlanWarps * 32)
     k_lbfgs_step(const __grid_constant__ KOpt ko, long long B, int T, const float *__restrict__ f_trial,
                  const float *__restrict__ g_trial, KLbfgsPtrs p) {
@@ -69,8 +70,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
     st.first = p.meta[b * 4 + 2];
     st.accepts = p.meta[b * 4 + 3];
     __syncwarp();
-    lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, f_trial[b], ws, p.s + (size_t)b * m * n, p.y + (size_t)b * m * n,
-                          xt);
+    lbfgs_update<NPL>(ko, n, st, xt, ws.gs, f_trial[b], ws, p.s + (size_t)b * m * n, p.y + (size_t)b * m * n, xt);
     for (int e = lane; e < n; e += 32) {
         p.x_trial[b * n + e] = xt[e];
         p.x[b * n + e] = ws.xa[e];
@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 // update) -> success test of the accepted point -> outputs.  best_key[p] holds
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
 // their bit patterns order like the values); it must start at ~0.
-template <int TPL, int MH, bool SELF>
-__global__ void __launch_bounds__(kPlanWarps * 32, SELF ? 2 : DSEED_PLAN_MINBLOCKS)
+template <int TPL, bool SELF>
+__global__ void __launch_bounds__(kPlanWarps * 32, plan_min_blocks(TPL, SELF))
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
            float *__restrict__ hist_y, unsigned long long *__restrict__ best_key, float *traj,
@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32, SELF ? 2 : DSEED_PLAN_MINBLOC
     for (int it = 0; it < ko.iters; ++it) {
         const EvalOut o = warp_eval<TPL, MODE_GRAD, SELF>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
-        lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
+        lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
     }
     // success test of the accepted point
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
@@ -199,9 +199,9 @@ int launch_lbfgs_step(const KOpt &ko, int B, int T, const float *f_trial, const 
         kern<<<blocks, kPlanWarps * 32, smem, st>>>(ko, (long long)B, T, f_trial, g_trial, p);
         return (int)cudaGetLastError();
     };
-    if (T <= 32) return ko.m <= 5 ? go(k_lbfgs_step<7, 5>) : go(k_lbfgs_step<7, 0>);
-    if (T <= 64) return go(k_lbfgs_step<14, 0>);
-    return go(k_lbfgs_step<28, 0>);
+    if (T <= 32) return go(k_lbfgs_step<7>);
+    if (T <= 64) return go(k_lbfgs_step<14>);
+    return go(k_lbfgs_step<28>);
 }
 
 int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch &kb, const float *seeds,
@@ -223,13 +223,13 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
     };
     int r;
     if (self) {
-        if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5, true>) : go(k_plan<1, 0, true>);
-        else if (kb.T <= 64) r = go(k_plan<2, 0, true>);
-        else r = go(k_plan<4, 0, true>);
+        if (kb.T <= 32) r = go(k_plan<1, true>);
+        else if (kb.T <= 64) r = go(k_plan<2, true>);
+        else r = go(k_plan<4, true>);
     } else {
-        if (kb.T <= 32) r = ko.m <= kPrefetchM ? go(k_plan<1, 5, false>) : go(k_plan<1, 0, false>);
-        else if (kb.T <= 64) r = go(k_plan<2, 0, false>);
-        else r = go(k_plan<4, 0, false>);
+        if (kb.T <= 32) r = go(k_plan<1, false>);
+        else if (kb.T <= 64) r = go(k_plan<2, false>);
+        else r = go(k_plan<4, false>);
     }
     if (r) return r;
     k_best<<<(kb.P + 127) / 128, 128, 0, st>>>(kb.P, best_key, best);

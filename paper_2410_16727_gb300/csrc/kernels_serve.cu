@@ -14,12 +14,13 @@
 namespace dseed {
 
 #ifndef DSEED_SERVE_MINBLOCKS
-#define DSEED_SERVE_MINBLOCKS 4
+#define DSEED_SERVE_MINBLOCKS 5
 #endif
 constexpr int kServeWarps = 4;
 
-template <int TPL, int MH>
-__global__ void __launch_bounds__(kServeWarps * 32, DSEED_SERVE_MINBLOCKS)
+// resident blocks per SM the registers are sized for (as for the one-shot plan)
+template <int TPL>
+__global__ void __launch_bounds__(kServeWarps * 32, TPL == 1 ? DSEED_SERVE_MINBLOCKS : 4)
     k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
             float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
     constexpr int NPL = 7 * TPL;
@@ -85,7 +86,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, DSEED_SERVE_MINBLOCKS)
     for (int it = 0; it < E.iters_round; ++it) {
         const EvalOut o = warp_eval<TPL, MODE_GRAD>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
-        lbfgs_update<NPL, MH>(ko, n, st, xt, ws.gs, o.cost, ws, S_, Y_, xt);
+        lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S_, Y_, xt);
     }
     if (!E.final_round) {
         for (int e = lane; e < n; e += 32) {
@@ -135,9 +136,9 @@ int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_
         kern<<<blocks, kServeWarps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
         return (int)cudaGetLastError();
     };
-    if (tpl == 1) return ko.m <= 5 ? go(k_serve<1, 5>) : go(k_serve<1, 0>);
-    if (tpl == 2) return go(k_serve<2, 0>);
-    return go(k_serve<4, 0>);
+    if (tpl == 1) return go(k_serve<1>);
+    if (tpl == 2) return go(k_serve<2>);
+    return go(k_serve<4>);
 }
 
 }  // namespace dseed
