@@ -22,6 +22,9 @@
  *   - joint limits: quadratic penalty outside [lower, upper],
  *   - self collision (C_self, optional): linear hinge w_s * max(0, r_i + r_j +
  *     eta_s - |c_i - c_j|) over the sphere pairs the robot marks as checked,
+ *   - swept collision (optional): the world hinge also at n_sweep joint-space
+ *     interpolants of every segment between consecutive waypoints (the robot
+ *     executes the trajectory by linear interpolation between waypoints),
  *   - success (Sec. 5.1 and Appendix A.6): collision free, translation error
  *     below delta_t, rotation error below delta_r, within limits,
  *   - optimiser: L-BFGS (history m) with Armijo accept/reject and step halving.
@@ -55,6 +58,7 @@ typedef struct {
 typedef struct {
     double w_c, eta, dt, w_v, w_a, w_j, w_p, w_R, w_l;
     double w_s, eta_s;       /* self-collision hinge weight and margin (w_s = 0: off) */
+    int n_sweep;             /* interpolants checked per segment (0: waypoints only) */
 } orc_cost_params;
 
 typedef struct {
@@ -351,6 +355,50 @@ static void quat_normalise(const double *in, double out[4])
     for (int i = 0; i < 4; ++i) out[i] = in[i] / n;
 }
 
+/* World hinge at one configuration q[7]: sum over spheres of
+ * w_c * max(0, r + eta - phi(c)).  gq (optional) receives its derivative with
+ * respect to q; min_clear (optional) is lowered to min over spheres of phi - r. */
+static double world_hinge(const orc_problem *pb, const double *q, double *gq, double *min_clear)
+{
+    const orc_robot *rb = pb->robot;
+    const orc_cost_params *cp = pb->cp;
+    double frames[9 * 16], zax[8][3], org[8][3], c_world = 0.0;
+    orc_fk(rb->dh, q, frames);
+    for (int i = 1; i <= 7; ++i) {
+        frame_zaxis(frames + 16 * i, zax[i]);
+        frame_origin(frames + 16 * i, org[i]);
+    }
+    if (gq) memset(gq, 0, sizeof(double) * 7);
+    for (int k = 0; k < rb->ns; ++k) {
+        int L = rb->sph_frame[k];
+        double c[3], gphi[3];
+        sphere_centre(frames, L, rb->sph_o + 3 * k, c);
+        double phi = orc_esdf_lookup(pb->grid, c, gphi);
+        if (min_clear && phi - rb->sph_r[k] < *min_clear) *min_clear = phi - rb->sph_r[k];
+        double h = rb->sph_r[k] + cp->eta - phi;
+        if (h <= 0.0) continue;
+        c_world += cp->w_c * h;
+        if (!gq) continue;
+        double dc[3] = { -cp->w_c * gphi[0], -cp->w_c * gphi[1], -cp->w_c * gphi[2] };
+        int top = L < 7 ? L : 7;
+        for (int i = 1; i <= top; ++i) {
+            double r[3] = { c[0] - org[i][0], c[1] - org[i][1], c[2] - org[i][2] }, J[3];
+            cross3(zax[i], r, J);
+            gq[i - 1] += dot3(dc, J);
+        }
+    }
+    return c_world;
+}
+
+/* Interpolant j (1..n_sweep) of segment t (1..T): q = (1 - u) y_t + u y_{t-1},
+ * u = j / (n_sweep + 1); returns u. */
+static double sweep_config(const orc_problem *pb, const double *x, int t, int j, double q[7])
+{
+    double u = (double)j / (double)(pb->cp->n_sweep + 1);
+    for (int i = 0; i < 7; ++i) q[i] = (1.0 - u) * traj_y(pb, x, t, i) + u * traj_y(pb, x, t - 1, i);
+    return u;
+}
+
 /* Total cost of x = [T][7] (waypoints 1..T).  grad (optional) receives dC/dx,
  * terms (optional) receives [C_world (+ C_self), C_smooth, C_goal, C_limit]. */
 double orc_cost(const orc_problem *pb, const double *x, double *grad, double *terms)
@@ -485,6 +533,21 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
         }
     }
     free(cent);
+
+    /* swept collision: the world hinge at the interpolants of every segment
+     * (y_{t-1}, y_t), t = 1..T; the derivative g at q reaches y_t with weight
+     * 1 - u and y_{t-1} (when it is optimised, t >= 2) with weight u */
+    for (int t = 1; t <= T; ++t)
+        for (int j = 1; j <= cp->n_sweep; ++j) {
+            double q[7], gq[7];
+            double u = sweep_config(pb, x, t, j, q);
+            c_world += world_hinge(pb, q, grad ? gq : NULL, NULL);
+            if (!grad) continue;
+            for (int i = 0; i < 7; ++i) {
+                grad[7 * (t - 1) + i] += (1.0 - u) * gq[i];
+                if (t >= 2) grad[7 * (t - 2) + i] += u * gq[i];
+            }
+        }
     if (terms) { terms[0] = c_world; terms[1] = c_smooth; terms[2] = c_goal; terms[3] = c_limit; }
     return c_world + c_smooth + c_goal + c_limit;
 }
@@ -494,7 +557,8 @@ double orc_cost(const orc_problem *pb, const double *x, double *grad, double *te
 /* ------------------------------------------------------------------------ */
 
 /* metrics[7] = min over waypoints/spheres of (phi - r) (and, with the self cost
- * on, of the checked pairs' |c_i - c_j| - r_i - r_j), translation error |p - p*|,
+ * on, of the checked pairs' |c_i - c_j| - r_i - r_j; with n_sweep > 0, also over
+ * the segments' interpolants and spheres), translation error |p - p*|,
  * rotation error 2 acos(|<q, q*>|), max |jerk| over waypoints and joints,
  * worst joint-limit violation, total cost, 1/0 collision free.
  * thr = [delta_t, delta_r].  Returns 1 on success. */
@@ -522,6 +586,11 @@ int orc_evaluate(const orc_problem *pb, const double *x, const double *thr, doub
                     double clr = sqrt(dot3(d, d)) - rb->sph_r[i] - rb->sph_r[j];
                     if (clr < min_clear) min_clear = clr;
                 }
+        for (int j = 1; j <= pb->cp->n_sweep; ++j) {
+            double q[7];
+            sweep_config(pb, x, t, j, q);
+            world_hinge(pb, q, NULL, &min_clear);
+        }
         for (int j = 0; j < 7; ++j) {
             double jk = (traj_y(pb, x, t, j) - 3.0 * traj_y(pb, x, t - 1, j)
                          + 3.0 * traj_y(pb, x, t - 2, j) - traj_y(pb, x, t - 3, j))

@@ -29,7 +29,7 @@ class _Robot(C.Structure):
 
 class _CostParams(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l",
-                                          "w_s", "eta_s")]
+                                          "w_s", "eta_s")] + [("n_sweep", C.c_int)]
 
 
 class _Grid(C.Structure):
@@ -206,7 +206,7 @@ class Oracle:
                                                          float(robot.self_margin),
                                                          self.self_mask.ctypes.data_as(C.POINTER(C.c_ubyte))))
         self.robot.self_pair = self.self_mask.ctypes.data_as(C.POINTER(C.c_ubyte))
-        self.cp = _CostParams(*[float(v) for v in cost.as_array()])
+        self.cp = _CostParams(*[float(v) for v in cost.as_array()], int(cost.n_sweep))
         self.grids_meta = list(grids)
         self.phis = [esdf_build(c, g) for c, g in zip(cuboids, grids)]
         self.grids = [_grid_struct(g, phi) for g, phi in zip(self.grids_meta, self.phis)]
@@ -280,10 +280,10 @@ class Oracle:
         return ok.astype(bool), met
 
     def clearance(self, scene: int, q) -> np.ndarray:
-        """min over spheres of (phi - r) for single configurations q [N][7]."""
+        """min over spheres of (phi - r) for single configurations q [N][7]
+        (each its own start, so a swept check adds nothing)."""
         q = _d(q).reshape(-1, 1, 7)
-        _, met = self.evaluate(scene, q[0, 0], None, q)
-        return met[:, 0]
+        return np.array([self.evaluate(scene, q[i, 0], None, q[i:i + 1])[1][0, 0] for i in range(q.shape[0])])
 
     # -- optimiser ------------------------------------------------------------
     def plan(self, scenes, q_start, goal, seeds, opt, thr=None, trace: bool = False) -> dict:

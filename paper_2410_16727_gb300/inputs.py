@@ -135,6 +135,7 @@ class CostParams:
     w_l: float = 1e3        # joint-limit weight
     w_self: float = 0.0     # self-collision hinge weight (0: the self term is off)
     eta_self: float = 0.01  # self-collision margin (m)
+    n_sweep: int = 0        # joint-space interpolants checked per segment between waypoints (0: off)
 
     def as_array(self) -> np.ndarray:
         return np.array([self.w_c, self.eta, self.dt, self.w_v, self.w_a, self.w_j,
