@@ -49,11 +49,12 @@
 extern "C" {
 #endif
 
-#define DSEED_ABI_VERSION 2
+#define DSEED_ABI_VERSION 3
 
 #define DSEED_MAX_SPHERES 64    /* collision spheres per robot */
 #define DSEED_MAX_T 128         /* waypoints per trajectory */
 #define DSEED_MAX_HISTORY 8     /* L-BFGS history length m */
+#define DSEED_MAX_SWEEP 8       /* interpolants per segment of the swept collision check */
 #define DSEED_ESDF_FAR 1000.0f  /* ESDF value of a scene with no cuboid (m) */
 
 /* status codes */
@@ -121,6 +122,12 @@ typedef struct {
                      * added to the collision term; with w_self > 0 a trajectory is collision free
                      * only if it is also free of self-collision */
     float eta_self; /* self-collision margin (m) */
+    int   n_sweep;  /* swept collision, 0..DSEED_MAX_SWEEP (0: waypoints only).  The robot executes a
+                     * trajectory by linear interpolation in joint space, so each segment (y_{t-1}, y_t),
+                     * t = 1..T with y_0 = q_start, is also checked at the n_sweep configurations
+                     * q = (1 - u) y_t + u y_{t-1}, u = j / (n_sweep + 1), j = 1..n_sweep: the collision
+                     * hinge (world term only) is added there, its derivative reaches y_t with weight 1 - u
+                     * and y_{t-1} with weight u, and the success test's clearance includes them */
 } DseedCostParams;
 
 /* L-BFGS settings.  One iteration = one cost+gradient evaluation of the trial

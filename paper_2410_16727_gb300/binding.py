@@ -49,7 +49,7 @@ COST_FIELDS = ("w_c", "eta", "dt", "w_v", "w_a", "w_j", "w_p", "w_R", "w_l", "w_
 
 
 class CostParams(C.Structure):
-    _fields_ = [(k, C.c_float) for k in COST_FIELDS]
+    _fields_ = [(k, C.c_float) for k in COST_FIELDS] + [("n_sweep", C.c_int)]
 
 
 class OptParams(C.Structure):
@@ -301,6 +301,7 @@ def plan_desc(P: int, S: int, T: int, cost, opt=None, delta_t: float = 0.005,
     d.P, d.S, d.T = int(P), int(S), int(T)
     for k, v in zip(COST_FIELDS, cost.as_array()):
         setattr(d.cost, k, float(v))
+    d.cost.n_sweep = int(cost.n_sweep)
     if opt is not None:
         d.opt.iters, d.opt.m = int(opt.iters), int(opt.m)
         d.opt.c1, d.opt.max_step = float(opt.c1), float(opt.max_step)

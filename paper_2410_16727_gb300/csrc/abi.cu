@@ -55,6 +55,8 @@ int check_desc(const DseedPlanDesc *d, bool need_opt) {
         if (!finite(v)) return fail(DSEED_EINVAL, "non-finite cost or success parameter");
     if (!(c.dt > 0.f)) return fail(DSEED_EINVAL, "dt must be > 0");
     if (c.w_self < 0.f || c.eta_self < 0.f) return fail(DSEED_EINVAL, "w_self and eta_self must be >= 0");
+    if (c.n_sweep < 0 || c.n_sweep > DSEED_MAX_SWEEP)
+        return fail(DSEED_EINVAL, "n_sweep = %d outside 0..%d", c.n_sweep, DSEED_MAX_SWEEP);
     if (need_opt) {
         const DseedOptParams &o = d->opt;
         if (o.iters < 1) return fail(DSEED_EINVAL, "iters = %d < 1", o.iters);
@@ -90,6 +92,8 @@ dseed::KCost make_cost(const DseedCostParams &c) {
     k.w_l = c.w_l;
     k.w_s = c.w_self;
     k.eta_s = c.eta_self;
+    k.n_sweep = c.n_sweep;
+    k.sweep_u = (float)(1.0 / (double)(c.n_sweep + 1));
     return k;
 }
 

@@ -232,10 +232,15 @@ __device__ __forceinline__ unsigned long long frame_bits(const KRobot &rb, int a
 // gathers use.
 constexpr int kFrameScratch = 21;
 
+// The configuration is q = qt (interp false) or the swept-check interpolant
+// q = qt + u (qp - qt) of the segment from qp = y_{t-1} to qt = y_t (interp
+// true: world term only, no goal or self term).
 template <int MODE, bool SELF = false>
 __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc, const SceneView &sv,
-                                               const float *q, bool last, const Goal &G, WaypointAcc &acc,
-                                               float (&gq)[7], float *fsc, float *sbuf = nullptr) {
+                                               const float *qt, const float *qp, float u, bool interp, bool last,
+                                               const Goal &G, WaypointAcc &acc, float (&gq)[7], float *fsc,
+                                               float *sbuf = nullptr) {
+    const bool self_on = SELF && !interp;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
     constexpr bool KEEP = MODE == MODE_GRAD && !DSEED_ADJOINT_RECOMPUTE;
@@ -246,7 +251,8 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
     for (int L = 1; L <= 8; ++L) {
         float st, ct;
         if (L <= 7) {
-            sincosf(q[L - 1] + rb.off[L - 1], &st, &ct);
+            const float qL = interp ? fmaf(u, qp[L - 1] - qt[L - 1], qt[L - 1]) : qt[L - 1];
+            sincosf(qL + rb.off[L - 1], &st, &ct);
             if (MODE == MODE_GRAD) {
                 sn[(L - 1) * 32] = st;
                 cs[(L - 1) * 32] = ct;
@@ -269,7 +275,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             }
             bj[i * 32] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
         }
-        if (SELF) {
+        if (self_on) {
             // C_self against frames a <= L - 2: for a checked pair (k on frame L, j on
             // frame a) the hinge w_s max(0, r_k + r_j + eta_s - |c_k - c_j|) pushes
             // sphere k with g = dC/dc_k = -w_s (c_k - c_j) / |c_k - c_j| (entered now,
@@ -464,7 +470,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             // self-collision reactions deposited on frames 1..6: joint i moves frames
             // >= i + 1, so it takes the deposits of frames a >= i + 1 (a suffix sum)
             float SD[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-            if (SELF) {
+            if (self_on) {
                 const int lane = threadIdx.x & 31;
                 for (int a = 0; a < kSelfFrames; ++a)
 #pragma unroll
@@ -478,7 +484,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                 const float w1 = z2 * p2[0] - z0 * p2[2];
                 const float w2 = z0 * p2[1] - z1 * p2[0];
                 gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i * 32];
-                if (SELF) {
+                if (self_on) {
                     gq[i] += (z0 * SD[3] + z1 * SD[4] + z2 * SD[5]) - (w0 * SD[0] + w1 * SD[1] + w2 * SD[2]);
                     if (i < kSelfFrames) {
                         const int lane = threadIdx.x & 31;
@@ -538,7 +544,7 @@ struct EvalOut {
 // Cost (MODE_COST), cost and gradient into ws.gs (MODE_GRAD), or cost and
 // success metrics (MODE_EVAL) of the trajectory held in ws.xs.  Warp-uniform
 // result.  ws.es rows T..T+2 must be zero (MODE_GRAD).
-template <int TPL, int MODE, bool SELF = false>
+template <int TPL, int MODE, bool SELF = false, bool SWEEP = false>
 __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, const SceneView &sv,
                                              int T, const Goal &G, const WarpSmem &ws, bool want_terms) {
     const int lane = threadIdx.x & 31;
@@ -547,20 +553,54 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
     float gq[TPL][7];
     const float inv_dt = kc.inv_dt;
     const int R3 = (T + kPad) * 7;
+    if (MODE == MODE_GRAD && SWEEP) {
+        // gs row t - 1 collects the interpolants' share of waypoint t - 1 from the lane of waypoint t
+        for (int e = lane; e < T * 7; e += 32) ws.gs[e] = 0.f;
+        __syncwarp();
+    }
 #pragma unroll
     for (int u = 0; u < TPL; ++u) {
         const int t0 = lane + 32 * u;   // waypoint t = t0 + 1
 #pragma unroll
         for (int j = 0; j < 7; ++j) gq[u][j] = 0.f;
-        if (t0 < T) {
+        if (t0 < T && !SWEEP) {
             WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
-            waypoint_terms<MODE, SELF>(rb, kc, sv, ws.xs + (t0 + kPad) * 7, t0 == T - 1, G, acc, gq[u],
-                                       ws.es + lane, ws.self);
+            const float *y = ws.xs + (t0 + kPad) * 7;
+            waypoint_terms<MODE, SELF>(rb, kc, sv, y, y, 0.0f, false, t0 == T - 1, G, acc, gq[u], ws.es + lane,
+                                       ws.self);
             c_world += acc.c_world;
             c_goal += acc.c_goal;
             if (MODE == MODE_EVAL) {
                 min_clear = fminf(min_clear, acc.min_clear);
                 if (t0 == T - 1) { pos_err = acc.pos_err; rot_err = acc.rot_err; }
+            }
+        }
+        if (t0 < T && SWEEP) {
+            const float *y = ws.xs + (t0 + kPad) * 7;   // y_t; y - 7 = y_{t-1} (y_0 = q_start)
+            // s = 0: the waypoint; s = 1..n_sweep: the interpolants of segment (y_{t-1}, y_t)
+            for (int s = 0; s <= kc.n_sweep; ++s) {
+                const float us = (float)s * kc.sweep_u;   // weight of y_{t-1}
+                float gw[7];
+#pragma unroll
+                for (int j = 0; j < 7; ++j) gw[j] = 0.f;
+                WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
+                waypoint_terms<MODE, SELF>(rb, kc, sv, y, y - 7, us, s > 0, s == 0 && t0 == T - 1, G, acc, gw,
+                                           ws.es + lane, ws.self);
+                c_world += acc.c_world;
+                c_goal += acc.c_goal;
+                if (MODE == MODE_EVAL) {
+                    min_clear = fminf(min_clear, acc.min_clear);
+                    if (s == 0 && t0 == T - 1) { pos_err = acc.pos_err; rot_err = acc.rot_err; }
+                }
+                if (MODE == MODE_GRAD) {
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) gq[u][j] = fmaf(1.0f - us, gw[j], gq[u][j]);
+                    if (s > 0 && t0 > 0) {
+                        float *gp = ws.gs + (t0 - 1) * 7;
+#pragma unroll
+                        for (int j = 0; j < 7; ++j) gp[j] = fmaf(us, gw[j], gp[j]);
+                    }
+                }
             }
         }
     }
@@ -619,6 +659,7 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
                     g += ev[j] - ev[j + 7];
                     g += ea[j] - 2.0f * ea[j + 7] + ea[j + 14];
                     g += ej[j] - 3.0f * ej[j + 7] + 3.0f * ej[j + 14] - ej[j + 21];
+                    if (SWEEP) g += ws.gs[t0 * 7 + j];      // from the interpolants after waypoint t
                     ws.gs[t0 * 7 + j] = g;
                 }
             }

@@ -34,6 +34,8 @@ struct KRobot {
 struct KCost {
     float w_c, eta, inv_dt, w_v, w_a, w_j, w_p, w_R, w_l;
     float w_s, eta_s;                        // self-collision hinge (w_s = 0: off)
+    int n_sweep;                             // interpolants per segment (0: waypoints only)
+    float sweep_u;                           // 1 / (n_sweep + 1): interpolant j sits at u = j sweep_u
 };
 
 struct KOpt {

@@ -1,6 +1,8 @@
 // kernels_eval.cu -- forward kinematics, cost, cost+adjoint and evaluation kernels.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace dseed {
@@ -52,7 +54,7 @@ __global__ void __launch_bounds__(128) k_fk(const __grid_constant__ KRobot rb, c
 // One warp per trajectory.  A problem whose scene index is out of range, or
 // whose scene descriptor is unusable, gets a NaN cost, NaN gradient and no
 // success (and no memory outside the inputs is touched).
-template <int TPL, int MODE, bool SELF>
+template <int TPL, int MODE, bool SELF, bool SWEEP>
 __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     k_eval(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KBatch kb,
            const float *__restrict__ x, const float *__restrict__ grad_scale, float *__restrict__ cost,
@@ -91,7 +93,7 @@ __global__ void __launch_bounds__(kWarpsPerBlock * 32)
     const Goal G = make_goal(kb.goal + (size_t)p * 7);
     const SceneView sv = load_scene(kb.scenes, si);
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE, SELF>(rb, kc, sv, T, G, ws, terms != nullptr);
+    const EvalOut o = warp_eval<TPL, MODE, SELF, SWEEP>(rb, kc, sv, T, G, ws, terms != nullptr);
     __syncwarp();
     if (lane == 0) {
         if (cost) cost[b] = o.cost;
@@ -135,14 +137,17 @@ static int launch_eval_mode(const KRobot &rb, const KCost &kc, const KBatch &kb,
         kern<<<blocks, kWarpsPerBlock * 32, smem, st>>>(rb, kc, kb, x, grad_scale, cost, terms, grad, success, metrics);
         return (int)cudaGetLastError();
     };
-    if (self) {
-        if (kb.T <= 32) return go(k_eval<1, MODE, true>);
-        if (kb.T <= 64) return go(k_eval<2, MODE, true>);
-        return go(k_eval<4, MODE, true>);
-    }
-    if (kb.T <= 32) return go(k_eval<1, MODE, false>);
-    if (kb.T <= 64) return go(k_eval<2, MODE, false>);
-    return go(k_eval<4, MODE, false>);
+    // variants: waypoints per lane x self-collision term x swept check
+    auto by_t = [&](auto self_c, auto sweep_c) {
+        constexpr bool kSelf = decltype(self_c)::value, kSweep = decltype(sweep_c)::value;
+        if (kb.T <= 32) return go(k_eval<1, MODE, kSelf, kSweep>);
+        if (kb.T <= 64) return go(k_eval<2, MODE, kSelf, kSweep>);
+        return go(k_eval<4, MODE, kSelf, kSweep>);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool sweep = kc.n_sweep > 0;
+    return self ? (sweep ? by_t(T_{}, T_{}) : by_t(T_{}, F_{})) : (sweep ? by_t(F_{}, T_{}) : by_t(F_{}, F_{}));
 }
 
 int launch_cost(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x, float *cost, float *terms,

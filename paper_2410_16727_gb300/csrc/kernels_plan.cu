@@ -8,6 +8,8 @@
 // independent, so no warp ever waits on another.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace dseed {
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 // update) -> success test of the accepted point -> outputs.  best_key[p] holds
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
 // their bit patterns order like the values); it must start at ~0.
-template <int TPL, bool SELF>
+template <int TPL, bool SELF, bool SWEEP>
 __global__ void __launch_bounds__(kPlanWarps * 32, plan_min_blocks(TPL, SELF))
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
@@ -138,14 +140,14 @@ __global__ void __launch_bounds__(kPlanWarps * 32, plan_min_blocks(TPL, SELF))
     LbUni st{CUDART_INF_F, 1.0f, 0.0f, 0, -1, 1, 0};
     __syncwarp();
     for (int it = 0; it < ko.iters; ++it) {
-        const EvalOut o = warp_eval<TPL, MODE_GRAD, SELF>(rb, kc, sv, T, G, ws, false);
+        const EvalOut o = warp_eval<TPL, MODE_GRAD, SELF, SWEEP>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
         lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
     }
     // success test of the accepted point
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE_EVAL, SELF>(rb, kc, sv, T, G, ws, false);
+    const EvalOut o = warp_eval<TPL, MODE_EVAL, SELF, SWEEP>(rb, kc, sv, T, G, ws, false);
     for (int e = lane; e < n; e += 32) traj[b * n + e] = ws.xa[e];
     const bool free = o.min_clear >= 0.0f;
     const bool ok = free && o.pos_err < kb.delta_t && o.rot_err < kb.delta_r && o.lim_viol == 0.0f;
@@ -221,16 +223,17 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
                                                    success, metrics);
         return (int)cudaGetLastError();
     };
-    int r;
-    if (self) {
-        if (kb.T <= 32) r = go(k_plan<1, true>);
-        else if (kb.T <= 64) r = go(k_plan<2, true>);
-        else r = go(k_plan<4, true>);
-    } else {
-        if (kb.T <= 32) r = go(k_plan<1, false>);
-        else if (kb.T <= 64) r = go(k_plan<2, false>);
-        else r = go(k_plan<4, false>);
-    }
+    // variants: waypoints per lane x self-collision term x swept check
+    auto by_t = [&](auto self_c, auto sweep_c) {
+        constexpr bool kSelf = decltype(self_c)::value, kSweep = decltype(sweep_c)::value;
+        if (kb.T <= 32) return go(k_plan<1, kSelf, kSweep>);
+        if (kb.T <= 64) return go(k_plan<2, kSelf, kSweep>);
+        return go(k_plan<4, kSelf, kSweep>);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool sweep = kc.n_sweep > 0;
+    const int r = self ? (sweep ? by_t(T_{}, T_{}) : by_t(T_{}, F_{})) : (sweep ? by_t(F_{}, T_{}) : by_t(F_{}, F_{}));
     if (r) return r;
     k_best<<<(kb.P + 127) / 128, 128, 0, st>>>(kb.P, best_key, best);
     return (int)cudaGetLastError();

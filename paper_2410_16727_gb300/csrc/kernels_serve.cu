@@ -14,13 +14,14 @@
 namespace dseed {
 
 #ifndef DSEED_SERVE_MINBLOCKS
-#define DSEED_SERVE_MINBLOCKS 5
+#define DSEED_SERVE_MINBLOCKS 4
 #endif
 constexpr int kServeWarps = 4;
 
-// resident blocks per SM the registers are sized for (as for the one-shot plan)
-template <int TPL>
-__global__ void __launch_bounds__(kServeWarps * 32, TPL == 1 ? DSEED_SERVE_MINBLOCKS : 4)
+// Four resident blocks (128 registers): the round's bookkeeping keeps more
+// values live than the one-shot plan, which spills at 96.
+template <int TPL, bool SWEEP>
+__global__ void __launch_bounds__(kServeWarps * 32, DSEED_SERVE_MINBLOCKS)
     k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
             float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
     constexpr int NPL = 7 * TPL;
@@ -84,7 +85,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, TPL == 1 ? DSEED_SERVE_MINBL
     const Goal G = make_goal(R + L.goal);
     __syncwarp();
     for (int it = 0; it < E.iters_round; ++it) {
-        const EvalOut o = warp_eval<TPL, MODE_GRAD>(rb, kc, sv, T, G, ws, false);
+        const EvalOut o = warp_eval<TPL, MODE_GRAD, false, SWEEP>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
         lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S_, Y_, xt);
     }
@@ -110,7 +111,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, TPL == 1 ? DSEED_SERVE_MINBL
     // last round: success test of the accepted point, outputs
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE_EVAL>(rb, kc, sv, T, G, ws, false);
+    const EvalOut o = warp_eval<TPL, MODE_EVAL, false, SWEEP>(rb, kc, sv, T, G, ws, false);
     for (int e = lane; e < n; e += 32) g_xa[e] = ws.xa[e];
     const bool ok = o.min_clear >= 0.0f && o.pos_err < delta_t && o.rot_err < delta_r && o.lim_viol == 0.0f;
     if (lane == 0) {
@@ -136,9 +137,14 @@ int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_
         kern<<<blocks, kServeWarps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
         return (int)cudaGetLastError();
     };
-    if (tpl == 1) return go(k_serve<1>);
-    if (tpl == 2) return go(k_serve<2>);
-    return go(k_serve<4>);
+    if (kc.n_sweep > 0) {
+        if (tpl == 1) return go(k_serve<1, true>);
+        if (tpl == 2) return go(k_serve<2, true>);
+        return go(k_serve<4, true>);
+    }
+    if (tpl == 1) return go(k_serve<1, false>);
+    if (tpl == 2) return go(k_serve<2, false>);
+    return go(k_serve<4, false>);
 }
 
 }  // namespace dseed

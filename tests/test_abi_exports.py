@@ -1,6 +1,7 @@
 """The C-ABI library builds for sm_103a and exports every entry point that
 include/dseed.h declares (no GPU needed: nothing is called but version/error)."""
 import ctypes
+import dataclasses
 import os
 import re
 import subprocess
@@ -43,7 +44,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_library_loads_and_reports_version(libpath):
     lib = ctypes.CDLL(libpath)
     lib.dseed_abi_version.restype = ctypes.c_int
-    assert lib.dseed_abi_version() == 2
+    assert lib.dseed_abi_version() == 3
     lib.dseed_last_error.restype = ctypes.c_char_p
     assert lib.dseed_last_error() is not None
 
@@ -63,6 +64,12 @@ def test_host_argument_checks_without_gpu(libpath):
     d = BD.plan_desc(2, 3, 32, I.CostParams(), I.OptParams(iters=5, m=5))
     assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == 0
     assert n.value >= 2 * 2 * 3 * 5 * 224 * 4
+    for bad in (-1, 9):                                           # swept check: 0..8 interpolants
+        d = BD.plan_desc(2, 3, 32, dataclasses.replace(I.CostParams(), n_sweep=bad), I.OptParams())
+        assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1
+        assert f"n_sweep = {bad}" in BD.last_error()
+    d = BD.plan_desc(2, 3, 32, dataclasses.replace(I.CostParams(), n_sweep=8), I.OptParams())
+    assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == 0
     r = I.make_robot()
     r.sph_r = r.sph_r.copy()
     r.sph_r[3] = -1.0
