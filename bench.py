@@ -38,10 +38,10 @@ UNIT = "ST-evals/s"
 FLOP_PER_ST = 5800.0
 # 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one k_plan launch per problem of the batched workload
-# (64 seeds x 32 waypoints x 100 iterations, 128^3 shelf ESDF): ncu capture of the
-# 32-problem case, 35.97 MB per launch, scaled by the problems processed.
-K_PLAN_DRAM_BYTES_PER_PROBLEM = 35.97e6 / 32
+# DRAM bytes (read + write) of one k_plan launch of the full batched workload (256
+# problems x 64 seeds x 32 waypoints x 100 iterations, 256 shelf ESDFs at 128^3):
+# ncu capture of that launch, 387.64 MB read + 191.05 MB written.
+K_PLAN_DRAM_BYTES_BATCHED = 387.64e6 + 191.05e6
 
 
 def parse():
@@ -58,6 +58,8 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=10000)
     ap.add_argument("--serve-round-iters", type=int, default=10, help="L-BFGS iterations per serving round")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-proposal comparison")
+    ap.add_argument("--sweep", type=int, default=2,
+                    help="interpolants per segment of the swept-check comparison (0: skip it)")
     ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
     ap.add_argument("--learned-steps", type=int, default=6000, help="denoiser training steps (batch 256)")
     ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
@@ -254,12 +256,65 @@ def run_gpu(args, rank: int, world: int):
         roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
                   "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
                   "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                  "traffic": (K_PLAN_DRAM_BYTES_PER_PROBLEM * P
-                              if spec.name == "batched" and S == 64 and T == 32 and iters == 100 else None),
-                  "traffic_source": "ncu dram__bytes_read+write of a 32-problem launch, scaled by problems"},
+                  "traffic": (K_PLAN_DRAM_BYTES_BATCHED
+                              if (spec.name, P, S, T, iters) == ("batched", 256, 64, 32, 100) else None),
+                  "traffic_source": "ncu dram__bytes_read+write of the full-size launch"},
         clocks=sampler.summary(),
     )
     return res, wl
+
+
+# ---------------------------------------------------------------------------- swept check
+
+def run_sweep(args, wl) -> dict:
+    """Waypoint-only plans against plans with the swept check (args.sweep
+    joint-space interpolants per segment) on the benchmark's own problems: plan
+    time (ESDFs built, inputs resident, 2 GB of ESDF so L2 holds no whole
+    input), success, and every result re-checked at 8 interpolants per segment
+    (the continuous-collision test the waypoint-only success does not make)."""
+    import dataclasses
+    import torch
+    from paper_2410_16727_gb300 import api, binding as B
+
+    def planner_for(n):
+        pl = api.Planner(wl.robot, dataclasses.replace(wl.cost, n_sweep=n), wl.opt)
+        pl.set_scenes(wl.cuboids, wl.grids)
+        return pl, pl.batch(wl.q_start, wl.goal, wl.scene_of_problem, wl.S, wl.T)
+
+    checker, cbatch = planner_for(8)
+    seeds = torch.as_tensor(np.ascontiguousarray(wl.seeds)).cuda()
+    rows = []
+    for n in (0, args.sweep):
+        pl, batch = planner_for(n)
+        for _ in range(2):
+            out = pl.plan(batch, seeds)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(5):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            out = pl.plan(batch, seeds)
+            b.record()
+            b.synchronize()
+            ts.append(a.elapsed_time(b))
+        ok = out["success"].bool()
+        ok8 = B.evaluate(checker.robot, cbatch.desc, cbatch.pr, out["traj"])[0].bool() & ok
+        best = out["best"].long()
+        has = best >= 0
+        best_ok8 = torch.zeros_like(has)
+        best_ok8[has] = ok8[has.nonzero()[:, 0], best[has]]
+        ms = statistics.median(ts)
+        P, S, T, it = wl.P, wl.S, wl.T, wl.opt.iters
+        rows.append({"n_sweep": n, "plan_ms": ms,
+                     "config_evals_per_s": P * S * T * (1 + n) * (it + 1) / (ms * 1e-3),
+                     "seed_success": float(ok.float().mean()), "problems_solved": float(ok.any(1).float().mean()),
+                     "seed_success_checked_8": float(ok8.float().mean()),
+                     "problems_solved_checked_8": float(ok8.any(1).float().mean()),
+                     "best_seed_passes_8": float(best_ok8[has].float().mean()) if bool(has.any()) else None})
+        del pl, batch, out
+    return {"workload": f"the benchmark's {wl.P} problems x {wl.S} seeds x {wl.T} waypoints, "
+                        f"{wl.opt.iters} iterations; success re-checked at 8 interpolants per segment",
+            "runs": rows}
 
 
 # ---------------------------------------------------------------------------- serving
@@ -584,6 +639,8 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     res, wl = run_gpu(args, rank, world)
+    if rank == 0 and args.sweep > 0:
+        res["sweep"] = run_sweep(args, wl)
     if not args.no_serving:
         res["serving"] = run_serving(args, rank)
     if rank == 0 and not args.no_learned:
