@@ -13,6 +13,13 @@ convolutions run channels-first where the CUDA path uses im2col + GEMM.
 Pins (tests/test_oracle_denoiser.py): finite-difference gradcheck of the whole
 network on a small configuration, group-norm moments, Mish closed forms, the
 sinusoidal embedding's closed form, DDPM noising and the DDIM step identities.
+
+Also Eq. 2's loss measured on the robot (fk_mse): the drawn and the predicted
+noise are decoded to the joint configurations they stand for and placed by a
+forward-kinematics chain of 4x4 modified-DH products written here (pins in
+tests/test_oracle_fk_loss.py: zero at pred = eps, a base-joint rotation's closed
+form, per-sample weights, sphere centres against the C oracle's, central
+differences).
 """
 from __future__ import annotations
 
@@ -146,3 +153,63 @@ def ddim_step(xk, eps, ab_k, ab_prev, clip):
     """Deterministic DDIM update from step k to an earlier step (eta = 0)."""
     x0 = np.clip((xk - np.sqrt(1 - ab_k) * eps) / np.sqrt(ab_k), -clip, clip)
     return np.sqrt(ab_prev) * x0 + np.sqrt(1 - ab_prev) * eps
+
+
+# ------------------------------------------------------------------ Eq. 2 on the robot
+
+def robot_points(robot, q: torch.Tensor) -> torch.Tensor:
+    """Collision-sphere centres [..., N_s, 3] of joint configurations q [..., 7]:
+    frame i = frame i-1 RotX(alpha_i) TransX(a_i) RotZ(q_i + offset_i) TransZ(d_i)
+    (modified DH, rows (a, d, alpha, offset) of robot.dh; the eighth row, the
+    flange, has no joint), sphere k at its offset in frame sph_frame[k]."""
+    dh = torch.as_tensor(np.asarray(robot.dh, np.float64))
+    lead = q.shape[:-1]
+    one = torch.ones(lead, dtype=DT)
+    zero = torch.zeros(lead, dtype=DT)
+
+    def mat(rows):
+        return torch.stack([torch.stack(r, -1) for r in rows], -2)
+
+    frames = [torch.eye(4, dtype=DT).expand(*lead, 4, 4)]
+    for i in range(8):
+        a, d, al, off = (float(v) for v in dh[i])
+        th = (q[..., i] if i < 7 else zero) + off
+        ca, sa = math.cos(al), math.sin(al)
+        rx = mat([[one, zero, zero, zero], [zero, ca * one, -sa * one, zero], [zero, sa * one, ca * one, zero],
+                  [zero, zero, zero, one]])
+        tx = mat([[one, zero, zero, a * one], [zero, one, zero, zero], [zero, zero, one, zero], [zero, zero, zero, one]])
+        rz = mat([[torch.cos(th), -torch.sin(th), zero, zero], [torch.sin(th), torch.cos(th), zero, zero],
+                  [zero, zero, one, zero], [zero, zero, zero, one]])
+        tz = mat([[one, zero, zero, zero], [zero, one, zero, zero], [zero, zero, one, d * one], [zero, zero, zero, one]])
+        frames.append(frames[-1] @ rx @ tx @ rz @ tz)
+    F = torch.stack(frames, -3)                                           # [..., 9, 4, 4]
+    o = torch.as_tensor(np.asarray(robot.sph_o, np.float64))
+    oh = torch.cat([o, torch.ones(o.shape[0], 1, dtype=DT)], 1)           # [N_s, 4]
+    fr = torch.as_tensor(np.asarray(robot.sph_frame, np.int64))
+    Fk = F[..., fr, :, :]                                                 # [..., N_s, 4, 4]
+    return (Fk @ oh[..., None])[..., :3, 0]
+
+
+def decode(robot, lin, v, res_scale: float) -> torch.Tensor:
+    """Joint configuration a diffused-space vector v stands for: the residual
+    v / res_scale added to the normalised straight path lin, un-normalised by
+    the limits (mid + half * n)."""
+    lim = torch.as_tensor(np.asarray(robot.limits, np.float64))
+    mid, half = (lim[:, 0] + lim[:, 1]) / 2, (lim[:, 1] - lim[:, 0]) / 2
+    return mid + half * (lin + v / res_scale)
+
+
+def fk_mse(robot, lin, eps, pred, res_scale: float, weights=None):
+    """Eq. 2 measured on the robot: with c_k(q) the sphere centres,
+    loss = sum_n w_n sum_{t,k} |c_k(q(pred_nt)) - c_k(q(eps_nt))|^2 / (N T N_s 3).
+    lin, eps, pred [N][T][7]; returns (loss, dloss/dpred [N][T][7])."""
+    t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
+    lin, eps = t(lin), t(eps)
+    pr = t(pred).clone().requires_grad_(True)
+    N = lin.shape[0]
+    w = torch.ones(N, dtype=DT) if weights is None else t(weights)
+    cl = robot_points(robot, decode(robot, lin, eps, res_scale))
+    cp = robot_points(robot, decode(robot, lin, pr, res_scale))
+    loss = (w.view(-1, 1, 1, 1) * (cp - cl) ** 2).sum() / cp.numel()
+    loss.backward()
+    return float(loss.detach()), pr.grad.detach().numpy()
