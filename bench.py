@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
     ap.add_argument("--learned-steps", type=int, default=6000, help="denoiser training steps (batch 256)")
     ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
+    ap.add_argument("--learned-fk", action="store_true",
+                    help="also train a denoiser with Eq. 2's loss measured on the robot and compare it")
     ap.add_argument("--problems", type=int, default=None,
                     help="smaller case for profiling: this many problems (and scenes) of the workload")
     return ap.parse_args()
@@ -431,7 +433,7 @@ def run_learned(args) -> dict:
     arrivals at one offered load, plain (64 seeds x 100 iterations) vs seeded
     (proposals on arrival + 20 iterations), p50/p99 latency and plans/s."""
     import torch
-    from paper_2410_16727_gb300 import api, denoiser as DN, learned as L, netspec as NS, serving as SV
+    from paper_2410_16727_gb300 import api, binding as B, denoiser as DN, learned as L, netspec as NS, serving as SV
 
     robot = I.make_robot()
     planner = api.Planner(robot)
@@ -448,6 +450,16 @@ def run_learned(args) -> dict:
     torch.cuda.synchronize()
     out["training"] = {"steps": args.learned_steps, "batch": 256, "params": int(net.n_params),
                        "seconds": round(time.perf_counter() - t0, 1), "loss": [round(l, 4) for _, l in losses]}
+    net_fk = None
+    if args.learned_fk:
+        # the same data and schedule, the error measured on the robot's sphere centres (Eq. 2)
+        net_fk = DN.Denoiser(NS.NetSpec(), seed=0)
+        t0 = time.perf_counter()
+        losses = L.train(net_fk, data, args.learned_steps, batch=256, lr=3e-4,
+                         log_every=max(1, args.learned_steps // 4), fk_robot=B.Robot(robot))
+        torch.cuda.synchronize()
+        out["training_fk_loss"] = {"steps": args.learned_steps, "seconds": round(time.perf_counter() - t0, 1),
+                                   "loss_m2": [float(f"{l:.4g}") for _, l in losses]}
     del data, tr
     te = L.make_problems(planner, 64, 8, seed=1)
     P = int(te.q_start.shape[0])
@@ -470,26 +482,31 @@ def run_learned(args) -> dict:
         sv, ss = score(o)
         plain[it] = {"iters": it, "solved": round(sv, 4), "seed_success": round(ss, 4), "ms": round(dt * 1e3, 2)}
     out["heldout"] = {"problems": P, "scenes": 64, "plain_seeds": 64, "plain": list(plain.values())}
-    learned = []
-    diff_only = []
-    for S, d, it in ((64, 10, 20), (12, 5, 20), (12, 5, 10)):
-        L.propose(net, robot, te, S, steps=d)                                  # warm-up
-        seeds, t_d = timed(lambda: L.propose(net, robot, te, S, steps=d))
-        if it == 20:
-            diff_only.append({"samples": S, "ddim_steps": d, **L.diffusion_only(planner, te, seeds)})
-        o, t_p = timed(lambda: L.solve(planner, te, seeds, it, chunk=P))
-        sv, ss = score(o)
-        total = (t_d + t_p) * 1e3
-        # the plain method at the same wall time: its largest measured budget that fits
-        fit = [v for v in plain.values() if v["ms"] <= total]
-        eq = max(fit, key=lambda v: v["iters"]) if fit else None
-        learned.append({"samples": S, "ddim_steps": d, "iters": it, "solved": round(sv, 4),
-                        "seed_success": round(ss, 4), "ddim_ms": round(t_d * 1e3, 2), "plan_ms": round(t_p * 1e3, 2),
-                        "total_ms": round(total, 2),
-                        "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
-                                                if eq else None)})
-    out["heldout"]["learned"] = learned
-    out["heldout"]["diffusion_only"] = diff_only
+    def evaluate_net(model):
+        learned, diff_only = [], []
+        for S, d, it in ((64, 10, 20), (12, 5, 20), (12, 5, 10)):
+            L.propose(model, robot, te, S, steps=d)                            # warm-up
+            seeds, t_d = timed(lambda: L.propose(model, robot, te, S, steps=d))
+            if it == 20:
+                diff_only.append({"samples": S, "ddim_steps": d, **L.diffusion_only(planner, te, seeds)})
+            o, t_p = timed(lambda: L.solve(planner, te, seeds, it, chunk=P))
+            sv, ss = score(o)
+            total = (t_d + t_p) * 1e3
+            # the plain method at the same wall time: its largest measured budget that fits
+            fit = [v for v in plain.values() if v["ms"] <= total]
+            eq = max(fit, key=lambda v: v["iters"]) if fit else None
+            learned.append({"samples": S, "ddim_steps": d, "iters": it, "solved": round(sv, 4),
+                            "seed_success": round(ss, 4), "ddim_ms": round(t_d * 1e3, 2),
+                            "plan_ms": round(t_p * 1e3, 2), "total_ms": round(total, 2),
+                            "plain_at_equal_time": ({"iters": eq["iters"], "solved": eq["solved"], "ms": eq["ms"]}
+                                                    if eq else None)})
+        return learned, diff_only
+
+    out["heldout"]["learned"], out["heldout"]["diffusion_only"] = evaluate_net(net)
+    if net_fk is not None:
+        lf, df = evaluate_net(net_fk)
+        out["heldout"]["fk_loss"] = {"learned": lf, "diffusion_only": df}
+        del net_fk
     # the (12, 5) proposal for all 512 problems as one CUDA-graph replay, without and
     # with cost-gradient guidance (Eq. 5, k = 60, n = 20)
     occ_all = te.occ[te.scene_of_problem.long()]

@@ -479,6 +479,23 @@ int dseed_nn_ddpm_noise(const float *x0_dev, const float *eps_dev, const int *k_
  * written as `blocks` partial sums into loss_partial_dev; dpred = dloss/dpred. */
 int dseed_nn_mse(const float *pred_dev, const float *target_dev, const float *w_dev, int N, int per,
                  float *dpred_dev, float *loss_partial_dev, int blocks, cudaStream_t stream);
+/* The loss of Eq. 2 measured on the robot (Sec. 4.3: the noise and the
+ * predicted noise both go through forward kinematics to points on the robot).
+ * eps_dev, pred_dev [N][T][7] live in the diffused space, the scaled residual
+ * from the straight path: vector v stands for the joint configuration
+ * q(v) = mid + half (lin + v / res_scale) per waypoint and joint, lin_dev
+ * [N][T][7] the normalised straight start-goal path, mid and half the centre
+ * and half-width of the robot's joint limits.  With c_k(q) the robot's
+ * collision-sphere centres and w_dev [N] optional weights (Eq. 2's
+ * 1 + alpha 1(tau); NULL = 1):
+ *   loss = sum_n w_n sum_{t,k} |c_k(q(pred_nt)) - c_k(q(eps_nt))|^2 / (N T N_s 3),
+ * written as `blocks` (1..1024) partial sums into loss_partial_dev; dpred_dev
+ * [N][T][7] = dloss/dpred.  Device arrays are the caller's; asynchronous on
+ * stream.  EINVAL: NULL robot or array, T outside 1..DSEED_MAX_T, res_scale
+ * not > 0. */
+int dseed_nn_fk_mse(const DseedRobot *robot, const float *lin_dev, const float *eps_dev, const float *pred_dev,
+                    const float *w_dev, int N, int T, float res_scale, float *dpred_dev, float *loss_partial_dev,
+                    int blocks, cudaStream_t stream);
 /* One deterministic DDIM step (App. A.5) from step k to an earlier step:
  * x0 = clamp((x_k - sqrt(1 - ab_k) eps) / sqrt(ab_k), -clip, clip),
  * out = sqrt(ab_prev) x0 + sqrt(1 - ab_prev) eps. */

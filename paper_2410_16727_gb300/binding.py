@@ -167,6 +167,8 @@ _SIGS = {
                              C.c_void_p], C.c_int),
     "dseed_nn_mse": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_int,
                       C.c_void_p], C.c_int),
+    "dseed_nn_fk_mse": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_float,
+                         C.c_void_p, C.c_void_p, C.c_int, C.c_void_p], C.c_int),
     "dseed_nn_ddim_step": ([C.c_void_p, C.c_void_p, C.c_float, C.c_float, C.c_longlong, C.c_float, C.c_void_p,
                            C.c_void_p], C.c_int),
     "dseed_nn_to_bf16": ([C.c_void_p, C.c_void_p, C.c_longlong, C.c_void_p], C.c_int),

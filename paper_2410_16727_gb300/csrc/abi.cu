@@ -423,6 +423,20 @@ int dseed_fk(const DseedRobot *robot, const float *q_dev, int N, float *pose_dev
     return cuda_status(dseed::launch_fk(robot->k, q_dev, N, pose_dev, spheres_dev, stream), "fk");
 }
 
+int dseed_nn_fk_mse(const DseedRobot *robot, const float *lin_dev, const float *eps_dev, const float *pred_dev,
+                    const float *w_dev, int N, int T, float res_scale, float *dpred_dev, float *loss_partial_dev,
+                    int blocks, cudaStream_t stream) {
+    if (!robot) return fail(DSEED_EINVAL, "robot is NULL");
+    if (N < 0 || T < 1 || T > DSEED_MAX_T) return fail(DSEED_EINVAL, "fk_mse: N = %d, T = %d", N, T);
+    if (!finite(res_scale) || !(res_scale > 0.f)) return fail(DSEED_EINVAL, "fk_mse: res_scale must be > 0");
+    if (blocks < 1 || blocks > 1024) return fail(DSEED_EINVAL, "fk_mse: blocks = %d outside 1..1024", blocks);
+    if (!loss_partial_dev || (N > 0 && (!lin_dev || !eps_dev || !pred_dev || !dpred_dev)))
+        return fail(DSEED_EINVAL, "fk_mse: a required array is NULL");
+    return cuda_status(dseed::launch_fk_mse(robot->k, lin_dev, eps_dev, pred_dev, w_dev, N, T, res_scale, dpred_dev,
+                                            loss_partial_dev, blocks, stream),
+                       "fk_mse");
+}
+
 int dseed_cost(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr, const float *x_dev,
                float *cost_dev, float *terms_dev, cudaStream_t stream) {
     if (!robot) return fail(DSEED_EINVAL, "robot is NULL");

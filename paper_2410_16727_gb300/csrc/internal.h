@@ -63,6 +63,8 @@ struct KLbfgsPtrs {
 constexpr int kMaxEsdfJobs = 256;                // ESDF jobs per launch (carried in the kernel parameters)
 int launch_esdf_build(const DseedEsdfJob *jobs, int n_jobs, cudaStream_t st);
 int launch_fk(const KRobot &rb, const float *q, int N, float *pose, float *spheres, cudaStream_t st);
+int launch_fk_mse(const KRobot &rb, const float *lin, const float *eps, const float *pred, const float *w, int N,
+                  int T, float res_scale, float *dpred, float *loss_partial, int blocks, cudaStream_t st);
 int launch_cost(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x, float *cost,
                 float *terms, cudaStream_t st);
 int launch_cost_grad(const KRobot &rb, const KCost &kc, const KBatch &kb, const float *x,

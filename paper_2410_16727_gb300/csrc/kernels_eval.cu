@@ -171,4 +171,98 @@ int launch_fk(const KRobot &rb, const float *q, int N, float *pose, float *spher
     return (int)cudaGetLastError();
 }
 
+// ---------------------------------------------------------------- Eq. 2 in the workspace
+// One thread per (trajectory, waypoint).  The drawn noise eps and the predicted
+// noise pred stand for the joint configurations q(v) = mid + half (lin + v / res)
+// (lin: the normalised straight start-goal path; mid, half: centre and
+// half-width of each joint's limits); both are placed by the kinematic chain
+// and the squared distances between the predicted and the drawn sphere
+// centres are summed, weighted per trajectory.  The derivative with respect
+// to pred runs back through the predicted chain by Jacobian-transpose
+// accumulation: each sphere pushes with g = dloss/dc at its predicted centre,
+// joint i receives z_i . (M - M_<i) - (z_i x p_i) . (F - F_<i) with F, M the
+// sum of the pushes and of their moments about the origin (the _<i parts are
+// the spheres met before frame i), times half / res.
+__global__ void __launch_bounds__(256) k_fk_mse(const __grid_constant__ KRobot rb, const float *__restrict__ lin,
+                                                const float *__restrict__ eps, const float *__restrict__ pred,
+                                                const float *__restrict__ w, int N, int T, float inv_res,
+                                                float inv_norm, float *__restrict__ dpred,
+                                                float *__restrict__ loss_partial) {
+    __shared__ float red[256];
+    float acc = 0.f;
+    const long long total = (long long)N * T;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float wn = w ? w[i / T] : 1.f;
+        const float *li = lin + i * 7, *ei = eps + i * 7, *pi = pred + i * 7;
+        float Rl[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}, pl[3] = {0.f, 0.f, 0.f};
+        float Rp[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f}, pp[3] = {0.f, 0.f, 0.f};
+        float zj[7][3], wj[7][3], bj[7];
+        float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f, dsum = 0.f;
+        const float gs = 2.f * wn * inv_norm;
+#pragma unroll
+        for (int L = 1; L <= 8; ++L) {
+            float stl, ctl, stp, ctp;
+            if (L <= 7) {
+                const int j = L - 1;
+                const float mid = 0.5f * (rb.hi[j] + rb.lo[j]), half = 0.5f * (rb.hi[j] - rb.lo[j]);
+                sincosf(fmaf(half, fmaf(ei[j], inv_res, li[j]), mid) + rb.off[j], &stl, &ctl);
+                sincosf(fmaf(half, fmaf(pi[j], inv_res, li[j]), mid) + rb.off[j], &stp, &ctp);
+            } else {
+                stl = stp = rb.sf8;
+                ctl = ctp = rb.cf8;
+            }
+            dh_step(Rl, pl, rb.a[L - 1], rb.d[L - 1], rb.ca[L - 1], rb.sa[L - 1], ctl, stl);
+            dh_step(Rp, pp, rb.a[L - 1], rb.d[L - 1], rb.ca[L - 1], rb.sa[L - 1], ctp, stp);
+            if (L <= 7) {
+                const int j = L - 1;
+                zj[j][0] = Rp[2]; zj[j][1] = Rp[5]; zj[j][2] = Rp[8];
+                wj[j][0] = Rp[5] * pp[2] - Rp[8] * pp[1];
+                wj[j][1] = Rp[8] * pp[0] - Rp[2] * pp[2];
+                wj[j][2] = Rp[2] * pp[1] - Rp[5] * pp[0];
+                bj[j] = (zj[j][0] * Mx + zj[j][1] * My + zj[j][2] * Mz) - (wj[j][0] * Fx + wj[j][1] * Fy + wj[j][2] * Fz);
+            }
+            for (int k = rb.frame_begin[L - 1]; k < rb.frame_begin[L]; ++k) {
+                const float4 s = rb.sph[k];
+                const float cx = fmaf(Rp[0], s.x, fmaf(Rp[1], s.y, fmaf(Rp[2], s.z, pp[0])));
+                const float cy = fmaf(Rp[3], s.x, fmaf(Rp[4], s.y, fmaf(Rp[5], s.z, pp[1])));
+                const float cz = fmaf(Rp[6], s.x, fmaf(Rp[7], s.y, fmaf(Rp[8], s.z, pp[2])));
+                const float dx = cx - fmaf(Rl[0], s.x, fmaf(Rl[1], s.y, fmaf(Rl[2], s.z, pl[0])));
+                const float dy = cy - fmaf(Rl[3], s.x, fmaf(Rl[4], s.y, fmaf(Rl[5], s.z, pl[1])));
+                const float dz = cz - fmaf(Rl[6], s.x, fmaf(Rl[7], s.y, fmaf(Rl[8], s.z, pl[2])));
+                dsum += dx * dx + dy * dy + dz * dz;
+                const float gx = gs * dx, gy = gs * dy, gz = gs * dz;
+                Fx += gx; Fy += gy; Fz += gz;
+                Mx += cy * gz - cz * gy;
+                My += cz * gx - cx * gz;
+                Mz += cx * gy - cy * gx;
+            }
+        }
+        acc = fmaf(wn, dsum, acc);
+#pragma unroll
+        for (int j = 0; j < 7; ++j) {
+            const float half = 0.5f * (rb.hi[j] - rb.lo[j]);
+            const float gq = (zj[j][0] * Mx + zj[j][1] * My + zj[j][2] * Mz) -
+                             (wj[j][0] * Fx + wj[j][1] * Fy + wj[j][2] * Fz) - bj[j];
+            dpred[i * 7 + j] = gq * half * inv_res;
+        }
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) loss_partial[blockIdx.x] = red[0] * inv_norm;
+}
+
+int launch_fk_mse(const KRobot &rb, const float *lin, const float *eps, const float *pred, const float *w, int N,
+                  int T, float res_scale, float *dpred, float *loss_partial, int blocks, cudaStream_t st) {
+    const double norm = (double)N * T * rb.n_spheres * 3.0;
+    const float inv_norm = norm > 0.0 ? (float)(1.0 / norm) : 0.f;
+    k_fk_mse<<<blocks, 256, 0, st>>>(rb, lin, eps, pred, w, N, T, (float)(1.0 / (double)res_scale), inv_norm, dpred,
+                                     loss_partial);
+    return (int)cudaGetLastError();
+}
+
 }  // namespace dseed

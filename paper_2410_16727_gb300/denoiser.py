@@ -394,10 +394,14 @@ class Denoiser:
             fn()
 
     # ------------------------------------------------------------------ training
-    def loss_and_grad(self, x0, qs, qg, goal, occ, k, eps, weights=None):
+    def loss_and_grad(self, x0, qs, qg, goal, occ, k, eps, weights=None, fk=None):
         """Eq. 1 (optionally weighted per sample as in Eq. 2): noise the clean
         normalised trajectories x0 to step k with eps, predict the noise,
         accumulate parameter gradients of the mean squared error into self.grads.
+        With fk = (robot, lin, res_scale) the error is measured on the robot as
+        in Eq. 2 (dseed_nn_fk_mse): eps and the prediction are decoded to joint
+        configurations around the samples' normalised straight paths lin
+        [N][T][7] and compared through the robot's sphere centres.
         Returns the loss (device scalar)."""
         N = x0.shape[0]
         per = x0.numel() // N
@@ -408,7 +412,12 @@ class Denoiser:
         dpred = torch.empty_like(pred)
         blocks = 64
         part = torch.empty(blocks, dtype=torch.float32, device=self.dev)
-        _nn("mse", pred, eps, weights, N, per, dpred, part, blocks)
+        if fk is None:
+            _nn("mse", pred, eps, weights, N, per, dpred, part, blocks)
+        else:
+            robot, lin, res_scale = fk
+            _nn("fk_mse", robot.handle, lin, eps, pred, weights, N, x0.shape[1], float(res_scale), dpred, part,
+                blocks)
         self.backward(tape, pred, dpred)
         return part.sum()
 

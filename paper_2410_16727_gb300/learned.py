@@ -223,7 +223,7 @@ class GraphStep:
     sequence of a fixed batch size never changes, so replaying it removes the
     host cost of issuing ~400 launches per step."""
 
-    def __init__(self, net: DN.Denoiser, batch: int, weighted: bool):
+    def __init__(self, net: DN.Denoiser, batch: int, weighted: bool, fk_robot: Optional[B.Robot] = None):
         s, dev = net.spec, net.dev
         self.net = net
         self.x0 = torch.zeros((batch, s.T, s.D), device=dev)
@@ -236,16 +236,22 @@ class GraphStep:
         self.eps = torch.zeros((batch, s.T, s.D), device=dev)
         self.w = torch.ones((batch,), device=dev) if weighted else None
         args = (self.x0, self.qs, self.qg, self.goal, self.occ, self.k, self.eps, self.w)
+
+        def step():
+            # Eq. 2 on the robot needs the samples' straight paths (one GEMM, inside the graph)
+            fk = None if fk_robot is None else (fk_robot, linear_path(self.qs, self.qg, s.T), RES_SCALE)
+            return net.loss_and_grad(*args, fk=fk)
+
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):                  # warm-up outside the capture
-            net.loss_and_grad(*args)
+            step()
         torch.cuda.current_stream().wait_stream(side)
         torch.cuda.synchronize()
         net.grads.zero_()
         self.graph = torch.cuda.CUDAGraph()
         with torch.cuda.graph(self.graph):
-            self.loss = net.loss_and_grad(*args)
+            self.loss = step()
         torch.cuda.synchronize()
         net.grads.zero_()
 
@@ -255,14 +261,15 @@ class GraphStep:
 
 
 def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: float = 3e-4, seed: int = 0,
-          log_every: int = 0, weighted: bool = True, graph: bool = True):
+          log_every: int = 0, weighted: bool = True, graph: bool = True, fk_robot: Optional[B.Robot] = None):
     """DDPM training (Eq. 1 / Eq. 2 weights) with Adam and a cosine learning
-    rate; returns the loss curve [(step, loss)]."""
+    rate; returns the loss curve [(step, loss)].  With fk_robot the error is
+    measured on that robot's sphere centres (Eq. 2), else on the joints (Eq. 1)."""
     g = torch.Generator(device=data.x0.device)
     g.manual_seed(seed)
     M = data.x0.shape[0]
     losses = []
-    gs = GraphStep(net, batch, weighted) if graph else None
+    gs = GraphStep(net, batch, weighted, fk_robot) if graph else None
     for it in range(steps):
         idx = torch.randint(0, M, (batch,), device=data.x0.device, generator=g)
         k = torch.randint(0, net.spec.K, (batch,), device=data.x0.device, generator=g, dtype=torch.int32)
@@ -279,10 +286,11 @@ def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: flo
                 gs.w.copy_(data.weight[idx])
             loss = gs.run()
         else:
-            loss = net.loss_and_grad(data.x0[idx].contiguous(), data.qs[idx].contiguous(),
-                                     data.qg[idx].contiguous(), data.goal[idx].contiguous(),
+            qs_b, qg_b = data.qs[idx].contiguous(), data.qg[idx].contiguous()
+            fk = None if fk_robot is None else (fk_robot, linear_path(qs_b, qg_b, net.spec.T), RES_SCALE)
+            loss = net.loss_and_grad(data.x0[idx].contiguous(), qs_b, qg_b, data.goal[idx].contiguous(),
                                      data.occ[data.scene[idx]].contiguous(), k, eps,
-                                     data.weight[idx].contiguous() if weighted else None)
+                                     data.weight[idx].contiguous() if weighted else None, fk=fk)
         cos = 0.5 * (1 + math.cos(math.pi * it / max(steps, 1)))
         net.adam_step(lr=lr * (0.1 + 0.9 * cos))
         if log_every and (it % log_every == 0 or it == steps - 1):
