@@ -7,7 +7,7 @@
 // deepest-penetration reading of min_k sdf_k); otherwise min_k sdf_k is the
 // square root of the former.  Both equal min_k sdf_k exactly.
 //
-// One block owns an 8x8x8 tile of voxels (a thread per 4-voxel column) of one scene;
+// One block owns an 8x8x8 tile of voxels (a thread per column of kZPer voxels) of one scene;
 // a launch covers up to kMaxJobs scenes (job descriptors travel in the kernel
 // parameters, so no device-side table is needed).  Before the per-voxel loop
 // the block drops the boxes that cannot be the minimum anywhere in the tile:
@@ -20,6 +20,11 @@
 // leaves every min, and every output bit, unchanged; the remaining boxes go
 // through the same per-voxel arithmetic as without the culling (checked
 // bitwise against a build without culling on the benchmark workloads).
+//
+// A kept box's z terms depend only on its z-slice of the tile, so they are
+// formed once per box and slice (dz = |z - c_z| - h_z and max(dz, 0), 8 of each)
+// and read from shared memory by the columns; the per-voxel work is one fused
+// multiply-add and three min/max, with the same roundings as forming them in place.
 #include <cuda_runtime.h>
 #include <math_constants.h>
 
@@ -28,9 +33,13 @@
 namespace dseed {
 
 constexpr int kTile = 8;
-constexpr int kZPer = 4;                              // voxels per thread along z
-constexpr int kEsdfThreads = kTile * kTile * kTile / kZPer;   // 128
-constexpr int kEsdfChunk = 512;                       // boxes staged per pass
+#ifndef DSEED_ESDF_ZPER
+#define DSEED_ESDF_ZPER 4
+#endif
+constexpr int kZPer = DSEED_ESDF_ZPER;                // voxels per thread along z (4 or 8)
+static_assert(kZPer == 4 || kZPer == 8, "a thread owns 4 or 8 voxels of a column");
+constexpr int kEsdfThreads = kTile * kTile * kTile / kZPer;   // 64 or 128
+constexpr int kEsdfChunk = 256;                       // boxes staged per pass
 
 struct EsdfBatch {
     int n_jobs;
@@ -50,7 +59,10 @@ __device__ __forceinline__ float box_sdf(float px, float py, float pz, const flo
 // One block = one 8^3 tile of one scene; a thread owns a column of kZPer voxels
 // along z, so each box's x and y terms are formed once for the column.
 __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_constant__ EsdfBatch batch) {
-    __shared__ float4 sb[kEsdfChunk * 2];              // kept boxes: (cx, cy, cz, hx), (hy, hz, -, -)
+    __shared__ float4 s_xy[kEsdfChunk];                // kept boxes: (cx, cy, hx, hy)
+    __shared__ float2 s_zc[kEsdfChunk];                // (cz, hz)
+    __shared__ float4 s_dz[kEsdfChunk][2];             // dz of the tile's 8 z-slices
+    __shared__ float4 s_oz[kEsdfChunk][2];             // max(dz, 0)
     __shared__ float s_red[kEsdfThreads / 32];
     __shared__ int s_count;
     const int jid = blockIdx.z / batch.tiles_z;
@@ -65,9 +77,6 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
     const int i = tx * kTile + lx, j = ty * kTile + ly, k0 = tz * kTile + lz * kZPer;
     const float px = fmaf((float)i + 0.5f, g.res, g.origin[0]);
     const float py = fmaf((float)j + 0.5f, g.res, g.origin[1]);
-    float pz[kZPer];
-#pragma unroll
-    for (int e = 0; e < kZPer; ++e) pz[e] = fmaf((float)(k0 + e) + 0.5f, g.res, g.origin[2]);
     // tile extent in voxel centres (the full 8^3 tile, also past the grid edge)
     float lo[3], hi[3];
     lo[0] = fmaf((float)(tx * kTile) + 0.5f, g.res, g.origin[0]);
@@ -135,25 +144,40 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
             const float lb = gap2 > 0.f ? sqrtf(gap2) : -CUDART_INF_F;
             if (lb <= tau) {
                 const int slot = atomicAdd(&s_count, 1);
-                sb[2 * slot] = make_float4(bx[0], bx[1], bx[2], bx[3]);
-                sb[2 * slot + 1] = make_float4(bx[4], bx[5], 0.f, 0.f);
+                s_xy[slot] = make_float4(bx[0], bx[1], bx[3], bx[4]);
+                s_zc[slot] = make_float2(bx[2], bx[5]);
             }
         }
         __syncthreads();
         const int kept = s_count;
+        // the z terms of every kept box, once per z-slice of the tile
+        for (int w = threadIdx.x; w < kept * kTile; w += kEsdfThreads) {
+            const int q = w >> 3, zl = w & 7;
+            const float pz = fmaf((float)(tz * kTile + zl) + 0.5f, g.res, g.origin[2]);
+            const float2 zc = s_zc[q];
+            const float dz = fabsf(pz - zc.x) - zc.y;
+            reinterpret_cast<float *>(s_dz[q])[zl] = dz;
+            reinterpret_cast<float *>(s_oz[q])[zl] = fmaxf(dz, 0.f);
+        }
+        __syncthreads();
         for (int q = 0; q < kept; ++q) {
-            const float4 b0 = sb[2 * q], b1 = sb[2 * q + 1];
-            const float dx = fabsf(px - b0.x) - b0.w;
-            const float dy = fabsf(py - b0.y) - b1.x;
+            const float4 b = s_xy[q];
+            const float dx = fabsf(px - b.x) - b.z;
+            const float dy = fabsf(py - b.y) - b.w;
             const float ox = fmaxf(dx, 0.f), oy = fmaxf(dy, 0.f);
             const float sxy = fmaf(ox, ox, oy * oy);
             const float mxy = fmaxf(dx, dy);
+            float dz[kZPer], oz[kZPer];
+#pragma unroll
+            for (int h = 0; h < kZPer / 4; ++h) {
+                const float4 d4 = s_dz[q][lz * (kZPer / 4) + h], o4 = s_oz[q][lz * (kZPer / 4) + h];
+                dz[4 * h] = d4.x; dz[4 * h + 1] = d4.y; dz[4 * h + 2] = d4.z; dz[4 * h + 3] = d4.w;
+                oz[4 * h] = o4.x; oz[4 * h + 1] = o4.y; oz[4 * h + 2] = o4.z; oz[4 * h + 3] = o4.w;
+            }
 #pragma unroll
             for (int e = 0; e < kZPer; ++e) {
-                const float dz = fabsf(pz[e] - b0.z) - b1.y;
-                const float oz = fmaxf(dz, 0.f);
-                out2[e] = fminf(out2[e], fmaf(oz, oz, sxy));
-                in[e] = fminf(in[e], fmaxf(mxy, dz));
+                out2[e] = fminf(out2[e], fmaf(oz[e], oz[e], sxy));
+                in[e] = fminf(in[e], fmaxf(mxy, dz[e]));
             }
         }
     }
