@@ -11,9 +11,9 @@
 // a launch covers up to kMaxJobs scenes (job descriptors travel in the kernel
 // parameters, so no device-side table is needed).  Before the per-voxel loop
 // the block drops the boxes that cannot be the minimum anywhere in the tile:
-// sdf_k is convex, so its maximum over the tile is at one of the tile's 8
-// corner voxel centres (an upper bound U_k; the 8 corners of a box are
-// evaluated by 8 neighbouring lanes), and its minimum over the tile is at least
+// sdf_k is nondecreasing in each |p_i - c_i|, so its maximum over the tile is
+// at the corner voxel centre farthest from the box centre along every axis (an
+// upper bound U_k from one evaluation), and its minimum over the tile is at least
 // the distance from the tile's box of voxel centres to the cuboid (a lower
 // bound L_k, or -inf when they overlap).  A box with L_k > min_j U_j + 1e-4 is
 // larger than another box's value at every voxel of the tile, so skipping it
@@ -86,28 +86,19 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
     hi[1] = fmaf((float)(ty * kTile + kTile - 1) + 0.5f, g.res, g.origin[1]);
     hi[2] = fmaf((float)(tz * kTile + kTile - 1) + 0.5f, g.res, g.origin[2]);
 
-    // pass 1: tau = min over boxes of the max of sdf_k over the 8 tile corners;
-    // lane group (8 lanes) = one box, lane & 7 = corner
+    // pass 1: tau = min over boxes of the max of sdf_k over the tile, taken at the
+    // corner farthest from the box along each axis (the same value as the largest
+    // of the 8 corner evaluations: every rounded step is monotone too)
     float ub = CUDART_INF_F;
-    const int corner = threadIdx.x & 7;
-    const float cxp = (corner & 1) ? hi[0] : lo[0];
-    const float cyp = (corner & 2) ? hi[1] : lo[1];
-    const float czp = (corner & 4) ? hi[2] : lo[2];
-    for (int base = 0; base < n * 8; base += kEsdfThreads) {
-        const int w = base + threadIdx.x;
-        const bool valid = w < n * 8;
-        float v = -CUDART_INF_F;
-        if (valid) {
-            float bx[6];
-            const float *src = cub + (size_t)(w >> 3) * 6;
+    for (int b = threadIdx.x; b < n; b += kEsdfThreads) {
+        float bx[6];
+        const float *src = cub + (size_t)b * 6;
 #pragma unroll
-            for (int c = 0; c < 6; ++c) bx[c] = src[c];
-            v = box_sdf(cxp, cyp, czp, bx);
-        }
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 2));
-        v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
-        if (valid) ub = fminf(ub, v);
+        for (int c = 0; c < 6; ++c) bx[c] = src[c];
+        const float fx = fabsf(hi[0] - bx[0]) >= fabsf(lo[0] - bx[0]) ? hi[0] : lo[0];
+        const float fy = fabsf(hi[1] - bx[1]) >= fabsf(lo[1] - bx[1]) ? hi[1] : lo[1];
+        const float fz = fabsf(hi[2] - bx[2]) >= fabsf(lo[2] - bx[2]) ? hi[2] : lo[2];
+        ub = fminf(ub, box_sdf(fx, fy, fz, bx));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) ub = fminf(ub, __shfl_xor_sync(0xffffffffu, ub, o));
