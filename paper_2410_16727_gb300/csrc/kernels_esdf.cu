@@ -158,17 +158,24 @@ __global__ void __launch_bounds__(kEsdfThreads) k_esdf_build(const __grid_consta
             const float ox = fmaxf(dx, 0.f), oy = fmaxf(dy, 0.f);
             const float sxy = fmaf(ox, ox, oy * oy);
             const float mxy = fmaxf(dx, dy);
-            float dz[kZPer], oz[kZPer];
 #pragma unroll
             for (int h = 0; h < kZPer / 4; ++h) {
-                const float4 d4 = s_dz[q][lz * (kZPer / 4) + h], o4 = s_oz[q][lz * (kZPer / 4) + h];
-                dz[4 * h] = d4.x; dz[4 * h + 1] = d4.y; dz[4 * h + 2] = d4.z; dz[4 * h + 3] = d4.w;
-                oz[4 * h] = o4.x; oz[4 * h + 1] = o4.y; oz[4 * h + 2] = o4.z; oz[4 * h + 3] = o4.w;
-            }
+                const float4 o4 = s_oz[q][lz * (kZPer / 4) + h];
+                const float oz[4] = {o4.x, o4.y, o4.z, o4.w};
 #pragma unroll
-            for (int e = 0; e < kZPer; ++e) {
-                out2[e] = fminf(out2[e], fmaf(oz[e], oz[e], sxy));
-                in[e] = fminf(in[e], fmaxf(mxy, dz[e]));
+                for (int e = 0; e < 4; ++e) out2[4 * h + e] = fminf(out2[4 * h + e], fmaf(oz[e], oz[e], sxy));
+            }
+            // the inside track can only go <= 0 over the box's x-y footprint (mxy <= 0);
+            // elsewhere its value is positive and never read, so a warp with no such
+            // column skips it (the output is unchanged)
+            if (__any_sync(0xffffffffu, mxy <= 0.f)) {
+#pragma unroll
+                for (int h = 0; h < kZPer / 4; ++h) {
+                    const float4 d4 = s_dz[q][lz * (kZPer / 4) + h];
+                    const float dz[4] = {d4.x, d4.y, d4.z, d4.w};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) in[4 * h + e] = fminf(in[4 * h + e], fmaxf(mxy, dz[e]));
+                }
             }
         }
     }
