@@ -77,6 +77,18 @@ def test_host_argument_checks_without_gpu(libpath):
         BD.Robot(r)
     h = BD.Robot(I.make_robot())
     assert h.n_spheres == 50
+    # Eq. 2 on the robot: argument checks run before any device work
+    fk = lib.dseed_nn_fk_mse
+    part = ctypes.c_void_p(1)
+    assert fk(h.handle, None, None, None, None, 2, 0, 4.0, None, part, 8, None) == -1
+    assert "T = 0" in BD.last_error()
+    assert fk(h.handle, None, None, None, None, 2, 32, 0.0, None, part, 8, None) == -1
+    assert "res_scale" in BD.last_error()
+    assert fk(h.handle, None, None, None, None, 2, 32, 4.0, None, part, 2000, None) == -1
+    assert "blocks" in BD.last_error()
+    assert fk(h.handle, None, None, None, None, 2, 32, 4.0, None, part, 8, None) == -1
+    assert "NULL" in BD.last_error()
+    assert fk(None, None, None, None, None, 2, 32, 4.0, None, part, 8, None) == -1
 
 
 def test_conv_tc_descriptor_checks_without_gpu(libpath):
