@@ -20,13 +20,17 @@ namespace dseed {
 #ifndef DSEED_PLAN_MINBLOCKS
 #define DSEED_PLAN_MINBLOCKS 5
 #endif
-constexpr int kPlanWarps = DSEED_PLAN_WARPS;
-// Resident blocks per SM that the register allocation is sized for.  A T <= 32
-// plan fits 96 registers without spills, so five blocks of four warps stay
-// resident (shared memory would allow six, but the 80-register build is
-// slower); longer horizons are held to three or fewer blocks by shared memory,
-// and the self-collision scratch leaves room for two.
-constexpr int plan_min_blocks(int tpl, bool self) { return self ? 2 : tpl == 1 ? DSEED_PLAN_MINBLOCKS : 4; }
+constexpr int kPlanWarps = DSEED_PLAN_WARPS;    // warps per block of the standalone L-BFGS step
+// Block shape of the fused plan.  A T <= 32 plan fits 96 registers without
+// spills, so five blocks of four warps stay resident (shared memory would allow
+// six, but the 80-register build is slower).  Longer horizons and the
+// self-collision scratch are limited by shared memory per warp: two-warp blocks
+// pack it more finely (T = 64: 14 resident warps instead of 12), and the
+// minimum-block counts below leave each variant at least the registers it uses.
+__host__ __device__ constexpr int plan_warps(int tpl, bool self) { return tpl == 1 && !self ? kPlanWarps : 2; }
+__host__ __device__ constexpr int plan_min_blocks(int tpl, bool self) {
+    return tpl == 1 && !self ? DSEED_PLAN_MINBLOCKS : self ? (tpl == 1 ? 5 : tpl == 2 ? 3 : 2) : (tpl == 2 ? 7 : 3);
+}
 
 // ---------------------------------------------------------------- standalone L-BFGS
 __global__ void k_lbfgs_init(long long B, int n, int m, const float *__restrict__ x0, KLbfgsPtrs p) {
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
 // their bit patterns order like the values); it must start at ~0.
 template <int TPL, bool SELF, bool SWEEP>
-__global__ void __launch_bounds__(kPlanWarps * 32, plan_min_blocks(TPL, SELF))
+__global__ void __launch_bounds__(plan_warps(TPL, SELF) * 32, plan_min_blocks(TPL, SELF))
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
            float *__restrict__ hist_y, unsigned long long *__restrict__ best_key, float *traj,
@@ -107,7 +111,7 @@ __global__ void __launch_bounds__(kPlanWarps * 32, plan_min_blocks(TPL, SELF))
     extern __shared__ float smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const long long B = (long long)kb.P * kb.S;
-    const long long b = (long long)blockIdx.x * kPlanWarps + wid;
+    const long long b = (long long)blockIdx.x * plan_warps(TPL, SELF) + wid;
     if (b >= B) return;
     const int T = kb.T, n = 7 * T, m = ko.m;
     const int p = (int)(b / kb.S);
@@ -172,8 +176,8 @@ __global__ void k_best(int P, const unsigned long long *__restrict__ key, int *_
     if (p < P) best[p] = key[p] == ~0ull ? -1 : (int)(key[p] & 0xffffffffull);
 }
 
-static size_t plan_smem_bytes(int T, bool self = false) {
-    return (size_t)kPlanWarps * warp_smem_floats(T, self) * sizeof(float);
+static size_t plan_smem_bytes(int T, bool self = false, int warps = kPlanWarps) {
+    return (size_t)warps * warp_smem_floats(T, self) * sizeof(float);
 }
 
 template <typename K>
@@ -213,14 +217,16 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
     cudaError_t e = cudaMemsetAsync(best_key, 0xff, sizeof(unsigned long long) * kb.P, st);
     if (e != cudaSuccess) return (int)e;
     const long long B = (long long)kb.P * kb.S;
-    const unsigned blocks = (unsigned)((B + kPlanWarps - 1) / kPlanWarps);
     const bool self = kc.w_s > 0.f;
-    const size_t smem = plan_smem_bytes(kb.T, self);
+    const int tpl = kb.T <= 32 ? 1 : kb.T <= 64 ? 2 : 4;
+    const int warps = self ? plan_warps(tpl, true) : plan_warps(tpl, false);
+    const unsigned blocks = (unsigned)((B + warps - 1) / warps);
+    const size_t smem = plan_smem_bytes(kb.T, self, warps);
     auto go = [&](auto kern) {
         int r = set_smem(kern, smem);
         if (r) return r;
-        kern<<<blocks, kPlanWarps * 32, smem, st>>>(rb, kc, ko, kb, seeds, hist_s, hist_y, best_key, traj, cost,
-                                                   success, metrics);
+        kern<<<blocks, warps * 32, smem, st>>>(rb, kc, ko, kb, seeds, hist_s, hist_y, best_key, traj, cost, success,
+                                               metrics);
         return (int)cudaGetLastError();
     };
     // variants: waypoints per lane x self-collision term x swept check

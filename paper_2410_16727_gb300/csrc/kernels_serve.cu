@@ -16,12 +16,16 @@ namespace dseed {
 #ifndef DSEED_SERVE_MINBLOCKS
 #define DSEED_SERVE_MINBLOCKS 4
 #endif
+#ifndef DSEED_SERVE_MINBLOCKS_T32
+#define DSEED_SERVE_MINBLOCKS_T32 5
+#endif
 constexpr int kServeWarps = 4;
 
-// Four resident blocks (128 registers): the round's bookkeeping keeps more
-// values live than the one-shot plan, which spills at 96.
+// Resident blocks the registers are sized for: five (96 registers) for T <= 32
+// without the swept check, whose round fits them with a few spilled bytes;
+// four (128) otherwise, where the round's bookkeeping would spill more.
 template <int TPL, bool SWEEP>
-__global__ void __launch_bounds__(kServeWarps * 32, DSEED_SERVE_MINBLOCKS)
+__global__ void __launch_bounds__(kServeWarps * 32, (TPL == 1 && !SWEEP) ? DSEED_SERVE_MINBLOCKS_T32 : DSEED_SERVE_MINBLOCKS)
     k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
             float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
     constexpr int NPL = 7 * TPL;
