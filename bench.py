@@ -33,8 +33,10 @@ from paper_2410_16727_gb300 import inputs as I  # noqa: E402
 
 METRIC = "seed-timestep cost+grad evals/s"
 UNIT = "ST-evals/s"
-# FP32 operations per seed-timestep evaluation of the fused kernel (cost +
-# adjoint + L-BFGS share), counted from the source; see the design doc.
+# FP32 operations per seed-timestep evaluation of the fused kernel, counted from
+# the source: kinematics with sincos ~400, 50 spheres ~90 each (their bound
+# checks, and the interpolation where a bound does not clear them), adjoint,
+# smoothness and limits ~500, the L-BFGS update's share ~350.
 FLOP_PER_ST = 5800.0
 # 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12

@@ -3,7 +3,7 @@ plain optimiser): generate problems on shelf scenes, solve them with the plain
 random-seed optimiser, train the conditional denoiser on the solutions
 (Eq. 1, optionally weighted as in Eq. 2), then propose seeds by DDIM and
 refine them with a few optimiser iterations.  The plain optimiser stays both
-the fallback and the judge (success is tested by the same kernels).
+the fallback and the arbiter of success (tested by the same kernels).
 
 Data handling (batch assembly, repetition of per-problem inputs) uses PyTorch
 indexing on the device; every numeric step of the method -- the optimiser,
