@@ -172,16 +172,6 @@ __device__ __forceinline__ Goal make_goal(const float *g) {
 
 enum { MODE_COST = 0, MODE_GRAD = 1, MODE_EVAL = 2 };
 
-// Spheres of one frame whose first ESDF loads are issued together.
-#ifndef DSEED_SPHERE_BATCH
-#define DSEED_SPHERE_BATCH 1
-#endif
-constexpr int kSphereBatch = DSEED_SPHERE_BATCH;
-// Skip a whole frame when the ESDF at its bounding sphere clears all its spheres.
-#ifndef DSEED_FRAME_EARLY_OUT
-#define DSEED_FRAME_EARLY_OUT 1
-#endif
-
 struct WaypointAcc {
     float c_world, c_goal;
     float min_clear;          // MODE_EVAL
@@ -195,21 +185,9 @@ struct WaypointAcc {
 // running sums F = sum g_k and M = sum c_k x g_k over the spheres met so far,
 // that is z_i . (M_all - M_<i) - (z_i x p_i) . (F_all - F_<i): the prefix
 // part b_i is recorded when frame i is reached, the rest once all spheres and
-// the goal wrench are in.
-#ifndef DSEED_ADJOINT_RECOMPUTE
-#define DSEED_ADJOINT_RECOMPUTE 1
-#endif
-// Unroll the 8-frame loop (1) or keep it rolled (0, default): one copy of the
+// the goal wrench are in.  The 8-frame loop stays rolled: one copy of the
 // sphere loop keeps the fused kernel small enough for the instruction cache
-// (rolled: 32% faster plans, bit-identical results).
-#ifndef DSEED_FRAME_UNROLL
-#define DSEED_FRAME_UNROLL 0
-#endif
-#if DSEED_FRAME_UNROLL
-#define DSEED_FRAME_LOOP _Pragma("unroll")
-#else
-#define DSEED_FRAME_LOOP _Pragma("unroll 1")
-#endif
+// (unrolled, the plans were 32% slower with the same results).
 
 // Self-collision scratch of one lane, in its warp's shared slice (element e of
 // lane l at sbuf[e * 32 + l]): the transforms (R row-major, p) of frames 1..6
@@ -243,11 +221,9 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
     const bool self_on = SELF && !interp;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
-    constexpr bool KEEP = MODE == MODE_GRAD && !DSEED_ADJOINT_RECOMPUTE;
-    float zj[KEEP ? 7 : 1][3], wj[KEEP ? 7 : 1][3];
     float *const sn = fsc, *const cs = fsc + 7 * 32, *const bj = fsc + 14 * 32;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
-    DSEED_FRAME_LOOP
+#pragma unroll 1
     for (int L = 1; L <= 8; ++L) {
         float st, ct;
         if (L <= 7) {
@@ -268,11 +244,6 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             float w0 = z1 * p[2] - z2 * p[1];
             float w1 = z2 * p[0] - z0 * p[2];
             float w2 = z0 * p[1] - z1 * p[0];
-            if (KEEP) {
-                const int ii = KEEP ? i : 0;
-                zj[ii][0] = z0; zj[ii][1] = z1; zj[ii][2] = z2;
-                wj[ii][0] = w0; wj[ii][1] = w1; wj[ii][2] = w2;
-            }
             bj[i * 32] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
         }
         if (self_on) {
@@ -358,7 +329,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
         pv[1] = fmaf(p[1] - sv.oy, sv.inv_res, -0.5f);
         pv[2] = fmaf(p[2] - sv.oz, sv.inv_res, -0.5f);
         const int k1 = rb.frame_begin[L];
-        if (DSEED_FRAME_EARLY_OUT && MODE != MODE_EVAL && sv.lip > 0.0f && k1 > rb.frame_begin[L - 1]) {
+        if (MODE != MODE_EVAL && sv.lip > 0.0f && k1 > rb.frame_begin[L - 1]) {
             // all spheres of the frame lie inside its bounding sphere (centre b,
             // radius R): for sphere k, phi(c_k) >= v_b - L (2 sqrt(3) res + R - r_k)
             // (corner of b's cell to corner of c_k's cell, through the clamped
@@ -373,30 +344,23 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
                               fmaxf(one_m_l * rb.frmin[L - 1], one_m_l * rb.frmax[L - 1]) + 1e-5f;
             if (corner_value(sv, ux, uy, uz) >= thr) continue;
         }
-        for (int k0 = rb.frame_begin[L - 1]; k0 < k1; k0 += kSphereBatch) {
-            // phase 1: one corner of each sphere's cell, all loads in flight together.
-            // Every corner of a cell lies within sqrt(3) res of the others, so for an
-            // L-Lipschitz field phi(c) >= v0 - L sqrt(3) res: when v0 >= r + eta +
-            // skip_pad the hinge is inactive and the sphere contributes nothing.
-            float v0[kSphereBatch];
-#pragma unroll
-            for (int c = 0; c < kSphereBatch; ++c) {
-                v0[c] = -CUDART_INF_F;
-                if (MODE != MODE_EVAL && k0 + c < k1) {
-                    const float4 s = rb.sph[k0 + c];
-                    const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
-                    const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
-                    const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
-                    v0[c] = corner_value(sv, ux, uy, uz);
-                }
+        for (int k = rb.frame_begin[L - 1]; k < k1; ++k) {
+            // one corner of the sphere's cell first: every corner lies within sqrt(3) res
+            // of the others, so for an L-Lipschitz field phi(c) >= v0 - L sqrt(3) res, and
+            // v0 >= r + eta + skip_pad means the hinge is inactive (the other 7 loads skipped)
+            float v0 = -CUDART_INF_F;
+            if (MODE != MODE_EVAL) {
+                const float4 s = rb.sph[k];
+                const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
+                const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
+                const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
+                v0 = corner_value(sv, ux, uy, uz);
             }
-            // phase 2: full interpolation of the spheres the bound cannot clear
-#pragma unroll
-            for (int c = 0; c < kSphereBatch; ++c) {
-                if (k0 + c >= k1) continue;
-                const float4 s = rb.sph[k0 + c];
+            // then the full interpolation of a sphere the bound cannot clear
+            {
+                const float4 s = rb.sph[k];
                 const float hinge_at = s.w + kc.eta;
-                if (MODE != MODE_EVAL && v0[c] >= hinge_at + sv.skip_pad) continue;
+                if (MODE != MODE_EVAL && v0 >= hinge_at + sv.skip_pad) continue;
                 const float ux = fmaf(Rv[0], s.x, fmaf(Rv[1], s.y, fmaf(Rv[2], s.z, pv[0])));
                 const float uy = fmaf(Rv[3], s.x, fmaf(Rv[4], s.y, fmaf(Rv[5], s.z, pv[1])));
                 const float uz = fmaf(Rv[6], s.x, fmaf(Rv[7], s.y, fmaf(Rv[8], s.z, pv[2])));
@@ -454,14 +418,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
         }
     }
     if (MODE == MODE_GRAD) {
-        if (KEEP) {
-#pragma unroll
-            for (int i = 0; i < 7; ++i) {
-                const int ii = KEEP ? i : 0;
-                gq[i] += (zj[ii][0] * Mx + zj[ii][1] * My + zj[ii][2] * Mz)
-                         - (wj[ii][0] * Fx + wj[ii][1] * Fy + wj[ii][2] * Fz) - bj[i * 32];
-            }
-        } else {
+        {
             // second pass: rebuild the joint axes z_i and origins p_i from the
             // stored sin/cos (bit-identical to the first pass) instead of keeping
             // 42 values per waypoint live across the sphere loop
