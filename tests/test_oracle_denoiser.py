@@ -43,7 +43,7 @@ def test_gradcheck_whole_network():
     flat.grad = None
     ref = loss(flat)
     ref.backward()
-    assert abs(l - float(ref)) < 1e-12
+    assert abs(l - float(ref.detach())) < 1e-12
     np.testing.assert_allclose(g, flat.grad.numpy(), rtol=1e-10, atol=1e-14)
 
 
