@@ -253,7 +253,10 @@ def run_gpu(args, rank: int, world: int):
         breakdown_ms={"esdf_build": esdf_avg, "plan": plan_avg},
         success_rate=success_rate, problems_solved=solved,
         wall_s_timed=wall,
-        gpu_launches=(len(cub) + 255) // 256 + 2,
+        # our kernels in the timed region: per step the ESDF build (one launch per 256
+        # scenes), the fused plan and the best-seed pick
+        gpu_launches=args.steps * ((len(cub) + 255) // 256 + 2),
+        gpu_launches_per_step=(len(cub) + 255) // 256 + 2,
         e2e={"value": D.job_throughput(st_evals, e2e_ms, world) if e_ms else None, "unit": UNIT,
              "ms_per_step": e2e_ms if e_ms else None,
              "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
