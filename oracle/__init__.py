@@ -8,5 +8,5 @@ part is pinned.
 """
 from .oracle import (  # noqa: F401
     build, load, Oracle, fk_frames, flange_pose, esdf_build, esdf_lookup, num_threads,
-    lbfgs_quadratic,
+    lbfgs_quadratic, success_thresholds,
 )

@@ -6,6 +6,7 @@ to float64 exactly, so the oracle and the CUDA path see the same numbers.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 from typing import Optional, Sequence
@@ -16,6 +17,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dseed_oracle.c")
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "libdseed_oracle.so")
+# Sec. 5.1's success thresholds, as the cited text fixture states them
+_THRESHOLDS = os.path.join(os.path.dirname(_HERE), "tests", "golden", "success_thresholds.txt")
 _lib = None
 
 _dp = C.POINTER(C.c_double)
@@ -97,6 +100,20 @@ def _ptr(a: np.ndarray):
     if a.dtype == np.int32:
         return a.ctypes.data_as(_ip)
     raise TypeError(a.dtype)
+
+
+def success_thresholds() -> np.ndarray:
+    """[delta_t (m), delta_r (rad)]: a plan succeeds when its final flange lies
+    closer than delta_t to the goal position and turns by less than delta_r
+    from the goal orientation (Sec. 5.1: 5 mm and 2.86 degrees), read from the
+    fixture that cites that passage (degrees converted to radians here)."""
+    vals = {}
+    with open(_THRESHOLDS) as f:
+        for line in f:
+            line = line.split("#", 1)[0].split()
+            if len(line) == 2:
+                vals[line[0]] = float(line[1])
+    return np.array([vals["delta_t_m"], math.radians(vals["delta_r_deg"])], dtype=np.float64)
 
 
 def num_threads() -> int:
@@ -265,7 +282,7 @@ class Oracle:
 
     def evaluate(self, scene: int, q_start, goal, x, thr=None):
         """Success flags [B] and metrics [B][7] (see orc_evaluate)."""
-        from_thr = _d(thr if thr is not None else [0.005, 2.86 * np.pi / 180.0])
+        from_thr = _d(thr if thr is not None else success_thresholds())
         x = _d(x)
         T = x.shape[-2]
         x = x.reshape(-1, T, 7)
@@ -292,7 +309,7 @@ class Oracle:
         P, S, T = seeds.shape[0], seeds.shape[1], seeds.shape[2]
         probs = self._problems(scenes, q_start, goal, T)
         o = _opt_struct(opt)
-        th = _d(thr if thr is not None else [0.005, 2.86 * np.pi / 180.0])
+        th = _d(thr if thr is not None else success_thresholds())
         x = np.zeros_like(seeds)
         f = np.zeros((P, S))
         ok = np.zeros((P, S), np.int32)

@@ -209,3 +209,20 @@ def test_full_batched_cost_grad_sampled(gpu_lib, batched_full):
         wc, wg = orc.cost(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], wl.seeds[p, s:s + 1])
         assert abs(c[p, s] - wc[0]) <= 1e-4 * max(abs(wc[0]), 1e-6)
         assert rel_l2(g[p, s], wg[0]) <= 1e-3
+
+
+def test_best_seed_pick_matches_oracle_pins(gpu_lib):
+    """The hand-built best-seed cases of the oracle's pins (one-iteration plans
+    keep the seeds): only the dearer seed succeeds, a tie of two successes, no
+    success, the cheapest success at the highest index.  The fused plan's success
+    flags and best seeds equal the pinned values."""
+    from test_oracle_success import EMPTY, GRID, ROBOT, best_seed_case
+    qs, goal, seeds, want = best_seed_case()
+    planner = api.Planner(ROBOT, I.CostParams(), I.OptParams(iters=1))
+    planner.set_scenes([EMPTY], [GRID])
+    P, S, T = seeds.shape[:3]
+    batch = planner.batch(qs.astype(np.float32), goal.astype(np.float32), np.zeros(P, np.int32), S, T)
+    out = planner.plan(batch, seeds.astype(np.float32))
+    np.testing.assert_array_equal(to_np(out["traj"]), seeds.astype(np.float32))
+    np.testing.assert_array_equal(to_np(out["success"]), [[0, 1, 0], [1, 1, 1], [0, 0, 0], [1, 0, 1]])
+    np.testing.assert_array_equal(to_np(out["best"]), want)
