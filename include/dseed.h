@@ -49,7 +49,7 @@
 extern "C" {
 #endif
 
-#define DSEED_ABI_VERSION 3
+#define DSEED_ABI_VERSION 4
 
 #define DSEED_MAX_SPHERES 64    /* collision spheres per robot */
 #define DSEED_MAX_T 128         /* waypoints per trajectory */
@@ -62,6 +62,7 @@ extern "C" {
 #define DSEED_EINVAL (-1)       /* bad argument: null pointer, size out of range, NaN parameter */
 #define DSEED_ENOMEM (-2)       /* host allocation failed, or a caller buffer is too small */
 #define DSEED_ECUDA (-3)        /* a CUDA call or kernel launch failed (message has the CUDA error) */
+#define DSEED_ETIMEOUT (-4)     /* serving only: a wait on the GPU reached the server's wait limit */
 
 /* Robot: a serial 7-joint arm in modified Denavit-Hartenberg form plus a
  * fixed flange frame, and its collision spheres.  Frame i (i = 1..7) turns
@@ -178,6 +179,15 @@ typedef struct {
 
 int dseed_abi_version(void);
 const char *dseed_last_error(void);
+
+/* What the roofline of the optimiser's FP32 kernels is computed from (no
+ * counterpart in the paper): streaming multiprocessors, their peak clock (kHz),
+ * L2 bytes, compute capability and FP32 lanes per SM, from the CUDA runtime's
+ * device attributes of `device`.  ECUDA when the device cannot be queried. */
+typedef struct {
+    int sm_count, sm_clock_khz, l2_bytes, cc_major, cc_minor, fp32_lanes_per_sm;
+} DseedDeviceInfo;
+int dseed_device_info(int device, DseedDeviceInfo *out);
 
 /* Copy and check a robot description.  *out receives a handle owned by the
  * caller until dseed_robot_destroy.  EINVAL on a null pointer, a sphere count
@@ -380,7 +390,9 @@ void dseed_server_destroy(DseedServer *server);
  * used id or a bad grid.  Asynchronous on the server's stream. */
 int  dseed_server_add_scene(DseedServer *server, int scene_id, const float *cuboids_host, int n,
                             const DseedGrid *grid);
-/* Release a scene; EINVAL while queued or admitted requests use it. */
+/* Release a scene once the work already enqueued on the server's stream is done
+ * (a bounded wait, DSEED_ETIMEOUT at the wait limit); EINVAL while queued or
+ * admitted requests use it. */
 int  dseed_server_remove_scene(DseedServer *server, int scene_id);
 /* Queue a request (host-side only, returns at once); *ticket identifies it. */
 int  dseed_server_submit(DseedServer *server, const DseedRequest *req, long long *ticket);
@@ -389,8 +401,18 @@ int  dseed_server_submit(DseedServer *server, const DseedRequest *req, long long
  * any request is admitted and fewer than two rounds are in flight.  Never
  * blocks on the GPU unless `wait` is non-zero, in which case it first waits for
  * the oldest round in flight.  *n_done (optional) receives the number of
- * requests that finished in this call. */
+ * requests that finished in this call.
+ * Every wait of the server on the GPU (this one, the reuse of a staging buffer
+ * before a round's table upload, and dseed_server_remove_scene's wait for work
+ * that reads the scene) polls an event against the wait limit; when the limit
+ * is reached the call returns DSEED_ETIMEOUT (the failure-detection status of
+ * a serving watchdog) with the round still in flight and nothing retired, so a
+ * later call can wait again or the caller can give up on the device. */
 int  dseed_server_step(DseedServer *server, int wait, int *n_done);
+/* Limit, in seconds (>= 0; 0 = do not wait at all), of every wait of the
+ * server on the GPU; 60 s when the server is created.  EINVAL for a negative
+ * or NaN limit. */
+int  dseed_server_set_wait_limit(DseedServer *server, double seconds);
 /* State of a ticket: 0 queued, 1 admitted, 2 done, -1 failed (scene missing
  * or request larger than the whole arena).  t_submit/t_done (optional)
  * receive the host steady-clock times in seconds of submission and of the step
@@ -589,8 +611,10 @@ int dseed_nn_upsample2_bf16(const void *x_dev, int N, int L, int C, void *y_dev,
  *   - Every GPU on which the library's device code is loaded holds the array
  *     until the process exits.
  *   - The first call on a device looks up the array's device address (with
- *     that device current) and caches it; make that first call before any
- *     stream capture begins.
+ *     that device current) and caches it with the id of the current context;
+ *     make that first call before any stream capture begins.  After a device
+ *     reset the next call sees a new context and looks the address up again
+ *     (also before any capture).
  *   - All calls share the one array, and it keeps what the last call left in
  *     it.  The call resets the parts that must start at zero itself, but two
  *     calls whose work overlaps on the GPU (different streams without

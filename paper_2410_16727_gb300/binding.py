@@ -99,13 +99,27 @@ class ServerStats(C.Structure):
                 ("arena_used", C.c_size_t), ("arena_peak", C.c_size_t)]
 
 
+class DeviceInfo(C.Structure):
+    _fields_ = [(k, C.c_int) for k in ("sm_count", "sm_clock_khz", "l2_bytes", "cc_major", "cc_minor",
+                                      "fp32_lanes_per_sm")]
+
+
 class DseedError(RuntimeError):
     pass
+
+
+class DseedTimeout(DseedError):
+    """DSEED_ETIMEOUT: a serving wait on the GPU reached the server's wait limit
+    (the work stays in flight)."""
+
+
+ETIMEOUT = -4
 
 
 _SIGS = {
     "dseed_abi_version": ([], C.c_int),
     "dseed_last_error": ([], C.c_char_p),
+    "dseed_device_info": ([C.c_int, C.POINTER(DeviceInfo)], C.c_int),
     "dseed_robot_create": ([C.POINTER(RobotDesc), C.POINTER(C.c_void_p)], C.c_int),
     "dseed_robot_destroy": ([C.c_void_p], None),
     "dseed_scene_build_esdf": ([C.c_void_p, C.c_int, C.POINTER(Grid), C.c_void_p, C.c_void_p], C.c_int),
@@ -134,6 +148,7 @@ _SIGS = {
     "dseed_server_remove_scene": ([C.c_void_p, C.c_int], C.c_int),
     "dseed_server_submit": ([C.c_void_p, C.POINTER(Request), C.POINTER(C.c_longlong)], C.c_int),
     "dseed_server_step": ([C.c_void_p, C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "dseed_server_set_wait_limit": ([C.c_void_p, C.c_double], C.c_int),
     "dseed_server_poll": ([C.c_void_p, C.c_longlong, C.POINTER(C.c_int), C.POINTER(C.c_double),
                            C.POINTER(C.c_double)], C.c_int),
     "dseed_server_stats": ([C.c_void_p, C.POINTER(ServerStats)], C.c_int),
@@ -210,7 +225,7 @@ def load():
 def _check(rc: int, what: str):
     if rc != 0:
         msg = load().dseed_last_error().decode(errors="replace")
-        raise DseedError(f"{what} failed with status {rc}: {msg}")
+        raise (DseedTimeout if rc == ETIMEOUT else DseedError)(f"{what} failed with status {rc}: {msg}")
 
 
 def _stream() -> int:
@@ -235,6 +250,13 @@ def _dev(t: Optional[torch.Tensor], dtype, name: str, shape=None):
 
 def abi_version() -> int:
     return int(load().dseed_abi_version())
+
+
+def device_info(device: int = 0) -> dict:
+    """SM count, peak SM clock (kHz), L2 bytes, compute capability, FP32 lanes per SM."""
+    d = DeviceInfo()
+    _check(load().dseed_device_info(int(device), C.byref(d)), "dseed_device_info")
+    return {k: int(getattr(d, k)) for k, _ in DeviceInfo._fields_}
 
 
 def last_error() -> str:
@@ -607,6 +629,10 @@ def server_step(h, wait: bool = False) -> int:
     n = C.c_int()
     _check(load().dseed_server_step(h, 1 if wait else 0, C.byref(n)), "dseed_server_step")
     return int(n.value)
+
+
+def server_set_wait_limit(h, seconds: float):
+    _check(load().dseed_server_set_wait_limit(h, float(seconds)), "dseed_server_set_wait_limit")
 
 
 def server_poll(h, ticket: int):

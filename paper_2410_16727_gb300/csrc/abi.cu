@@ -1,5 +1,7 @@
 // abi.cu -- host side of the C ABI declared in include/dseed.h: argument
 // checks, robot handles, workspace layouts and kernel launches.
+#include <cuda.h>            // driver-API types only; entry points come through the runtime
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -285,6 +287,25 @@ extern "C" {
 
 int dseed_abi_version(void) { return DSEED_ABI_VERSION; }
 
+int dseed_device_info(int device, DseedDeviceInfo *out) {
+    if (!out) return fail(DSEED_EINVAL, "out is NULL");
+    int v[5] = {0, 0, 0, 0, 0};
+    const cudaDeviceAttr attrs[5] = {cudaDevAttrMultiProcessorCount, cudaDevAttrClockRate, cudaDevAttrL2CacheSize,
+                                     cudaDevAttrComputeCapabilityMajor, cudaDevAttrComputeCapabilityMinor};
+    for (int i = 0; i < 5; ++i) {
+        const cudaError_t e = cudaDeviceGetAttribute(&v[i], attrs[i], device);
+        if (e != cudaSuccess) return fail(DSEED_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+    }
+    out->sm_count = v[0];
+    out->sm_clock_khz = v[1];
+    out->l2_bytes = v[2];
+    out->cc_major = v[3];
+    out->cc_minor = v[4];
+    // FP32 lanes per SM: 128 on every compute capability 8.6+ part, 10.x included
+    out->fp32_lanes_per_sm = (v[3] > 8 || (v[3] == 8 && v[4] >= 6)) ? 128 : 64;
+    return DSEED_OK;
+}
+
 const char *dseed_last_error(void) { return g_last_error.c_str(); }
 
 int dseed_robot_create(const DseedRobotDesc *desc, DseedRobot **out) {
@@ -546,7 +567,39 @@ static __device__ __align__(256) unsigned char g_plan_scratch[DSEED_STATIC_SCRAT
 namespace {
 constexpr int kMaxDevices = 64;
 std::mutex g_scratch_mutex;
-void *g_scratch_ptr[kMaxDevices] = {};
+// per device: the array's address and the id of the context it was looked up in
+struct ScratchSlot {
+    void *ptr = nullptr;
+    unsigned long long ctx_id = 0;
+    bool valid = false;
+};
+ScratchSlot g_scratch[kMaxDevices];
+
+// Unique id (for the process lifetime) of the current context, 0 when none is
+// current.  A device reset destroys the context that an address was looked up
+// in, and the next context may load the module elsewhere, so the cached address
+// is only reused while the context id matches.
+unsigned long long current_ctx_id() {
+    static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+    static PFN_cuCtxGetId_v12000 get_id = nullptr;
+    static bool resolved = false;
+    if (!resolved) {
+        cudaDriverEntryPointQueryResult q1, q2;
+        void *f1 = nullptr, *f2 = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 12000, cudaEnableDefault, &q1) == cudaSuccess &&
+            q1 == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<PFN_cuCtxGetCurrent_v4000>(f1);
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000, cudaEnableDefault, &q2) == cudaSuccess &&
+            q2 == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<PFN_cuCtxGetId_v12000>(f2);
+        resolved = true;
+    }
+    if (!get_current || !get_id) return 0;
+    CUcontext ctx = nullptr;
+    if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+    unsigned long long id = 0;
+    return get_id(ctx, &id) == CUDA_SUCCESS ? id : 0;
+}
 
 int static_scratch(void **out) {
     int dev = 0;
@@ -554,14 +607,18 @@ int static_scratch(void **out) {
     if (e != cudaSuccess) return fail(DSEED_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
     if (dev < 0 || dev >= kMaxDevices) return fail(DSEED_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
     std::lock_guard<std::mutex> lock(g_scratch_mutex);
-    if (!g_scratch_ptr[dev]) {
+    ScratchSlot &slot = g_scratch[dev];
+    const unsigned long long id = current_ctx_id();
+    if (!slot.valid || id == 0 || slot.ctx_id != id) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_plan_scratch);
+        e = cudaGetSymbolAddress(&p, g_plan_scratch);     // makes the device's primary context current if needed
         if (e != cudaSuccess)
             return fail(DSEED_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
-        g_scratch_ptr[dev] = p;
+        slot.ptr = p;
+        slot.ctx_id = current_ctx_id();
+        slot.valid = true;
     }
-    *out = g_scratch_ptr[dev];
+    *out = slot.ptr;
     return DSEED_OK;
 }
 }  // namespace

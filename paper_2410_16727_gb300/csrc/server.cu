@@ -13,6 +13,7 @@
 #include <memory>
 #include <new>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -185,6 +186,7 @@ struct DseedServer {
     std::deque<Round> inflight;
     std::unordered_map<long long, std::unique_ptr<Req>> reqs;
     long long next_ticket = 1;
+    double wait_limit_s = 60.0;    // limit of every wait on the GPU (dseed_server_set_wait_limit)
     DseedServerStats stats{};
 };
 
@@ -193,6 +195,24 @@ namespace {
 int cuda_err(cudaError_t e, const char *what) {
     if (e == cudaSuccess) return DSEED_OK;
     return set_error(DSEED_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Wait for `ev` by polling cudaEventQuery, the host thread yielding between
+// polls, for at most sv->wait_limit_s seconds.  On expiry DSEED_ETIMEOUT: the
+// work stays in flight and the server's state is unchanged, so a later call can
+// wait again.  The GPU never spins on the host's behalf.
+int bounded_wait(const DseedServer *sv, cudaEvent_t ev, const char *what) {
+    const double t0 = now_s();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(ev);
+        if (e == cudaSuccess) return DSEED_OK;
+        if (e != cudaErrorNotReady) return cuda_err(e, what);
+        const double waited = now_s() - t0;
+        if (waited >= sv->wait_limit_s)
+            return set_error(DSEED_ETIMEOUT, "%s: not complete after %.3g s (limit %.3g s); it stays in flight", what,
+                             waited, sv->wait_limit_s);
+        std::this_thread::yield();
+    }
 }
 
 size_t request_bytes(const DseedServer *sv, int S, int T) {
@@ -218,8 +238,12 @@ int retire(DseedServer *sv, bool wait_oldest, int *n_done) {
     bool first = true;
     while (!sv->inflight.empty()) {
         Round &rd = sv->inflight.front();
-        cudaError_t e = (wait_oldest && first) ? cudaEventSynchronize(rd.done) : cudaEventQuery(rd.done);
+        if (wait_oldest && first) {
+            const int r = bounded_wait(sv, rd.done, "serving round");
+            if (r) return r;
+        }
         first = false;
+        const cudaError_t e = cudaEventQuery(rd.done);
         if (e == cudaErrorNotReady) break;
         if (e != cudaSuccess) return cuda_err(e, "serving round");
         const double t = now_s();
@@ -277,7 +301,7 @@ int admit(DseedServer *sv) {
 
 int launch_round(DseedServer *sv) {
     // the staging half we fill must no longer be read by an earlier upload
-    int r = cuda_err(cudaEventSynchronize(sv->stage_free[sv->stage_half]), "staging wait");
+    int r = bounded_wait(sv, sv->stage_free[sv->stage_half], "staging wait");
     if (r) return r;
     dseed::ServeEntry *st = sv->stage + (size_t)sv->stage_half * kClasses * sv->max_requests;
     int counts[kClasses] = {0, 0, 0};
@@ -450,8 +474,12 @@ extern "C" int dseed_server_remove_scene(DseedServer *sv, int scene_id) {
     if (it == sv->scenes.end()) return set_error(DSEED_EINVAL, "scene %d is not resident", scene_id);
     if (it->second.users > 0) return set_error(DSEED_EINVAL, "scene %d is used by %d requests", scene_id, it->second.users);
     // stream-ordered: work already enqueued that reads the scene finishes first
-    cudaError_t e = cudaStreamSynchronize(sv->stream);
-    if (e != cudaSuccess) return cuda_err(e, "remove scene");
+    cudaEvent_t ev = nullptr;
+    int r = cuda_err(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "event");
+    if (!r) r = cuda_err(cudaEventRecord(ev, sv->stream), "event");
+    if (!r) r = bounded_wait(sv, ev, "remove scene");
+    if (ev) cudaEventDestroy(ev);
+    if (r) return r;
     arena_give(&sv->arena, it->second.off_esdf);
     arena_give(&sv->arena, it->second.off_cub);
     sv->scenes.erase(it);
@@ -487,6 +515,13 @@ extern "C" int dseed_server_step(DseedServer *sv, int wait, int *n_done) {
     if (r) return r;
     if (!sv->active.empty() && sv->inflight.size() < 2) r = launch_round(sv);
     return r;
+}
+
+extern "C" int dseed_server_set_wait_limit(DseedServer *sv, double seconds) {
+    if (!sv) return set_error(DSEED_EINVAL, "server is NULL");
+    if (!(seconds >= 0.0)) return set_error(DSEED_EINVAL, "wait limit must be >= 0 seconds (got %g)", seconds);
+    sv->wait_limit_s = seconds;
+    return DSEED_OK;
 }
 
 extern "C" int dseed_server_poll(DseedServer *sv, long long ticket, int *state, double *t_submit, double *t_done) {

@@ -145,7 +145,12 @@ class Server:
         return t
 
     def step(self, wait: bool = False) -> int:
+        """One scheduling step; with wait, raises binding.DseedTimeout when the
+        oldest round is not done within the wait limit (it stays in flight)."""
         return B.server_step(self.h, wait)
+
+    def set_wait_limit(self, seconds: float):
+        B.server_set_wait_limit(self.h, seconds)
 
     def poll(self, ticket: int):
         return B.server_poll(self.h, ticket)

@@ -44,7 +44,7 @@ def test_library_exports_every_declared_symbol(libpath):
 def test_library_loads_and_reports_version(libpath):
     lib = ctypes.CDLL(libpath)
     lib.dseed_abi_version.restype = ctypes.c_int
-    assert lib.dseed_abi_version() == 3
+    assert lib.dseed_abi_version() == 4
     lib.dseed_last_error.restype = ctypes.c_char_p
     assert lib.dseed_last_error() is not None
 
@@ -142,3 +142,16 @@ def test_robot_self_pairs_match_the_oracle_without_gpu(libpath):
     bad.self_margin = float("nan")
     with pytest.raises(BD.DseedError, match="self_margin"):
         BD.Robot(bad)
+
+
+def test_static_scratch_size_matches_header():
+    from paper_2410_16727_gb300 import binding as BD
+    text = open(os.path.join(ROOT, "include", "dseed.h")).read()
+    m = re.search(r"#define DSEED_STATIC_SCRATCH_BYTES \((\d+)u << (\d+)\)", text)
+    assert m and BD.STATIC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+
+
+def test_status_codes_match_header():
+    from paper_2410_16727_gb300 import binding as BD
+    text = open(os.path.join(ROOT, "include", "dseed.h")).read()
+    assert int(re.search(r"#define DSEED_ETIMEOUT \((-\d+)\)", text).group(1)) == BD.ETIMEOUT

@@ -163,3 +163,48 @@ def test_poisson_trace_small(gpu_lib, setup):
     assert np.isfinite(res["latency_s"]).all() and (res["latency_s"] > 0).all()
     assert 0 < s["p50_ms"] <= s["p99_ms"]
     sv.close()
+
+
+def test_wait_limit_times_out_and_round_stays_in_flight(gpu_lib, setup):
+    """A serving watchdog: with the wait limit at 0 a wait on a round still on
+    the GPU returns DSEED_ETIMEOUT at once and retires nothing; with the limit
+    restored the same request drains to exactly what it computes without the
+    timeout.  The failure is made on the host (a zero limit), the GPU only runs
+    an ordinary round."""
+    wl, planner, cases = setup
+    p = 0
+    S, T = 1024, 128                       # a round long enough to be in flight when polled
+    seeds = I.make_seeds(np.random.default_rng(11), wl.q_start[p], wl.q_goal[p], S, T, wl.robot.limits)
+
+    def serve(limit_zero):
+        sv = _server(wl, arena_bytes=1 << 30, round_iters=ITERS)
+        torch.cuda.synchronize()
+        t = sv.submit(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], seeds)
+        sv.step()                          # admits the request and launches its only round
+        timed_out = False
+        if limit_zero:
+            sv.set_wait_limit(0.0)
+            with pytest.raises(B.DseedTimeout, match="stays in flight"):
+                sv.step(wait=True)
+            timed_out = True
+            assert sv.poll(t)[0] == 1      # still admitted: nothing retired
+            st = sv.stats()
+            assert st.completed == 0 and st.active == 1
+            sv.set_wait_limit(60.0)
+        sv.drain([t])
+        assert sv.poll(t)[0] == 2
+        res = {k: v.clone() for k, v in sv.result(t).items()}
+        sv.close()
+        return res, timed_out
+
+    plain, _ = serve(False)
+    after, timed_out = serve(True)
+    assert timed_out
+    for k in plain:
+        assert torch.equal(plain[k], after[k]), k
+    with pytest.raises(B.DseedError):
+        sv = _server(wl)
+        try:
+            sv.set_wait_limit(-1.0)
+        finally:
+            sv.close()
