@@ -4,10 +4,12 @@ independent replicas under torchrun).
 One step = the whole hot path over one batch: the brute-force ESDF build of
 every scene, then the fused optimiser (FK -> spheres -> ESDF trilinear + hinge,
 smoothness, goal, limits, hand-written adjoint, L-BFGS update; `iters` times)
-and the success test / best-seed selection.  Default workload: 256 problems,
-each with its own shelf scene (20-60 cuboids, 128^3 ESDF at 1 cm), 64 seeds x
-32 waypoints, 100 iterations.  Metric: seed-timestep cost+grad evaluations per
-second = P * S * T * iters / step time.
+and the success test / best-seed selection.  Default workload (the largest that
+fits one GPU, "stress"): 1024 problems over 16 dense-clutter scenes of 200
+cuboids (256^3 ESDF at 5 mm), 128 seeds x 64 waypoints, 200 iterations; the
+"batched" workload (256 problems, one shelf scene each, 128^3 at 1 cm, 64 seeds
+x 32 waypoints, 100 iterations) is measured alongside.  Metric: seed-timestep
+cost+grad evaluations per second = P * S * T * iters / step time.
 
 Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle on
 a bounded sample of the same workload instead.
@@ -33,17 +35,40 @@ from paper_2410_16727_gb300 import inputs as I  # noqa: E402
 
 METRIC = "seed-timestep cost+grad evals/s"
 UNIT = "ST-evals/s"
-# FP32 operations per seed-timestep evaluation of the fused kernel, counted from
-# the source: kinematics with sincos ~400, 50 spheres ~90 each (their bound
-# checks, and the interpolation where a bound does not clear them), adjoint,
-# smoothness and limits ~500, the L-BFGS update's share ~350.
-FLOP_PER_ST = 5800.0
-# 152 SMs x 128 FP32 lanes x 2 (FMA) x 2.07 GHz
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one k_plan launch of the full batched workload (256
-# problems x 64 seeds x 32 waypoints x 100 iterations, 256 shelf ESDFs at 128^3):
-# ncu capture of that launch, 387.64 MB read + 191.05 MB written.
-K_PLAN_DRAM_BYTES_BATCHED = 387.64e6 + 191.05e6
+# Algorithmic FP32 work per seed-timestep evaluation of the fused kernel: about
+# 4 kflop for kinematics, sphere placement, 50 trilinear lookups with their
+# gradient, the Jacobian-transpose adjoint and the smoothness/goal/limit terms,
+# plus about 0.3 kflop for the L-BFGS update's share.
+FLOP_PER_ST = 4300.0
+# Algorithmic HBM bytes per seed-timestep evaluation when nothing is reused from
+# L2: the ESDF corners of 50 spheres (8 x 4 B each) plus the trajectory in and
+# gradient out (56 B).
+HBM_BYTES_PER_ST_NO_REUSE = 50 * 8 * 4 + 56
+
+# ncu counters of one k_plan launch (dram__bytes_read.sum + dram__bytes_write.sum,
+# lts__t_sector_hit_rate.pct), per seed-timestep evaluation, valid only for the
+# kernel source they were taken with (KERNEL_SOURCES hashed below); the command
+# and the raw figures are in profiles/k_plan_<workload>.md.
+KERNEL_SOURCES = ("paper_2410_16727_gb300/csrc/device.cuh", "paper_2410_16727_gb300/csrc/kernels_plan.cu",
+                  "paper_2410_16727_gb300/csrc/internal.h")
+NCU_COUNTERS = {}
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(HERE, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(HERE, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
 def parse():
@@ -52,8 +77,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="dseed", choices=["dseed", "reference"])
-    ap.add_argument("--workload", default="batched", choices=list(I.WORKLOADS))
-    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU-baseline sample")
+    ap.add_argument("--workload", default="stress", choices=list(I.WORKLOADS))
+    ap.add_argument("--also", default="batched",
+                    help="comma-separated workloads measured alongside the headline ('' for none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
@@ -128,19 +154,47 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- GPU arm
 
-def run_gpu(args, rank: int, world: int):
+def workload_spec(args, name: str) -> I.WorkloadSpec:
+    spec = I.WORKLOADS[name]
+    if args.problems:
+        # smaller case of the same workload (profiling): this many problems, at most as many scenes
+        spec = I.WorkloadSpec(spec.name, spec.config_id, min(spec.n_scenes, args.problems), args.problems,
+                              spec.S, spec.T, spec.iters, spec.scene, spec.grid)
+    return spec
+
+
+def workload_config(spec: I.WorkloadSpec, world: int) -> dict:
+    """The `config` object of both arms (the same dict for the same workload)."""
+    return {"workload": f"{spec.name}: {spec.n_problems} problems x {spec.S} seeds x {spec.T} waypoints, "
+                        f"{spec.iters} L-BFGS iterations, {spec.n_scenes} {spec.scene} scenes, "
+                        f"ESDF {spec.grid.n[0]}^3 at {spec.grid.res * 1000:g} mm",
+            "problems": spec.n_problems, "seeds": spec.S, "waypoints": spec.T, "iters": spec.iters,
+            "scenes": spec.n_scenes, "l2": "flushed between steps (512 MiB write); inputs larger than L2",
+            "parallelism": f"replicas x{world}"}
+
+
+def fp32_peak(device: int):
+    """Peak FP32 rate of the device (TFLOP/s) from its attributes: SMs x FP32
+    lanes x 2 (FMA) x peak SM clock."""
+    from paper_2410_16727_gb300 import binding as B
+    d = B.device_info(device)
+    peak = d["sm_count"] * d["fp32_lanes_per_sm"] * 2 * d["sm_clock_khz"] * 1e3 / 1e12
+    return peak, (f"derived from cudaDeviceGetAttribute: {d['sm_count']} SMs x {d['fp32_lanes_per_sm']} FP32 "
+                  f"lanes x 2 x {d['sm_clock_khz'] / 1e3:g} MHz"), d
+
+
+def measure_plain(args, spec: I.WorkloadSpec, rank: int, world: int, with_e2e: bool):
+    """Time steps (ESDF build of every scene + fused plan + best seed) of one
+    workload with its inputs resident; with_e2e also times the same step end to
+    end from pinned host buffers through the public API."""
     import torch
     from paper_2410_16727_gb300 import api, binding as B
 
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    spec = I.WORKLOADS[args.workload]
     robot = I.make_robot()
     # each rank plans its own problems (replicas of the workload with different seeds)
-    if args.problems:
-        spec = I.WorkloadSpec(spec.name, spec.config_id, min(spec.n_scenes, args.problems), args.problems,
-                              spec.S, spec.T, spec.iters, spec.scene, spec.grid)
     cub, grids = I.make_scenes(spec, seed_offset=rank)
     planner = api.Planner(robot, I.CostParams(), I.OptParams(iters=spec.iters), dev)
     planner.set_scenes(cub, grids)
@@ -197,77 +251,108 @@ def run_gpu(args, rank: int, world: int):
     success_rate = float(out["success"].float().mean())
     solved = float((out["best"] >= 0).float().mean())
 
-    # end to end through the public API with host buffers: H2D of the step's
-    # inputs (cuboids, starts, goals, scene ids, seeds) from pinned memory, the
-    # step, D2H of trajectories, costs, success flags and best seeds
-    h_cub = planner.cub_packed.cpu().pin_memory()      # every scene's cuboids, packed
-    h_q = torch.as_tensor(wl.q_start).pin_memory()
-    h_goal = torch.as_tensor(wl.goal).pin_memory()
-    h_sc = torch.as_tensor(wl.scene_of_problem).pin_memory()
-    h_seeds = torch.as_tensor(wl.seeds).pin_memory()
-    h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "metrics"}
-    d_q = batch.q_start
-    d_goal = batch.goal
-    d_sc = batch.scene_of_problem
-    h2d = sum(t.numel() * t.element_size() for t in (h_cub, h_q, h_goal, h_sc, h_seeds))
-    d2h = sum(t.numel() * t.element_size() for t in h_out.values())
+    e2e = None
+    if with_e2e:
+        # end to end through the public API with host buffers: H2D of the step's
+        # inputs (cuboids, starts, goals, scene ids, seeds) from pinned memory, the
+        # step, D2H of trajectories, costs, success flags and best seeds
+        h_cub = planner.cub_packed.cpu().pin_memory()      # every scene's cuboids, packed
+        h_q = torch.as_tensor(wl.q_start).pin_memory()
+        h_goal = torch.as_tensor(wl.goal).pin_memory()
+        h_sc = torch.as_tensor(wl.scene_of_problem).pin_memory()
+        h_seeds = torch.as_tensor(wl.seeds).pin_memory()
+        h_out = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in out.items() if k != "metrics"}
+        d_q, d_goal, d_sc = batch.q_start, batch.goal, batch.scene_of_problem
+        h2d = sum(t.numel() * t.element_size() for t in (h_cub, h_q, h_goal, h_sc, h_seeds))
+        d2h = sum(t.numel() * t.element_size() for t in h_out.values())
 
-    def e2e_step():
-        d_q.copy_(h_q, non_blocking=True)
-        d_goal.copy_(h_goal, non_blocking=True)
-        d_sc.copy_(h_sc, non_blocking=True)
-        seeds.copy_(h_seeds, non_blocking=True)
-        planner.rebuild_scenes(h_cub)                    # one copy of all cuboids, then the ESDF build
-        B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
-        for k, v in h_out.items():
-            v.copy_(out[k], non_blocking=True)
+        def e2e_step():
+            d_q.copy_(h_q, non_blocking=True)
+            d_goal.copy_(h_goal, non_blocking=True)
+            d_sc.copy_(h_sc, non_blocking=True)
+            seeds.copy_(h_seeds, non_blocking=True)
+            planner.rebuild_scenes(h_cub)                    # one copy of all cuboids, then the ESDF build
+            B.plan_batch(planner.robot, batch.desc, batch.pr, seeds, ws, out)
+            for k, v in h_out.items():
+                v.copy_(out[k], non_blocking=True)
 
-    for _ in range(0 if args.no_e2e else 2):
-        e2e_step()
-    torch.cuda.synchronize()
-    e_ms = []
-    for _ in range(0 if args.no_e2e else max(2, args.steps)):
-        flush.zero_()
+        for _ in range(2):
+            e2e_step()
         torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e_ms.append(a.elapsed_time(b))
-    e2e_ms = D.max_over_ranks(sum(e_ms) / len(e_ms) if e_ms else float("nan"), dev)
+        e_ms = []
+        for _ in range(max(2, args.steps)):
+            flush.zero_()
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            e_ms.append(a.elapsed_time(b))
+        e2e_ms = D.max_over_ranks(sum(e_ms) / len(e_ms), dev)
+        e2e = {"value": D.job_throughput(st_evals, e2e_ms, world), "unit": UNIT, "ms_per_step": e2e_ms,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
     plan_avg = sum(plan_ms) / len(plan_ms)
     esdf_avg = sum(esdf_ms) / len(esdf_ms)
+    peak, peak_src, dinfo = fp32_peak(local)
     achieved = FLOP_PER_ST * st_evals / (plan_avg * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "peak_source": peak_src,
+            "flop_per_unit": FLOP_PER_ST, "unit_of_work": "seed-timestep evaluation",
+            "units_per_launch": st_evals, "ms_per_launch": plan_avg, "traffic": None,
+            "traffic_source": None}
+    # HBM side of the same launch (the cost+adjoint gathers): ncu DRAM bytes and
+    # L2 hit rate of the kernel as built now, scaled to this launch's evaluations
+    hbm = {"peak_gbs": measured_peaks().get("hbm_gbs"), "peak_source": "MEASURED_PEAKS.json hbm_gbs",
+           "algorithmic_bytes_per_unit_no_l2_reuse": HBM_BYTES_PER_ST_NO_REUSE,
+           "no_reuse_gbs_at_this_rate": HBM_BYTES_PER_ST_NO_REUSE * st_evals / (plan_avg * 1e-3) / 1e9}
+    ctr = NCU_COUNTERS.get(spec.name)
+    if ctr and ctr["kernel_hash"] == kernel_hash():
+        traffic = ctr["dram_bytes_per_st"] * st_evals
+        roof["traffic"] = traffic
+        roof["traffic_source"] = ctr["capture"]
+        hbm.update(dram_bytes_per_launch=traffic, achieved_gbs=traffic / (plan_avg * 1e-3) / 1e9,
+                   l2_hit_pct=ctr["l2_hit_pct"], counters_from=ctr["capture"])
+        if hbm["peak_gbs"]:
+            hbm["frac"] = hbm["achieved_gbs"] / hbm["peak_gbs"]
+    else:
+        hbm["note"] = "no ncu capture of the kernel as built now"
+    roof["hbm"] = hbm
     res = dict(
-        metric=METRIC, value=D.job_throughput(st_evals, ms, world), unit=UNIT, n_gpus=world, steps=args.steps,
-        warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak", vs_baseline=None,
-        dtype="f32", data="synthetic",
-        config={"workload": f"{spec.name}: {P} problems x {S} seeds x {T} waypoints, {iters} L-BFGS iterations, "
-                            f"{spec.scene} scenes, ESDF {spec.grid.n[0]}^3 at {spec.grid.res * 100:g} cm",
-                "problems": P, "seeds": S, "waypoints": T, "iters": iters, "scenes": len(cub),
-                "l2": "flushed between steps (512 MiB write)", "parallelism": f"replicas x{world}"},
-        plans_per_s=P * world / (ms * 1e-3),
-        breakdown_ms={"esdf_build": esdf_avg, "plan": plan_avg},
-        success_rate=success_rate, problems_solved=solved,
-        wall_s_timed=wall,
+        config=workload_config(spec, world), ms_per_step=ms, value=D.job_throughput(st_evals, ms, world),
+        plans_per_s=P * world / (ms * 1e-3), breakdown_ms={"esdf_build": esdf_avg, "plan": plan_avg},
+        seed_success=success_rate, problems_solved=solved, wall_s_timed=wall,
         # our kernels in the timed region: per step the ESDF build (one launch per 256
         # scenes), the fused plan and the best-seed pick
         gpu_launches=args.steps * ((len(cub) + 255) // 256 + 2),
         gpu_launches_per_step=(len(cub) + 255) // 256 + 2,
-        e2e={"value": D.job_throughput(st_evals, e2e_ms, world) if e_ms else None, "unit": UNIT,
-             "ms_per_step": e2e_ms if e_ms else None,
-             "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        roofline={"bound": "alu", "kernel": "k_plan (fused cost+adjoint+L-BFGS)", "achieved": achieved,
-                  "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                  "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
-                  "traffic": (K_PLAN_DRAM_BYTES_BATCHED
-                              if (spec.name, P, S, T, iters) == ("batched", 256, 64, 32, 100) else None),
-                  "traffic_source": "ncu dram__bytes_read+write of the full-size launch"},
-        clocks=sampler.summary(),
-    )
+        roofline=roof, clocks=sampler.summary(), device=dinfo)
+    if e2e is not None:
+        res["e2e"] = e2e
+    del flush, ws, out, seeds
+    torch.cuda.empty_cache()
+    return res, wl
+
+
+def run_gpu(args, rank: int, world: int):
+    spec = workload_spec(args, args.workload)
+    part, wl = measure_plain(args, spec, rank, world, with_e2e=not args.no_e2e)
+    res = dict(metric=METRIC, value=part.pop("value"), unit=UNIT, n_gpus=world, steps=args.steps,
+               warmup=args.warmup, ms_per_step=part.pop("ms_per_step"), higher_is_better=True, scaling="weak",
+               vs_baseline=None, dtype="f32", data="synthetic", config=part.pop("config"))
+    res.update(part)
+    if "e2e" not in res:
+        res["e2e"] = {"value": None, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    also = {}
+    for name in [n for n in args.also.split(",") if n and n != args.workload]:
+        a, _ = measure_plain(args, workload_spec(args, name), rank, world, with_e2e=False)
+        a.pop("clocks", None)
+        a.pop("device", None)
+        also[name] = a
+    if also:
+        res["also"] = also
     return res, wl
 
 
@@ -599,53 +684,73 @@ def run_learned(args) -> dict:
 
 # ---------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(spec, budget_s: float, seed_offset: int = 0):
-    """Time the FP64 oracle on whole problems of the workload (ESDF build of the
-    problem's scene + all seeds x iterations + success test) until the budget is
-    spent.  Inputs are drawn with the oracle's own callbacks."""
+def _oracle_problems(spec, n: int, seed_offset: int = 0):
+    """The first n problems of the workload exactly as the GPU arm draws them,
+    with the oracle's own ESDFs of the scenes they use (inputs drawn with the
+    oracle's callbacks).  Returns (oracle, workload, ESDF build seconds)."""
     import oracle
     robot = I.make_robot()
-    done = 0
-    t_total = 0.0
-    k = 0
-    chunk = max(1, min(spec.n_problems, oracle.num_threads() // 4 or 1))
     cub_all, grids_all = I.make_scenes(spec, seed_offset=seed_offset)
-    while t_total < budget_s and k < spec.n_problems:
-        idx = list(range(k, min(k + chunk, spec.n_problems)))
-        scenes = sorted({int(p * len(cub_all) // spec.n_problems) for p in idx})
-        t0 = time.perf_counter()
-        orc = oracle.Oracle(robot, I.CostParams(), [grids_all[s] for s in scenes], [cub_all[s] for s in scenes],
-                            T=spec.T)
-        t_esdf = time.perf_counter() - t0
-        # problem generation (not timed) draws each problem's own stream, as in the full workload
-        wl = I.build_workload(spec, [cub_all[s] for s in scenes], [grids_all[s] for s in scenes],
-                              orc.clearance, orc.flange_pose, n_problems=len(idx), seed_offset=seed_offset)
-        t0 = time.perf_counter()
-        orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
-        t_total += t_esdf + (time.perf_counter() - t0)
-        done += len(idx) * spec.S * spec.T * spec.iters
-        k += len(idx)
-    return done / t_total, k, t_total, oracle.num_threads()
+    scenes = sorted({p * spec.n_scenes // spec.n_problems for p in range(n)})
+    t0 = time.perf_counter()
+    orc = oracle.Oracle(robot, I.CostParams(), [grids_all[s] for s in scenes], [cub_all[s] for s in scenes],
+                        T=spec.T)
+    t_esdf = time.perf_counter() - t0
+    wl = I.build_workload(spec, [cub_all[s] for s in scenes], [grids_all[s] for s in scenes],
+                          orc.clearance, orc.flange_pose, n_problems=n, seed_offset=seed_offset)
+    return orc, wl, t_esdf, len(scenes)
+
+
+def oracle_sample(spec, seed_offset: int = 0):
+    """The FP64 oracle on a 1% sample of the workload (its first ceil(P / 100)
+    problems): the ESDF build of the scenes they use plus every seed's plan and
+    success test, timed on all host cores.  Returns (ST evals/s, description, cores)."""
+    import oracle
+    n = max(1, -(-spec.n_problems // 100))
+    orc, wl, t_esdf, n_sc = _oracle_problems(spec, n, seed_offset)
+    t0 = time.perf_counter()
+    orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
+    t_plan = time.perf_counter() - t0
+    evals = n * spec.S * spec.T * spec.iters
+    desc = (f"{n} of {spec.n_problems} problems ({n * spec.S} seeds x {spec.T} waypoints x {spec.iters} "
+            f"iterations) + the ESDF build of the {n_sc} scene(s) they use: {t_plan:.1f} s plan + "
+            f"{t_esdf:.1f} s ESDF")
+    return evals / (t_plan + t_esdf), desc, oracle.num_threads()
 
 
 def run_reference(args, rank: int, world: int):
-    spec = I.WORKLOADS[args.workload]
-    vals = []
-    sample = None
-    for _ in range(args.warmup):
-        oracle_sample(spec, min(2.0, args.cpu_seconds / 4))
-    for _ in range(args.steps):
-        v, k, t, cores = oracle_sample(spec, args.cpu_seconds / max(1, args.steps) * 2)
-        vals.append(v)
-        sample = f"{k} of {spec.n_problems} problems (ESDF build + {spec.S} seeds x {spec.iters} iterations each)"
-    v = statistics.mean(vals)
-    st_evals = spec.n_problems * spec.S * spec.T * spec.iters
+    """The FP64 oracle on the host cores, one problem of the workload per step:
+    the plans of its seeds, timed, plus its share of its scene's ESDF build
+    (the build time, measured once, divided by the problems that share the scene)."""
+    import oracle
+    spec = workload_spec(args, args.workload)
+    n_needed = args.warmup + args.steps
+    per_scene = max(1, spec.n_problems // spec.n_scenes)
+    # problems 0..n-1, wrapping over the first few if more steps than problems are asked for
+    n = min(n_needed, spec.n_problems)
+    orc, wl, t_esdf, n_sc = _oracle_problems(spec, n)
+    esdf_share = t_esdf / n_sc / per_scene
+    step_s = []
+    for k in range(n_needed):
+        p = k % n
+        t0 = time.perf_counter()
+        orc.plan(wl.scene_of_problem[p:p + 1], wl.q_start[p:p + 1], wl.goal[p:p + 1], wl.seeds[p:p + 1], wl.opt)
+        dt = time.perf_counter() - t0 + esdf_share
+        if k >= args.warmup:
+            step_s.append(dt)
+    evals = spec.S * spec.T * spec.iters
+    ms = statistics.mean(step_s) * 1e3
+    v = evals / (ms * 1e-3)
+    full_ms = spec.n_problems * ms
+    sample = (f"one problem per step ({spec.S} seeds x {spec.T} waypoints x {spec.iters} iterations, plans timed) "
+              f"+ 1/{per_scene} of its scene's measured ESDF build ({t_esdf / n_sc:.2f} s); "
+              f"{args.steps} steps over problems 0..{n - 1}")
     return dict(impl="reference", metric=METRIC, value=v, unit=UNIT, n_gpus=world, steps=args.steps,
-                warmup=args.warmup, ms_per_step=st_evals / v * 1e3, higher_is_better=True, scaling="weak",
-                vs_baseline=None, dtype="f64", data="synthetic",
-                config={"workload": spec.name, "problems": spec.n_problems, "seeds": spec.S, "waypoints": spec.T,
-                        "iters": spec.iters},
-                cpu_baseline={"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+                warmup=args.warmup, ms_per_step=ms, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", config=workload_config(spec, world),
+                extrapolated_ms_per_full_workload=full_ms,
+                cpu_baseline={"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                              "sample": sample},
                 e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
 
 
@@ -668,10 +773,8 @@ def main():
     if rank == 0 and not args.no_learned:
         res["learned"] = run_learned(args)
     if rank == 0 and not args.no_cpu_baseline:
-        v, k, t, cores = oracle_sample(I.WORKLOADS[args.workload], args.cpu_seconds)
-        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": f"{k} of {wl.P} problems (ESDF build + {wl.S} seeds x {wl.opt.iters} "
-                                         f"iterations each), {t:.1f} s"}
+        v, desc, cores = oracle_sample(workload_spec(args, args.workload))
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:

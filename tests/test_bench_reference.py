@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 
 def test_reference_arm_json_line():
     out = subprocess.run([sys.executable, os.path.join(HERE, "..", "bench.py"), "--impl", "reference",
-                          "--steps", "1", "--warmup", "0", "--cpu-seconds", "1", "--workload", "tiny"],
+                          "--steps", "2", "--warmup", "1", "--workload", "tiny"],
                          capture_output=True, text=True, timeout=600, check=True).stdout
     line = json.loads(out.strip().splitlines()[-1])
     for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
@@ -18,7 +18,14 @@ def test_reference_arm_json_line():
         assert k in line, k
     assert line["impl"] == "reference"
     assert line["value"] > 0 and line["higher_is_better"] is True
-    assert line["config"]["workload"] == "tiny"
+    # the same config object as the GPU arm's line for this workload
+    sys.path.insert(0, os.path.join(HERE, ".."))
+    import bench
+    from paper_2410_16727_gb300 import inputs as I
+    assert line["config"] == bench.workload_config(I.WORKLOADS["tiny"], 1)
+    # the step time is what one step measured: value x step time = one problem's evaluations
+    spec = I.WORKLOADS["tiny"]
+    assert abs(line["value"] * line["ms_per_step"] * 1e-3 - spec.S * spec.T * spec.iters) < 1e-6 * line["value"]
     cb = line["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == line["value"] and cb["sample"]
     e2e = line["e2e"]
