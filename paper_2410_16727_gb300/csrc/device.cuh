@@ -507,7 +507,12 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
     const int lane = threadIdx.x & 31;
     float c_world = 0.f, c_smooth = 0.f, c_goal = 0.f, c_limit = 0.f;
     float min_clear = CUDART_INF_F, pos_err = 0.f, rot_err = 0.f, max_jerk = 0.f, lim_viol = 0.f;
-    float gq[TPL][7];
+    // With several waypoints per lane (and no swept check) the waypoint loop stays
+    // rolled, so the kinematics / sphere / adjoint body is in the instruction
+    // stream once: each waypoint's gradient row is kept in ws.gs (the lane's own
+    // rows only) instead of a register array indexed by the waypoint.
+    constexpr bool kRoll = TPL >= 2 && !SWEEP;
+    float gq[kRoll ? 1 : TPL][7];
     const float inv_dt = kc.inv_dt;
     const int R3 = (T + kPad) * 7;
     if (MODE == MODE_GRAD && SWEEP) {
@@ -515,8 +520,33 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
         for (int e = lane; e < T * 7; e += 32) ws.gs[e] = 0.f;
         __syncwarp();
     }
+    if (kRoll) {
+#pragma unroll 1
+        for (int u = 0; u < TPL; ++u) {
+            const int t0 = lane + 32 * u;   // waypoint t = t0 + 1
+            if (t0 < T) {
+                float gw[7];
 #pragma unroll
-    for (int u = 0; u < TPL; ++u) {
+                for (int j = 0; j < 7; ++j) gw[j] = 0.f;
+                WaypointAcc acc{0.f, 0.f, CUDART_INF_F, 0.f, 0.f};
+                const float *y = ws.xs + (t0 + kPad) * 7;
+                waypoint_terms<MODE, SELF>(rb, kc, sv, y, y, 0.0f, false, t0 == T - 1, G, acc, gw, ws.es + lane,
+                                           ws.self);
+                c_world += acc.c_world;
+                c_goal += acc.c_goal;
+                if (MODE == MODE_EVAL) {
+                    min_clear = fminf(min_clear, acc.min_clear);
+                    if (t0 == T - 1) { pos_err = acc.pos_err; rot_err = acc.rot_err; }
+                }
+                if (MODE == MODE_GRAD) {
+#pragma unroll
+                    for (int j = 0; j < 7; ++j) ws.gs[t0 * 7 + j] = gw[j];
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < (kRoll ? 0 : TPL); ++u) {
         const int t0 = lane + 32 * u;   // waypoint t = t0 + 1
 #pragma unroll
         for (int j = 0; j < 7; ++j) gq[u][j] = 0.f;
@@ -566,11 +596,12 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
         __syncwarp();
         for (int e = lane; e < kPad * 7 * 3; e += 32) ws.es[(e / (kPad * 7)) * R3 + T * 7 + e % (kPad * 7)] = 0.f;
     }
-#pragma unroll
+#pragma unroll(kRoll ? 1 : TPL)
     for (int u = 0; u < TPL; ++u) {
         const int t0 = lane + 32 * u;
         if (t0 < T) {
             const float *y = ws.xs + (t0 + kPad) * 7;   // y_t; y - 7 = y_{t-1}, ...
+            float *gr = kRoll ? ws.gs + t0 * 7 : gq[kRoll ? 0 : u];
 #pragma unroll
             for (int j = 0; j < 7; ++j) {
                 const float y0 = y[j], y1 = y[j - 7], y2 = y[j - 14], y3 = y[j - 21];
@@ -583,11 +614,11 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
                 if (y0 > hi) {
                     viol = y0 - hi;
                     c_limit += kc.w_l * viol * viol;
-                    gq[u][j] += 2.0f * kc.w_l * viol;
+                    if (MODE == MODE_GRAD) gr[j] += 2.0f * kc.w_l * viol;
                 } else if (y0 < lo) {
                     viol = lo - y0;
                     c_limit += kc.w_l * viol * viol;
-                    gq[u][j] -= 2.0f * kc.w_l * viol;
+                    if (MODE == MODE_GRAD) gr[j] -= 2.0f * kc.w_l * viol;
                 }
                 if (MODE == MODE_EVAL) {
                     max_jerk = fmaxf(max_jerk, fabsf(jk));
@@ -605,14 +636,15 @@ __device__ __forceinline__ EvalOut warp_eval(const KRobot &rb, const KCost &kc, 
         __syncwarp();
         // transposed stencils: waypoint s receives e_v(s) - e_v(s+1),
         // e_a(s) - 2 e_a(s+1) + e_a(s+2), e_j(s) - 3 e_j(s+1) + 3 e_j(s+2) - e_j(s+3)
-#pragma unroll
+#pragma unroll(kRoll ? 1 : TPL)
         for (int u = 0; u < TPL; ++u) {
             const int t0 = lane + 32 * u;
             if (t0 < T) {
                 const float *ev = ws.es + t0 * 7, *ea = ev + R3, *ej = ev + 2 * R3;
+                const float *gr = kRoll ? ws.gs + t0 * 7 : gq[kRoll ? 0 : u];
 #pragma unroll
                 for (int j = 0; j < 7; ++j) {
-                    float g = gq[u][j];
+                    float g = gr[j];
                     g += ev[j] - ev[j + 7];
                     g += ea[j] - 2.0f * ea[j + 7] + ea[j + 14];
                     g += ej[j] - 3.0f * ej[j + 7] + 3.0f * ej[j + 14] - ej[j + 21];

@@ -226,3 +226,49 @@ def test_best_seed_pick_matches_oracle_pins(gpu_lib):
     np.testing.assert_array_equal(to_np(out["traj"]), seeds.astype(np.float32))
     np.testing.assert_array_equal(to_np(out["success"]), [[0, 1, 0], [1, 1, 1], [0, 0, 0], [1, 0, 1]])
     np.testing.assert_array_equal(to_np(out["best"]), want)
+
+
+def _fd_gradient(orc, scene, q_start, goal, x, h=1e-6, kink=0.05):
+    """Central differences of the FP64 oracle cost on every coordinate of one
+    trajectory x [T][7] (all perturbed copies in one batched oracle call), and a
+    mask of the coordinates with no hinge kink or cell face within h (equal
+    one-sided slopes)."""
+    flat = x.reshape(-1).astype(np.float64)
+    n = flat.size
+    pert = np.repeat(flat[None], 2 * n + 1, axis=0)
+    idx = np.arange(n)
+    pert[1 + idx, idx] += h
+    pert[1 + n + idx, idx] -= h
+    f = orc.cost(scene, q_start, goal, pert.reshape(2 * n + 1, *x.shape), grad=False)
+    f0, fp, fm = f[0], f[1:n + 1], f[n + 1:]
+    smooth = np.abs((fp - f0) / h - (f0 - fm) / h) < kink
+    return (fp - fm) / (2 * h), smooth
+
+
+def test_full_batched_gradient_against_finite_differences(gpu_lib, batched_full):
+    """The GPU adjoint on a 1% sample of the 16384 seeds of the full batched
+    launch, at the seeds and after 10 optimiser iterations (closer to the
+    obstacles, more active hinges), against central differences (h = 1e-6) of
+    the FP64 oracle cost: within 1e-3 relative L2 per trajectory over the
+    coordinates whose one-sided slopes agree."""
+    wl, orc = batched_full
+    planner, batch = gpu_side(wl)
+    seeds = _cuda(wl.seeds)
+    p10 = api.Planner(wl.robot, wl.cost, I.OptParams(iters=10))
+    p10.set_scenes(wl.cuboids, wl.grids)
+    x10 = p10.plan(p10.batch(wl.q_start, wl.goal, wl.scene_of_problem, wl.S, wl.T), seeds)["traj"]
+    rng = np.random.default_rng(11)
+    flat = rng.choice(wl.P * wl.S, size=(wl.P * wl.S) // 100, replace=False)
+    n_hinge = 0
+    for xs in (seeds, x10):
+        c, g = B.cost_grad(planner.robot, batch.desc, batch.pr, xs)
+        g, xh = to_np(g), to_np(xs)
+        for f in flat:
+            p, s = divmod(int(f), wl.S)
+            fd, smooth = _fd_gradient(orc, int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], xh[p, s])
+            assert smooth.mean() > 0.9
+            gs = g[p, s].reshape(-1)
+            assert rel_l2(gs[smooth], fd[smooth]) <= 1e-3, (p, s, rel_l2(gs[smooth], fd[smooth]))
+            n_hinge += int(orc.cost(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], xh[p, s][None],
+                                    grad=False, terms=True)[1][0, 0] > 0)
+    assert n_hinge >= 10, "the sample should include trajectories with active collision hinges"
