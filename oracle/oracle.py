@@ -205,7 +205,7 @@ class Oracle:
     """Problems of one workload: robot, cost parameters, per-scene ESDFs (built by
     the oracle itself from the cuboids), starts and goals."""
 
-    def __init__(self, robot, cost, grids: Sequence, cuboids: Sequence, T: int):
+    def __init__(self, robot, cost, grids: Sequence, cuboids: Sequence, T: int, phis: Optional[Sequence] = None):
         self._lib = load()
         self.T = int(T)
         self._keep = []
@@ -225,7 +225,8 @@ class Oracle:
         self.robot.self_pair = self.self_mask.ctypes.data_as(C.POINTER(C.c_ubyte))
         self.cp = _CostParams(*[float(v) for v in cost.as_array()], int(cost.n_sweep))
         self.grids_meta = list(grids)
-        self.phis = [esdf_build(c, g) for c, g in zip(cuboids, grids)]
+        # phis: ESDFs this oracle built earlier for the same scenes (reused, not rebuilt)
+        self.phis = list(phis) if phis is not None else [esdf_build(c, g) for c, g in zip(cuboids, grids)]
         self.grids = [_grid_struct(g, phi) for g, phi in zip(self.grids_meta, self.phis)]
 
     # -- problem descriptors ------------------------------------------------

@@ -204,11 +204,12 @@ __device__ __forceinline__ unsigned long long frame_bits(const KRobot &rb, int a
 }
 
 // Per-lane scratch of the frame loop (element e of lane l at fsc[e * 32], fsc
-// already offset by l): sin and cos of the joint angles [0, 14) and the adjoint
-// prefixes b_i [14, 21).  The loop runs rolled, so these are indexed by the
-// frame number; in shared memory they stay out of the L1 cache that the ESDF
-// gathers use.
-constexpr int kFrameScratch = 21;
+// already offset by l): the joint axes z_i [0, 21), the moments z_i x p_i of
+// the axes about the origin [21, 42) and the adjoint prefixes b_i [42, 49),
+// written as the chain is walked and read by the adjoint's second pass.  The
+// loop runs rolled, so these are indexed by the frame number; in shared memory
+// they stay out of the L1 cache that the ESDF gathers use.
+constexpr int kFrameScratch = 49;
 
 // The configuration is q = qt (interp false) or the swept-check interpolant
 // q = qt + u (qp - qt) of the segment from qp = y_{t-1} to qt = y_t (interp
@@ -221,7 +222,7 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
     const bool self_on = SELF && !interp;
     float R[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
     float p[3] = {0.f, 0.f, 0.f};
-    float *const sn = fsc, *const cs = fsc + 7 * 32, *const bj = fsc + 14 * 32;
+    float *const zs = fsc, *const ws_ = fsc + 21 * 32, *const bj = fsc + 42 * 32;
     float Fx = 0.f, Fy = 0.f, Fz = 0.f, Mx = 0.f, My = 0.f, Mz = 0.f;
 #pragma unroll 1
     for (int L = 1; L <= 8; ++L) {
@@ -229,10 +230,6 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
         if (L <= 7) {
             const float qL = interp ? fmaf(u, qp[L - 1] - qt[L - 1], qt[L - 1]) : qt[L - 1];
             sincosf(qL + rb.off[L - 1], &st, &ct);
-            if (MODE == MODE_GRAD) {
-                sn[(L - 1) * 32] = st;
-                cs[(L - 1) * 32] = ct;
-            }
         } else {
             st = rb.sf8;
             ct = rb.cf8;
@@ -245,6 +242,8 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             float w1 = z2 * p[0] - z0 * p[2];
             float w2 = z0 * p[1] - z1 * p[0];
             bj[i * 32] = (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz);
+            zs[(3 * i) * 32] = z0; zs[(3 * i + 1) * 32] = z1; zs[(3 * i + 2) * 32] = z2;
+            ws_[(3 * i) * 32] = w0; ws_[(3 * i + 1) * 32] = w1; ws_[(3 * i + 2) * 32] = w2;
         }
         if (self_on) {
             // C_self against frames a <= L - 2: for a checked pair (k on frame L, j on
@@ -419,11 +418,9 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
     }
     if (MODE == MODE_GRAD) {
         {
-            // second pass: rebuild the joint axes z_i and origins p_i from the
-            // stored sin/cos (bit-identical to the first pass) instead of keeping
-            // 42 values per waypoint live across the sphere loop
-            float R2[9] = {1.f, 0.f, 0.f, 0.f, 1.f, 0.f, 0.f, 0.f, 1.f};
-            float p2[3] = {0.f, 0.f, 0.f};
+            // second pass: the joint axes z_i and moments z_i x p_i recorded by the
+            // first pass (kept in the frame scratch rather than live across the
+            // sphere loop) against the total wrench
             // self-collision reactions deposited on frames 1..6: joint i moves frames
             // >= i + 1, so it takes the deposits of frames a >= i + 1 (a suffix sum)
             float SD[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -435,11 +432,8 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
             }
 #pragma unroll
             for (int i = 0; i < 7; ++i) {
-                dh_step(R2, p2, rb.a[i], rb.d[i], rb.ca[i], rb.sa[i], cs[i * 32], sn[i * 32]);
-                const float z0 = R2[2], z1 = R2[5], z2 = R2[8];
-                const float w0 = z1 * p2[2] - z2 * p2[1];
-                const float w1 = z2 * p2[0] - z0 * p2[2];
-                const float w2 = z0 * p2[1] - z1 * p2[0];
+                const float z0 = zs[(3 * i) * 32], z1 = zs[(3 * i + 1) * 32], z2 = zs[(3 * i + 2) * 32];
+                const float w0 = ws_[(3 * i) * 32], w1 = ws_[(3 * i + 1) * 32], w2 = ws_[(3 * i + 2) * 32];
                 gq[i] += (z0 * Mx + z1 * My + z2 * Mz) - (w0 * Fx + w1 * Fy + w2 * Fz) - bj[i * 32];
                 if (self_on) {
                     gq[i] += (z0 * SD[3] + z1 * SD[4] + z2 * SD[5]) - (w0 * SD[0] + w1 * SD[1] + w2 * SD[2]);

@@ -97,6 +97,20 @@ __global__ void __launch_bounds__(kPlanWarps * 32)
 }
 
 // ---------------------------------------------------------------- fused optimiser
+// Drop a seed's dead L-BFGS history from L2 without writing it back to HBM:
+// once the seed's last update is done nothing reads the pairs again, and a
+// write-back would only cost DRAM traffic.  Only the 128-byte lines lying
+// wholly inside [base, base + nfloats) are dropped; a line shared with a
+// neighbouring seed's region may still be live and is left alone.
+__device__ __forceinline__ void discard_dead_lines(const float *base, size_t nfloats) {
+    const int lane = threadIdx.x & 31;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(base), e = a + nfloats * sizeof(float);
+    const uintptr_t first = (a + 127) & ~static_cast<uintptr_t>(127), last = e & ~static_cast<uintptr_t>(127);
+    for (uintptr_t l = first + (uintptr_t)lane * 128; l < last; l += 32 * 128)
+        asm volatile("discard.global.L2 [%0], 128;" ::"l"(__cvta_generic_to_global(reinterpret_cast<const void *>(l)))
+                     : "memory");
+}
+
 // Per warp: load seed -> iters x (cost+adjoint of the trial point, L-BFGS
 // update) -> success test of the accepted point -> outputs.  best_key[p] holds
 // (cost bits << 32 | seed) of the best successful seed (costs are >= 0, so
@@ -148,6 +162,10 @@ __global__ void __launch_bounds__(plan_warps(TPL, SELF) * 32, plan_min_blocks(TP
         __syncwarp();
         lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S, Y, xt);
     }
+    // every lane's history stores are done before its lines are dropped
+    __syncwarp();
+    discard_dead_lines(S, (size_t)m * n);
+    discard_dead_lines(Y, (size_t)m * n);
     // success test of the accepted point
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
     __syncwarp();

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import gpu_side, oracle_workload, rel_l2, to_np
+from gpu_helpers import check_success_agreement, gpu_side, oracle_workload, rel_l2, to_np
 from paper_2410_16727_gb300 import api, binding as B, inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -102,8 +102,8 @@ def test_plan_tiny_success_agreement(gpu_lib):
     out = planner.plan(batch, wl.seeds)
     ref = orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
     ok = to_np(out["success"]).astype(bool)
-    agree = (ok == ref["success"]).mean()
-    assert agree >= AGREE, (agree, ok.mean(), ref["success"].mean())
+    check_success_agreement(ok, to_np(out["metrics"]), ref["success"], ref["metrics"], AGREE,
+                            to_np(out["traj"]), ref["traj"])
     assert ok.any(), "some seeds should succeed"
     # costs of seeds that both sides solve agree loosely (different float paths through 100 steps)
     both = ok & ref["success"]
@@ -178,8 +178,10 @@ def batched_full():
 def test_full_batched_plan_parity(gpu_lib, batched_full):
     """256 problems x 64 seeds x 32 waypoints, 100 iterations, in one plan call (as
     timed by the benchmark); the oracle re-plans every one of the 16384 seeds.
-    Success flags agree on >= 99% of them (FP32 and FP64 runs of a non-convex
-    optimisation part ways on a few hard seeds after tens of iterations)."""
+    Success flags agree on >= 99% of them, and every seed on which they differ
+    ends near a success threshold on one side (FP32 and FP64 runs of a
+    non-convex optimisation part ways by millimetres on a few hard seeds after
+    tens of iterations)."""
     wl, orc = batched_full
     planner, batch = gpu_side(wl)
     out = planner.plan(batch, wl.seeds)
@@ -187,8 +189,8 @@ def test_full_batched_plan_parity(gpu_lib, batched_full):
     ok = to_np(out["success"]).astype(bool)
     cost = to_np(out["cost"])
     ref = orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
-    agree = (ok == ref["success"]).mean()
-    assert agree >= AGREE, agree
+    agree, near, bif = check_success_agreement(ok, to_np(out["metrics"]), ref["success"], ref["metrics"], AGREE,
+                                               to_np(out["traj"]), ref["traj"])
     both = ok & ref["success"]
     rel = np.abs(cost[both] - ref["cost"][both]) / ref["cost"][both]
     assert np.median(rel) < 1e-2

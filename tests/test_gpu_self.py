@@ -10,7 +10,7 @@ import torch
 
 import oracle
 from golden.read import read
-from gpu_helpers import rel_l2, to_np
+from gpu_helpers import check_success_agreement, rel_l2, to_np
 from paper_2410_16727_gb300 import api, binding as B, inputs as I
 
 pytestmark = pytest.mark.gpu
@@ -22,13 +22,22 @@ def _cuda(a):
     return torch.as_tensor(np.ascontiguousarray(a, np.float32)).cuda()
 
 
-@pytest.fixture(scope="module")
-def tiny():
+def _tiny(n_problems):
     spec = I.WORKLOADS["tiny"]
     cub, grids = I.make_scenes(spec)
     orc = oracle.Oracle(I.make_robot(), COST, grids, cub, T=32)
-    wl = I.build_workload(spec, cub, grids, orc.clearance, orc.flange_pose, n_problems=8)
+    wl = I.build_workload(spec, cub, grids, orc.clearance, orc.flange_pose, n_problems=n_problems)
     return wl, orc
+
+
+@pytest.fixture(scope="module")
+def tiny():
+    return _tiny(8)
+
+
+@pytest.fixture(scope="module")
+def tiny32():
+    return _tiny(32)
 
 
 def _gpu(wl, T=None, S=None):
@@ -112,32 +121,35 @@ def test_plan_first_iterations_follow_oracle(gpu_lib, tiny, iters):
     assert np.quantile(rel, 0.95) <= tol and rel.max() <= 10 * tol, (np.quantile(rel, 0.95), rel.max())
 
 
-def test_plan_agrees_with_oracle(gpu_lib, tiny):
-    """100 iterations: the FP32 and FP64 runs follow each other closely for the
-    first iterations (previous test) and then part ways on some seeds: the self
-    pairs add many hinge kinks to a non-convex problem, and a seed can settle in
-    another local minimum.  Measured: 97.7% of 256 seeds agree, 99.1% of those
-    away from every success threshold; the bounds below leave room for that."""
-    wl, orc = tiny
+def test_plan_agrees_with_oracle(gpu_lib, tiny32):
+    """100 iterations on 32 problems x 32 seeds (1024 seeds).  The FP32 and FP64
+    runs follow each other to ~1e-6 relative cost for the first iterations
+    (previous test) and part ways by millimetres later on some seeds.  Success
+    flags agree on >= 99% of the seeds, every seed on which they differ ends
+    near a success threshold on one side (clearance within 5 mm of zero with
+    the self pairs included, or just beyond a soft joint limit), and every seed
+    away from the thresholds agrees."""
+    wl, orc = tiny32
     planner, batch = _gpu(wl)
     out = planner.plan(batch, wl.seeds)
     ok = to_np(out["success"]).astype(bool)
     met = to_np(out["metrics"])
     ref = orc.plan(wl.scene_of_problem, wl.q_start, wl.goal, wl.seeds, wl.opt)
-    rmet = ref["metrics"]
-    assert (ok == ref["success"]).mean() >= 0.95
-    # away from the success thresholds: clearance 0, 5 mm, 2.86 degrees
-    clear = lambda m: (np.abs(m[..., 0]) > 3e-3) & (np.abs(m[..., 1] - 0.005) > 5e-4) & \
-        (np.abs(m[..., 2] - np.radians(2.86)) > 5e-3)
-    far = clear(met) & clear(rmet)
-    assert far.mean() > 0.5
-    assert (ok[far] == ref["success"][far]).mean() >= 0.98, (ok[far] != ref["success"][far]).sum()
+    agree, near, _ = check_success_agreement(ok, met, ref["success"], ref["metrics"], 0.99, to_np(out["traj"]),
+                                             ref["traj"])
+    assert near < 0.6
     both = ok & ref["success"]
     if both.any():
         rel = np.abs(to_np(out["cost"])[both] - ref["cost"][both]) / ref["cost"][both]
         assert np.median(rel) < 2e-2
     # successful plans are free of self-collision (the clearance includes the checked pairs)
     assert (met[ok][:, 0] >= 0).all()
+    # the GPU's success test is the oracle's: the FP64 evaluation of the GPU's own trajectories
+    traj = to_np(out["traj"])
+    for p in range(wl.P):
+        want, wmet = orc.evaluate(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], traj[p])
+        far = np.abs(wmet[:, 0]) > 1e-5
+        assert np.array_equal(ok[p][far], want[far])
 
 
 def test_server_refuses_self_term(gpu_lib, tiny):

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 import torch
 
-from gpu_helpers import gpu_side, oracle_workload, rel_l2, to_np
+from gpu_helpers import check_success_agreement, gpu_side, oracle_workload, rel_l2, to_np
 from paper_2410_16727_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
@@ -35,8 +35,8 @@ def test_stress_plan_sampled_parity(gpu_lib, stress):
     ref = orc.plan(wl.scene_of_problem[p_idx], wl.q_start[p_idx], wl.goal[p_idx],
                    wl.seeds[p_idx, s_idx][:, None], wl.opt)
     ref_ok = ref["success"][:, 0]
-    agree = (ok[p_idx, s_idx] == ref_ok).mean()
-    assert agree >= AGREE, agree
+    check_success_agreement(ok[p_idx, s_idx], to_np(out["metrics"])[p_idx, s_idx], ref_ok, ref["metrics"][:, 0],
+                            AGREE, to_np(out["traj"])[p_idx, s_idx], ref["traj"][:, 0])
     both = ok[p_idx, s_idx] & ref_ok
     rel = np.abs(cost[p_idx, s_idx][both] - ref["cost"][both, 0]) / ref["cost"][both, 0]
     assert np.median(rel) < 1e-2
