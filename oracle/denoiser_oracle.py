@@ -14,6 +14,12 @@ Pins (tests/test_oracle_denoiser.py): finite-difference gradcheck of the whole
 network on a small configuration, group-norm moments, Mish closed forms, the
 sinusoidal embedding's closed form, DDPM noising and the DDIM step identities.
 
+Cost-guided sampling (guided_ddim, the appendix's Eq. 5 read for a
+deterministic DDIM sampler; pins in tests/test_oracle_guided.py: the closed form
+of eps-free DDIM, the descent direction against central differences of the cost
+in the diffused space, the per-entry cap, and the guided-step count of the
+schedule).
+
 Also Eq. 2's loss measured on the robot (fk_mse): the drawn and the predicted
 noise are decoded to the joint configurations they stand for and placed by a
 forward-kinematics chain of 4x4 modified-DH products written here (pins in
@@ -213,3 +219,91 @@ def fk_mse(robot, lin, eps, pred, res_scale: float, weights=None):
     loss = (w.view(-1, 1, 1, 1) * (cp - cl) ** 2).sum() / cp.numel()
     loss.backward()
     return float(loss.detach()), pr.grad.detach().numpy()
+
+
+# ------------------------------------------------------------------ cost-guided sampling (Eq. 5)
+
+def normalise_joints(limits, q):
+    """Joints to [-1, 1] by the mechanical limits (App. A.4): 2 (q - lo) / (hi - lo) - 1."""
+    lim = np.asarray(limits, np.float64)
+    lo, hi = lim[:, 0], lim[:, 1]
+    return 2.0 * (np.asarray(q, np.float64) - lo) / (hi - lo) - 1.0
+
+
+def straight_path(qs_n, qg_n, T: int):
+    """The straight start-goal path in normalised joints at waypoints t = 1..T
+    (fraction t / T): [N][T][7]."""
+    tau = (np.arange(1, T + 1, dtype=np.float64) / T)[None, :, None]
+    return (1.0 - tau) * np.asarray(qs_n, np.float64)[:, None, :] + tau * np.asarray(qg_n, np.float64)[:, None, :]
+
+
+def decode_joints(limits, lin, r, res_scale: float):
+    """Joint trajectories a diffused residual r stands for: the normalised
+    straight path plus r / res_scale, clipped to [-1, 1] (inside the limits),
+    un-normalised as mid + half * n."""
+    lim = np.asarray(limits, np.float64)
+    mid, half = (lim[:, 0] + lim[:, 1]) / 2.0, (lim[:, 1] - lim[:, 0]) / 2.0
+    return mid + half * np.clip(lin + r / res_scale, -1.0, 1.0)
+
+
+def ddim_schedule(K: int, steps: int):
+    """Evenly spaced step indices of the K-step schedule, from K - 1 down to 0."""
+    return np.linspace(K - 1, 0, steps).round().astype(int)
+
+
+def guided_ddim(spec, flat_params, noise, q_start, q_goal, goal, occ, limits, res_scale, abar, steps, clip,
+                k_guide, n_grad, alpha, cap, cost_grad, eps_fn=None):
+    """DDIM sampling with the cost guidance of the paper's appendix (Eq. 5),
+    as read for a deterministic sampler: after each denoising step that reaches
+    a step index below k_guide, except the last step, the samples take n_grad
+    descent steps on the plan cost C of their problem,
+        x <- x + clip(-alpha dC/dx, -cap, cap),   dC/dx = dC/dq * half / res_scale,
+    where q = decode_joints(x) and half = (hi - lo) / 2 per joint (the limit clip
+    of the decoding passes the gradient through).  All per sample: noise, the
+    starts, goal configurations, goal poses and occupancy rows [N][...].
+    cost_grad(q [N][T][7]) -> dC/dq [N][T][7]; eps_fn(x, k) replaces the
+    network's noise prediction when given.  Returns (joint-space proposals
+    [N][T][7], final residuals [N][T][7])."""
+    noise = np.asarray(noise, np.float64)
+    N, T = noise.shape[0], noise.shape[1]
+    lim = np.asarray(limits, np.float64)
+    half = (lim[:, 1] - lim[:, 0]) / 2.0
+    qs_n, qg_n = normalise_joints(lim, q_start), normalise_joints(lim, q_goal)
+    lin = straight_path(qs_n, qg_n, T)
+    ks = ddim_schedule(spec.K, steps)
+    x = noise.copy()
+    for i, k in enumerate(ks):
+        if eps_fn is not None:
+            eps = eps_fn(x, int(k))
+        else:
+            eps = predict(spec, flat_params, x, np.full(N, int(k)), qs_n, qg_n, goal, occ)
+        last = i + 1 == len(ks)
+        x = ddim_step(x, eps, float(abar[k]), 1.0 if last else float(abar[ks[i + 1]]), clip)
+        if not last and int(ks[i + 1]) < k_guide and alpha != 0.0:
+            x = guided_descent(x, lin, lim, res_scale, n_grad, alpha, cap, cost_grad)
+    return decode_joints(lim, lin, x, res_scale), x
+
+
+def guided_descent(x, lin, limits, res_scale, n_grad, alpha, cap, cost_grad):
+    """n_grad capped descent steps on C(decode_joints(x)) in the diffused space:
+    x <- x + clip(-alpha (dC/dq) (half / res_scale), -cap, cap)."""
+    lim = np.asarray(limits, np.float64)
+    half = (lim[:, 1] - lim[:, 0]) / 2.0
+    x = np.asarray(x, np.float64)
+    for _ in range(n_grad):
+        g = cost_grad(decode_joints(lim, lin, x, res_scale))
+        x = x + np.clip(-alpha * g * half / res_scale, -cap, cap)
+    return x
+
+
+def cosine_abar(K: int, s: float = 0.008) -> np.ndarray:
+    """The squared-cosine noise schedule: with f(t) = cos^2(pi/2 (t/K + s)/(1 + s)),
+    beta_k = 1 - f(k + 1) / f(k) capped at 0.999, and abar_k = prod_{j <= k} (1 - beta_j),
+    k = 0..K-1."""
+    f = [math.cos(math.pi / 2 * (t / K + s) / (1 + s)) ** 2 for t in range(K + 1)]
+    out = np.empty(K)
+    acc = 1.0
+    for k in range(K):
+        acc *= 1.0 - min(1.0 - f[k + 1] / f[k], 0.999)
+        out[k] = acc
+    return out
