@@ -91,6 +91,10 @@ def parse():
     ap.add_argument("--learned-scenes", type=int, default=512, help="training scenes (x 196 problems each)")
     ap.add_argument("--learned-steps", type=int, default=6000, help="denoiser training steps (batch 256)")
     ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
+    ap.add_argument("--no-learned-stress", action="store_true",
+                    help="skip the learned proposal on the stress workload and the serving mix")
+    ap.add_argument("--clutter-scenes", type=int, default=256,
+                    help="dense-clutter training scenes (x 128 problems each) of the stress-workload denoiser")
     ap.add_argument("--learned-fk", action="store_true",
                     help="also train a denoiser with Eq. 2's loss measured on the robot and compare it")
     ap.add_argument("--problems", type=int, default=None,
@@ -682,6 +686,148 @@ def run_learned(args) -> dict:
     return out
 
 
+# ---------------------------------------------------------------------------- learned proposal on the stress and serving workloads
+
+def run_learned_stress(args, wl) -> dict:
+    """Learned seeding on the stress workload and in the serving mix.
+
+    Training: problems on generated dense-clutter scenes (the stress family,
+    other seeds), solved by the plain optimiser at the stress horizon (64
+    seeds x 200 iterations, T = 64); the best successful solution of each
+    solved problem (and its reversal) trains the denoiser at 32 waypoints
+    (every second waypoint).  Stress: the benchmark's own 1024 problems, plain
+    (its 128 random seeds at several iteration budgets) against DDIM
+    proposals (32 waypoints resampled in time to 64) refined by the plain
+    optimiser; plans/s at matched success.  Serving mix: the serving
+    workload's requests (horizons 32, 48, 64) seeded on arrival (the proposals
+    resampled to each request's horizon) against the plain requests."""
+    import torch
+    from paper_2410_16727_gb300 import api, denoiser as DN, learned as L, netspec as NS, serving as SV
+
+    robot = I.make_robot()
+    out = {}
+    planner = api.Planner(robot)
+    t0 = time.perf_counter()
+    tr = L.make_problems(planner, args.clutter_scenes, 128, seed=0, kind="clutter")
+    data = L.build_dataset(planner, robot, tr)
+    torch.cuda.synchronize()
+    out["train_data"] = {"scenes": args.clutter_scenes, "problems": int(tr.q_start.shape[0]),
+                         "trajectories": int(data.x0.shape[0]), "seconds": round(time.perf_counter() - t0, 1),
+                         "solved_at": "T = 64, 64 random seeds x 200 iterations; trained at 32 waypoints"}
+    net = DN.Denoiser(NS.NetSpec(), seed=0)
+    t0 = time.perf_counter()
+    losses = L.train(net, data, args.learned_steps, batch=256, lr=3e-4, log_every=max(1, args.learned_steps // 4))
+    torch.cuda.synchronize()
+    out["training"] = {"steps": args.learned_steps, "batch": 256, "seconds": round(time.perf_counter() - t0, 1),
+                       "loss": [round(l, 4) for _, l in losses]}
+    del data, tr
+    planner.set_scenes(wl.cuboids, wl.grids)
+    dev = planner.device
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a)).to(dev)
+    occ = L.occupancy(planner, wl.cuboids, L.OCC_GRIDS["clutter"])
+    ps = L.ProblemSet(wl.cuboids, wl.grids, t(wl.scene_of_problem), t(wl.q_start), t(wl.q_goal), t(wl.goal), occ,
+                      planner.table, T=wl.T, iters=wl.opt.iters, kind="clutter")
+    P = wl.P
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t_ = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t_
+
+    def score(o):
+        return float((o["best"] >= 0).float().mean()), float(o["success"].float().mean())
+
+    rnd = t(wl.seeds)
+    plain = []
+    L.solve(planner, ps, rnd, 10, chunk=P)                                     # warm-up
+    for S_p, it in ((128, 200), (128, 100), (128, 50), (64, 200), (32, 200)):
+        o, dt = timed(lambda: L.solve(planner, ps, rnd[:, :S_p].contiguous(), it, chunk=P))
+        sv_, ss_ = score(o)
+        plain.append({"seeds": S_p, "iters": it, "solved": round(sv_, 4), "seed_success": round(ss_, 4),
+                      "ms": round(dt * 1e3, 2), "plans_per_s": round(P / dt, 1)})
+    learned = []
+    occ_rows = occ[ps.scene_of_problem.long()].contiguous()
+    for S_l in (16, 32):
+        graph = L.ProposalGraph(net, robot, P, S_l, 5, seed=3, out_T=wl.T)
+        graph(ps.q_start, ps.q_goal, ps.goal, occ_rows)                      # warm-up
+        seeds, t_d = timed(lambda: graph(ps.q_start, ps.q_goal, ps.goal, occ_rows).contiguous().clone())
+        graph.check()
+        for it in (25, 50, 100, 200):
+            o, t_p = timed(lambda: L.solve(planner, ps, seeds, it, chunk=P))
+            sv_, ss_ = score(o)
+            total = t_d + t_p
+            learned.append({"samples": S_l, "ddim_steps": 5, "iters": it, "solved": round(sv_, 4),
+                            "seed_success": round(ss_, 4), "ddim_ms": round(t_d * 1e3, 2),
+                            "plan_ms": round(t_p * 1e3, 2), "ms": round(total * 1e3, 2),
+                            "plans_per_s": round(P / total, 1)})
+        del graph, seeds
+    ref = plain[0]
+    match = [r for r in learned if r["solved"] >= ref["solved"]]
+    best = max(match, key=lambda r: r["plans_per_s"]) if match else None
+    out["stress"] = {"problems": P, "plain": plain, "learned": learned,
+                     "matched_success": ({"plain": ref, "learned": best,
+                                          "plans_per_s_ratio": round(best["plans_per_s"] / ref["plans_per_s"], 2)}
+                                         if best else None)}
+    # serving mix: the serving workload's requests, plain vs seeded on arrival
+    n = args.learned_requests
+    cub, grids = SV.serving_scene_pool(64, seed=0)
+    planner.set_scenes(cub, grids)
+    cf, pf = api.device_workload_fns(planner)
+    sw = SV.build_serving_workload(n, cf, pf, n_scenes=64, seed=0)
+    occ_s = L.occupancy(planner, sw.cuboids, L.OCC_GRIDS["clutter"])
+    problems = [(pr.scene, pr.q_start, pr.goal) for pr in sw.problems]
+    budget = 120 * 10 ** 9
+
+    def server(iters, round_iters):
+        sv = SV.Server(sw.robot, budget, max_requests=4096, round_iters=round_iters, opt=I.OptParams(iters=iters))
+        for s_, (c, g) in enumerate(zip(sw.cuboids, sw.grids)):
+            sv.add_scene(s_, c, g)
+        torch.cuda.synchronize()
+        return sv
+
+    sv = server(100, args.serve_round_iters)
+    SV.run_trace(sv, SV.ServingWorkload(sw.robot, sw.cuboids, sw.grids, sw.problems, sw.requests[:64]), None)
+    sat = SV.summarize(SV.run_trace(sv, sw, None))
+    sv.close()
+    rate = 0.5 * sat["plans_per_s"]
+    arr = SV.poisson_arrivals(n, rate, seed=11)
+    sv = server(100, args.serve_round_iters)
+    at_p = SV.summarize(SV.run_trace(sv, sw, arr))
+    sv.close()
+    res_s = {"workload": f"{n} serving requests (S in {{4,16,64,256}}, T in {{32,48,64}}, 64 scenes), plain "
+                         f"100 iterations vs seeded on arrival; offered load = half the plain saturation",
+             "plain": {"saturation": sat, "at_load": at_p}, "offered_plans_per_s": rate}
+    S_l = 16
+    q_s = torch.as_tensor(np.stack([pr.q_start for pr in sw.problems])).to(dev)
+    q_g = torch.as_tensor(np.stack([pr.q_goal for pr in sw.problems])).to(dev)
+    g_s = torch.as_tensor(np.stack([pr.goal for pr in sw.problems])).to(dev)
+    sc_s = torch.as_tensor(np.array([pr.scene for pr in sw.problems])).to(dev).long()
+    graphs = {T_: L.ProposalGraphs(net, robot, (2, 8, 64), S_l, 5, seed=5 + T_, out_T=T_) for T_ in (32, 48, 64)}
+
+    def propose(idx, T_):
+        ix = torch.as_tensor(idx, dtype=torch.long, device=dev)
+        return graphs[T_](q_s[ix], q_g[ix], g_s[ix], occ_s[sc_s[ix]])
+
+    reqs = [(p_, T_) for (p_, _, T_) in sw.requests]
+    res_s["seeded"] = []
+    for it_l in (20, 50):
+        svl = server(it_l, it_l)
+        SV.run_trace_seeded(svl, problems, reqs[:64], None, propose)
+        sat_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, None, propose))
+        svl.close()
+        svl = server(it_l, it_l)
+        at_l = SV.summarize(SV.run_trace_seeded(svl, problems, reqs, arr, propose))
+        svl.close()
+        res_s["seeded"].append({"samples": S_l, "ddim_steps": 5, "iters": it_l, "saturation": sat_l,
+                                "at_load": at_l})
+    for g_ in graphs.values():
+        g_.check()
+    out["serving_mix"] = res_s
+    return out
+
+
 # ---------------------------------------------------------------------------- CPU oracle
 
 def _oracle_problems(spec, n: int, seed_offset: int = 0):
@@ -772,6 +918,8 @@ def main():
         res["serving"] = run_serving(args, rank)
     if rank == 0 and not args.no_learned:
         res["learned"] = run_learned(args)
+        if args.workload == "stress" and not args.no_learned_stress:
+            res["learned_stress"] = run_learned_stress(args, wl)
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(workload_spec(args, args.workload))
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}

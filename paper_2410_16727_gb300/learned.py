@@ -26,6 +26,9 @@ from . import inputs as I
 from . import netspec as NS
 
 OCC_GRID = I.Grid((-0.30, -0.64, -0.14), 0.04, (32, 32, 32))    # same box as the shelf ESDF grid
+# 32^3 occupancy boxes per scene family: the shelf box above; the clutter workspace's
+# 1.28 m cube (same box as the clutter ESDF grid), which also holds the serving pool's scenes
+OCC_GRIDS = {"shelf": OCC_GRID, "clutter": I.Grid((-0.64, -0.64, -0.14), 0.04, (32, 32, 32))}
 RES_SCALE = 4.0    # diffused quantity: RES_SCALE * (normalised trajectory - straight joint path)
 
 
@@ -35,7 +38,7 @@ def _nn(name, *a):
 
 @dataclasses.dataclass
 class ProblemSet:
-    """Problems on shelf scenes (device tensors)."""
+    """Problems on generated scenes (device tensors)."""
     cuboids: list
     grids: list
     scene_of_problem: torch.Tensor    # [P] int32
@@ -44,27 +47,42 @@ class ProblemSet:
     goal: torch.Tensor                # [P][7]
     occ: torch.Tensor                 # [n_scenes][32^3]
     table: B.SceneTable = None        # the scenes' ESDFs on the device
+    T: int = 32                       # horizon the problems are planned at
+    iters: int = 100                  # iterations of the plain method on them
+    kind: str = "shelf"
 
 
-def make_problems(planner: api.Planner, n_scenes: int, per_scene: int, seed: int) -> ProblemSet:
-    spec = I.WORKLOADS["batched"]
-    spec = I.WorkloadSpec("learned", 40 + seed, n_scenes, n_scenes * per_scene, 1, 32, 100, "shelf", spec.grid)
+def make_problems(planner: api.Planner, n_scenes: int, per_scene: int, seed: int, kind: str = "shelf",
+                  T: Optional[int] = None) -> ProblemSet:
+    """per_scene problems on each of n_scenes generated scenes.  shelf: the
+    batched workload's shelf scenes (128^3 ESDF at 1 cm), T = 32, 100
+    iterations; clutter: the stress workload's dense-clutter scenes (200
+    cuboids, 256^3 ESDF at 5 mm), T = 64, 200 iterations.  Each family's
+    random streams are keyed apart from the benchmark workloads' own."""
+    if kind == "shelf":
+        base, cid, T, iters = I.WORKLOADS["batched"], 40 + seed, T or 32, 100
+    elif kind == "clutter":
+        base, cid, T, iters = I.WORKLOADS["stress"], 60 + seed, T or 64, 200
+    else:
+        raise ValueError(kind)
+    spec = I.WorkloadSpec("learned-" + kind, cid, n_scenes, n_scenes * per_scene, 1, T, iters, base.scene, base.grid)
     cub, grids = I.make_scenes(spec)
     planner.set_scenes(cub, grids)
     cf, pf = api.device_workload_fns(planner)
     wl = I.build_workload(spec, cub, grids, cf, pf, S=1)
-    occ = occupancy(planner, cub)
+    occ = occupancy(planner, cub, OCC_GRIDS[kind])
     dev = planner.device
     return ProblemSet(cub, grids, torch.as_tensor(wl.scene_of_problem).to(dev), torch.as_tensor(wl.q_start).to(dev),
-                      torch.as_tensor(wl.q_goal).to(dev), torch.as_tensor(wl.goal).to(dev), occ, planner.table)
+                      torch.as_tensor(wl.q_goal).to(dev), torch.as_tensor(wl.goal).to(dev), occ, planner.table,
+                      T=T, iters=iters, kind=kind)
 
 
-def occupancy(planner: api.Planner, cuboids) -> torch.Tensor:
-    """32^3 occupancy of each scene over the shelf workspace: the ESDF at 4 cm
-    voxels thresholded at 0 (1 inside a cuboid)."""
+def occupancy(planner: api.Planner, cuboids, grid: I.Grid = OCC_GRID) -> torch.Tensor:
+    """32^3 occupancy of each scene over a workspace box (default: the shelf
+    box): the ESDF at 4 cm voxels thresholded at 0 (1 inside a cuboid)."""
     dev = planner.device
     cts = [torch.as_tensor(c).to(dev).reshape(-1, 6) for c in cuboids]
-    esdf = B.scene_build_esdf_batch(cts, [OCC_GRID] * len(cts))
+    esdf = B.scene_build_esdf_batch(cts, [grid] * len(cts))
     phi = torch.stack(esdf).reshape(len(cts), -1).contiguous()
     occ = torch.empty_like(phi)
     _nn("clamp_affine", phi, -1e6, 0.0, 0.0, 1.0, occ, phi.numel())
@@ -122,6 +140,39 @@ def linear_path(qs_n: torch.Tensor, qg_n: torch.Tensor, T: int) -> torch.Tensor:
     return out
 
 
+def resample(x: torch.Tensor, q0: torch.Tensor, T1: int) -> torch.Tensor:
+    """Trajectories x [N][T0][7], whose waypoint k sits at fraction k / T0 of a
+    path that starts at q0 [N][7] (fraction 0), resampled by linear
+    interpolation in time to T1 waypoints at fractions j / T1, j = 1..T1:
+    [N][T1][7].  Two GEMMs against constant interpolation weights (the
+    waypoints' share, then the start's, accumulated)."""
+    N, T0, D = x.shape
+    if T1 == T0:
+        return x
+    key = ("resample", T0, T1, D, str(x.device))
+    W = _AFFINE_CACHE.get(key)
+    if W is None:
+        Wx = np.zeros((T0 * D, T1 * D), np.float32)
+        Wq = np.zeros((D, T1 * D), np.float32)
+        for j in range(1, T1 + 1):
+            u = j * T0 / T1                       # position in input waypoints (the start at 0)
+            k0 = min(int(math.floor(u)), T0)
+            f = u - k0
+            for d in range(D):
+                col = (j - 1) * D + d
+                if k0 == 0:
+                    Wq[d, col] = 1.0 - f
+                else:
+                    Wx[(k0 - 1) * D + d, col] += 1.0 - f
+                if f > 0.0:
+                    Wx[k0 * D + d, col] += f
+        W = _AFFINE_CACHE[key] = (torch.from_numpy(Wx).to(x.device), torch.from_numpy(Wq).to(x.device))
+    out = torch.empty((N, T1, D), dtype=torch.float32, device=x.device)
+    _nn("gemm_f32", 0, 0, N, T1 * D, T0 * D, 1.0, x.contiguous(), T0 * D, W[0], T1 * D, 0.0, out, T1 * D, None)
+    _nn("gemm_f32", 0, 0, N, T1 * D, D, 1.0, q0.contiguous(), D, W[1], T1 * D, 1.0, out, T1 * D, None)
+    return out
+
+
 def to_residual(x_n: torch.Tensor, lin: torch.Tensor) -> torch.Tensor:
     out = torch.empty_like(x_n)
     _nn("axpby", RES_SCALE, x_n.contiguous(), -RES_SCALE, lin.contiguous(), out, x_n.numel())
@@ -170,18 +221,21 @@ class Dataset:
     weight: torch.Tensor   # [M] 1 + alpha * 1(non-linear solution)
 
 
-def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int = 64, iters: int = 100,
+def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int = 64, iters: Optional[int] = None,
                   alpha: float = 4.0, nonlinear_rad: float = 0.3, seed: int = 0, chunk: int = 256,
-                  reverse: bool = True) -> Dataset:
-    """Solve every problem with S random seeds; keep the best successful
-    trajectory of each solved problem.  A solution that leaves the straight
-    start-goal joint line by more than `nonlinear_rad` counts as non-linear
-    and gets weight 1 + alpha (the paper up-weights solutions a linear seed
-    does not reach, Eq. 2).  With reverse, every solution is also added run
-    backwards (App. A.4 swaps start and goal): start = its last waypoint,
-    goal = the original start configuration and its flange pose, waypoints
-    y_{T-1}, ..., y_1, q_start."""
-    T = 32
+                  reverse: bool = True, T_net: int = 32) -> Dataset:
+    """Solve every problem with S random seeds at the problems' horizon (ps.T,
+    ps.iters iterations unless given); keep the best successful trajectory of
+    each solved problem.  A solution that leaves the straight start-goal joint
+    line by more than `nonlinear_rad` counts as non-linear and gets weight
+    1 + alpha (the paper up-weights solutions a linear seed does not reach,
+    Eq. 2).  With reverse, every solution is also added run backwards (App. A.4
+    swaps start and goal): start = its last waypoint, goal = the original start
+    configuration and its flange pose, waypoints y_{T-1}, ..., y_1, q_start.
+    Solutions are resampled to the network's horizon T_net (for T = 64 and
+    T_net = 32: every second waypoint)."""
+    T = ps.T
+    iters = ps.iters if iters is None else iters
     P = ps.q_start.shape[0]
     opt = I.OptParams(iters=iters)
     keeps, trajs = [], []
@@ -213,7 +267,8 @@ def build_dataset(planner: api.Planner, robot: I.Robot, ps: ProblemSet, S: int =
     dev = (traj - lin).abs().amax(dim=(1, 2))
     weight = 1.0 + alpha * (dev > nonlinear_rad).float()
     qs_n, qg_n = normalise(robot, qs.contiguous()), normalise(robot, qg.contiguous())
-    x0 = to_residual(normalise(robot, traj.contiguous()), linear_path(qs_n, qg_n, T))
+    traj = resample(traj.contiguous(), qs.contiguous(), T_net)
+    x0 = to_residual(normalise(robot, traj.contiguous()), linear_path(qs_n, qg_n, T_net))
     return Dataset(x0, qs_n, qg_n, goal.contiguous(), scene.long(), ps.occ, weight.contiguous())
 
 
@@ -299,7 +354,7 @@ def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: flo
 
 
 def _propose_core(net: DN.Denoiser, robot: I.Robot, q_start, q_goal, goal, occ, noise, rows, steps: int,
-                  bf16: bool, check: bool, guide_ctx=None) -> torch.Tensor:
+                  bf16: bool, check: bool, guide_ctx=None, out_T: Optional[int] = None) -> torch.Tensor:
     qs = normalise(robot, q_start.contiguous())
     qg = normalise(robot, q_goal.contiguous())
     lin = linear_path(qs, qg, net.spec.T)[rows.long()].contiguous()
@@ -313,23 +368,29 @@ def _propose_core(net: DN.Denoiser, robot: I.Robot, q_start, q_goal, goal, occ, 
     x = from_residual(r, lin)
     _nn("clamp_affine", x, 1.0, 0.0, -1.0, 1.0, x, x.numel())
     P, S = q_start.shape[0], noise.shape[0] // q_start.shape[0]
-    return normalise(robot, x, inverse=True).view(P, S, net.spec.T, net.spec.D)
+    q = normalise(robot, x, inverse=True)
+    if out_T is not None and out_T != net.spec.T:
+        # the network's horizon resampled to the requested one (the start configuration at fraction 0)
+        q = resample(q.view(P * S, net.spec.T, net.spec.D), q_start[rows.long()], out_T)
+    return q.view(P, S, -1, net.spec.D)
 
 
 def propose_for(net: DN.Denoiser, robot: I.Robot, q_start: torch.Tensor, q_goal: torch.Tensor, goal: torch.Tensor,
-                occ: torch.Tensor, S: int, steps: int = 10, seed: int = 0, bf16: bool = True) -> torch.Tensor:
+                occ: torch.Tensor, S: int, steps: int = 10, seed: int = 0, bf16: bool = True,
+                out_T: Optional[int] = None) -> torch.Tensor:
     """DDIM proposals for P problems given as device tensors (q_start, q_goal,
     goal [P][7], occupancy rows [P][32^3]): S seed trajectories per problem,
     [P][S][T][7] in joint space.  DDIM generates the scaled residual from the
     straight start-goal path, which is added back; the result is clipped to
-    the joint limits like the random seeds, then un-normalised."""
+    the joint limits like the random seeds, then un-normalised, and resampled
+    in time to out_T waypoints when that differs from the network's T."""
     P = q_start.shape[0]
     dev = q_start.device
     g = torch.Generator(device=dev)
     g.manual_seed(1000 + seed)
     noise = torch.randn((P * S, net.spec.T, net.spec.D), device=dev, generator=g)
     rows = torch.arange(P, device=dev, dtype=torch.int32).repeat_interleave(S)
-    return _propose_core(net, robot, q_start, q_goal, goal, occ, noise, rows, steps, bf16, True)
+    return _propose_core(net, robot, q_start, q_goal, goal, occ, noise, rows, steps, bf16, True, out_T=out_T)
 
 
 @dataclasses.dataclass
@@ -411,7 +472,7 @@ class ProposalGraph:
 
     def __init__(self, net: DN.Denoiser, robot: I.Robot, G: int, S: int, steps: int, seed: int = 0,
                  guidance: Optional[Guidance] = None, planner: Optional[api.Planner] = None,
-                 table: Optional[B.SceneTable] = None):
+                 table: Optional[B.SceneTable] = None, out_T: Optional[int] = None):
         dev = net.dev
         s = net.spec
         self.G, self.S, self.net = G, S, net
@@ -427,7 +488,7 @@ class ProposalGraph:
         self.gen.manual_seed(2000 + seed)
         ctx = (planner, table, self.scene, guidance) if guidance is not None else None
         args = (net, robot, self.q_start, self.q_goal, self.goal, self.occ, self.noise, self.rows, steps, True, False,
-                ctx)
+                ctx, out_T)
         side = torch.cuda.Stream()
         side.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(side):                  # warm-up outside the capture (weight caches, constants)
@@ -466,9 +527,8 @@ class ProposalGraphs:
     """Several captured group sizes; a group of g problems replays the
     smallest graph with G >= g (less padded work for small groups)."""
 
-    def __init__(self, net: DN.Denoiser, robot: I.Robot, sizes, S: int, steps: int, seed: int = 0, **guide_kw):
-        self.graphs = [ProposalGraph(net, robot, G, S, steps, seed + i, **guide_kw)
-                       for i, G in enumerate(sorted(sizes))]
+    def __init__(self, net: DN.Denoiser, robot: I.Robot, sizes, S: int, steps: int, seed: int = 0, **kw):
+        self.graphs = [ProposalGraph(net, robot, G, S, steps, seed + i, **kw) for i, G in enumerate(sorted(sizes))]
 
     def __call__(self, q_start, q_goal, goal, occ, scene: Optional[torch.Tensor] = None) -> torch.Tensor:
         g = q_start.shape[0]
@@ -483,9 +543,9 @@ class ProposalGraphs:
 
 def propose(net: DN.Denoiser, robot: I.Robot, ps: ProblemSet, S: int, steps: int = 10, seed: int = 0,
             bf16: bool = True) -> torch.Tensor:
-    """DDIM proposals for every problem of a problem set: [P][S][T][7]."""
+    """DDIM proposals for every problem of a problem set at its horizon: [P][S][ps.T][7]."""
     occ = ps.occ[ps.scene_of_problem.long()]
-    return propose_for(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, S, steps, seed, bf16)
+    return propose_for(net, robot, ps.q_start, ps.q_goal, ps.goal, occ, S, steps, seed, bf16, out_T=ps.T)
 
 
 def diffusion_only(planner: api.Planner, ps: ProblemSet, seeds: torch.Tensor) -> dict:

@@ -49,6 +49,7 @@ class ServingProblem:
     q_start: np.ndarray
     goal: np.ndarray
     seeds: Dict[tuple, np.ndarray]      # (S, T) -> [S][T][7]
+    q_goal: Optional[np.ndarray] = None  # the goal configuration the random seeds interpolate towards
 
 
 @dataclasses.dataclass
@@ -76,7 +77,7 @@ def build_serving_workload(n_requests: int, clearance_fn, pose_fn, n_scenes: int
                           S=1, T=32, robot=robot)
     problems = []
     for p in range(wl.P):
-        problems.append(ServingProblem(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], {}))
+        problems.append(ServingProblem(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], {}, wl.q_goal[p]))
     rng = I._rng(4000 + seed, 0, 0)
     reqs = []
     for i in range(n_requests):
@@ -109,9 +110,13 @@ class Server:
         self._keep: Dict[int, tuple] = {}
 
     def close(self):
+        """Destroy the native server (it waits for its stream) and release the
+        arena at once, so a new server can take the budget before this object
+        is collected."""
         if getattr(self, "h", None) is not None:
             B.server_destroy(self.h)
             self.h = None
+        self.arena = None
 
     def __del__(self):
         self.close()
@@ -268,14 +273,18 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
                      timeout_s: float = 600.0) -> dict:
     """Replay requests whose seeds are proposed on the GPU when they arrive
     (the learned seeding): problems[p] = (scene_id, q_start [7], goal [7]);
-    requests[i] = problem index.  Arrived requests are grouped (up to
-    max_group), propose(problem indices) enqueues their seeds [g][S][T][7] on
-    the current stream (overlapping the server's own stream), the seeds are
-    copied to pinned host memory, and each request is submitted once its copy
-    has landed.  Latency runs from the arrival to the server's completion, so
+    requests[i] = problem index, or (problem index, horizon T) for a mix of
+    horizons.  Arrived requests are grouped (up to max_group; with horizons,
+    the arrived requests of the oldest one's horizon), propose(problem indices)
+    -- propose(problem indices, T) with horizons -- enqueues their seeds
+    [g][S][T][7] on the current stream (overlapping the server's own stream),
+    the seeds are copied to pinned host memory, and each request is submitted
+    once its copy has landed.  Latency runs from the arrival to the server's completion, so
     it includes the proposal.  Pinned buffers come from pools (allocating
     pinned memory can synchronise the device)."""
     n = len(requests)
+    mixed = len(requests) > 0 and isinstance(requests[0], tuple)
+    prob = (lambda k: requests[k][0]) if mixed else (lambda k: requests[k])
     arr = np.zeros(n) if arrivals is None else np.asarray(arrivals, np.float64)
     pin = {p: (torch.as_tensor(np.asarray(q, np.float32)).pin_memory(),
                torch.as_tensor(np.asarray(g, np.float32)).pin_memory()) for p, (_, q, g) in enumerate(problems)}
@@ -298,8 +307,15 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
                 t_first = time.monotonic()
             i += 1
         if waiting and len(props) < 2:
-            grp, waiting = waiting[:max_group], waiting[max_group:]
-            seeds = propose([requests[k] for k in grp])
+            if mixed:
+                Tg = requests[waiting[0]][1]
+                grp = [k for k in waiting if requests[k][1] == Tg][:max_group]
+                taken = set(grp)
+                waiting = [k for k in waiting if k not in taken]
+                seeds = propose([prob(k) for k in grp], Tg)
+            else:
+                grp, waiting = waiting[:max_group], waiting[max_group:]
+                seeds = propose([prob(k) for k in grp])
             key = tuple(seeds.shape[1:])
             lst = free_blocks.setdefault(key, [])
             block = lst.pop() if lst else torch.empty((max_group,) + key, dtype=torch.float32).pin_memory()
@@ -312,7 +328,7 @@ def run_trace_seeded(server: Server, problems: Sequence[tuple], requests: Sequen
             refs[id(block)] = [block, len(grp)]
             S, T = int(block.shape[1]), int(block.shape[2])
             for j, k in enumerate(grp):
-                p = requests[k]
+                p = prob(k)
                 lo = free_out.setdefault((S, T), [])
                 out = lo.pop() if lo else alloc_outputs(S, T)
                 ins = dict(q=pin[p][0], g=pin[p][1], s=block[j])
