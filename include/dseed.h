@@ -597,8 +597,9 @@ int dseed_nn_upsample2_bf16(const void *x_dev, int N, int L, int C, void *y_dev,
  * provide the workspace dseed_plan_batch asks for.
  *
  * dseed_plan_batch_static does the same work as dseed_plan_batch (same
- * kernels, same results) but keeps its scratch (the L-BFGS history and the
- * per-problem best-seed keys) in one array of DSEED_STATIC_SCRATCH_BYTES
+ * kernels, same results) but keeps its scratch (the L-BFGS history, for
+ * T > 32 the search directions, and the per-problem best-seed keys) in one
+ * array of DSEED_STATIC_SCRATCH_BYTES
  * bytes that lives in the library itself, as a file-scope device variable.
  * The caller still passes every input and output buffer.  The call never
  * allocates: no cudaMalloc, no cudaFree, no allocating library routine.

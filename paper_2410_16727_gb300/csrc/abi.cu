@@ -169,7 +169,7 @@ dseed::KLbfgsPtrs lbfgs_ptrs(void *base, const DseedLbfgsLayout &l) {
 
 // Plan workspace: history s [B][m][n], history y [B][m][n], best keys [P].
 struct PlanLayout {
-    size_t s, y, key, total;
+    size_t s, y, d, key, total;
 };
 
 PlanLayout plan_layout(const DseedPlanDesc *d) {
@@ -178,7 +178,8 @@ PlanLayout plan_layout(const DseedPlanDesc *d) {
     PlanLayout l;
     l.s = 0;
     l.y = align256(sizeof(float) * B * m * n);
-    l.key = l.y + align256(sizeof(float) * B * m * n);
+    l.d = l.y + align256(sizeof(float) * B * m * n);                 // search directions (T > 32)
+    l.key = l.d + (d->T > 32 ? align256(sizeof(float) * B * n) : 0);
     l.total = l.key + align256(sizeof(unsigned long long) * std::max(d->P, 1));
     return l;
 }
@@ -550,7 +551,7 @@ int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const D
     char *w = static_cast<char *>(workspace_dev);
     return cuda_status(dseed::launch_plan(robot->k, make_cost(desc->cost), make_opt(desc->opt), make_batch(desc, pr),
                                           seeds_dev, reinterpret_cast<float *>(w + l.s),
-                                          reinterpret_cast<float *>(w + l.y),
+                                          reinterpret_cast<float *>(w + l.y), reinterpret_cast<float *>(w + l.d),
                                           reinterpret_cast<unsigned long long *>(w + l.key), traj_dev, cost_dev,
                                           success_dev, metrics_dev, best_dev, stream),
                        "plan");
@@ -643,7 +644,7 @@ extern "C" int dseed_plan_batch_static(const DseedRobot *robot, const DseedPlanD
     // launch_plan resets the best-seed keys; the history is written before it is read
     return cuda_status(dseed::launch_plan(robot->k, make_cost(desc->cost), make_opt(desc->opt), make_batch(desc, pr),
                                           seeds_dev, reinterpret_cast<float *>(w + l.s),
-                                          reinterpret_cast<float *>(w + l.y),
+                                          reinterpret_cast<float *>(w + l.y), reinterpret_cast<float *>(w + l.d),
                                           reinterpret_cast<unsigned long long *>(w + l.key), traj_dev, cost_dev,
                                           success_dev, metrics_dev, best_dev, stream),
                        "plan (static scratch)");

@@ -455,7 +455,8 @@ __device__ __forceinline__ void waypoint_terms(const KRobot &rb, const KCost &kc
 //                      before they are written, the lanes' frame-loop scratch (at least
 //                      21 * 32 floats)
 //   gs [T * 7]         gradient of the trial point
-//   xa, ga, dd [T * 7] accepted point, its gradient, current search direction (optimiser)
+//   xa, ga, dd [T * 7] accepted point, its gradient, current search direction (optimiser;
+//                      the direction may live in global memory instead, see carve)
 //   v [32]             L-BFGS scalars: rho per slot [0, 8), y^T y of the newest pair [8],
 //                      alpha_i of the two-loop [16, 24)
 __host__ __device__ constexpr int es_floats(int T) {
@@ -473,15 +474,26 @@ __host__ __device__ constexpr int warp_smem_floats(int T, bool self) {
     return warp_smem_floats(T) + (self ? kSelfFloats * 32 : 0);
 }
 
-__device__ __forceinline__ WarpSmem carve(float *base, int T) {
+// Per-warp shared floats of a slice whose search direction lives elsewhere
+// (global memory), with the self-collision scratch when SELF.
+__host__ __device__ constexpr int warp_smem_floats_nodd(int T, bool self) { return warp_smem_floats(T, self) - 7 * T; }
+
+// Slice of one warp.  dd_global: the search direction is kept in global
+// memory at that address instead of the slice (the slice then omits it).
+__device__ __forceinline__ WarpSmem carve(float *base, int T, float *dd_global = nullptr) {
     WarpSmem w;
     w.xs = base;
     w.es = w.xs + (T + kPad) * 7;
     w.gs = w.es + es_floats(T);
     w.xa = w.gs + T * 7;
     w.ga = w.xa + T * 7;
-    w.dd = w.ga + T * 7;
-    w.v = w.dd + T * 7;
+    if (dd_global) {
+        w.dd = dd_global;
+        w.v = w.ga + T * 7;
+    } else {
+        w.dd = w.ga + T * 7;
+        w.v = w.dd + T * 7;
+    }
     w.self = w.v + 32;
     return w;
 }

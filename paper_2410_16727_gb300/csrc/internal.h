@@ -75,7 +75,7 @@ int launch_lbfgs_init(int B, int n, const float *x0, const KLbfgsPtrs &p, int m,
 int launch_lbfgs_step(const KOpt &ko, int B, int T, const float *f_trial, const float *g_trial,
                       const KLbfgsPtrs &p, cudaStream_t st);
 int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch &kb,
-                const float *seeds, float *hist_s, float *hist_y, unsigned long long *best_key,
+                const float *seeds, float *hist_s, float *hist_y, float *dirs, unsigned long long *best_key,
                 float *traj, float *cost, uint8_t *success, float *metrics, int *best, cudaStream_t st);
 
 }  // namespace dseed

@@ -28,8 +28,15 @@ constexpr int kPlanWarps = DSEED_PLAN_WARPS;    // warps per block of the standa
 // pack it more finely (T = 64: 14 resident warps instead of 12), and the
 // minimum-block counts below leave each variant at least the registers it uses.
 __host__ __device__ constexpr int plan_warps(int tpl, bool self) { return tpl == 1 && !self ? kPlanWarps : 2; }
+// With several waypoints per lane (and no self term) the search direction lives
+// in the workspace instead of shared memory: it is read once per iteration, and
+// the 7 T floats it frees let more warps stay resident (T = 64: 16 instead of 14).
+__host__ __device__ constexpr bool plan_dd_global(int tpl, bool self) { return tpl >= 2 && !self; }
 __host__ __device__ constexpr int plan_min_blocks(int tpl, bool self) {
-    return tpl == 1 && !self ? DSEED_PLAN_MINBLOCKS : self ? (tpl == 1 ? 5 : tpl == 2 ? 3 : 2) : (tpl == 2 ? 7 : 3);
+    return tpl == 1 && !self ? DSEED_PLAN_MINBLOCKS : self ? (tpl == 1 ? 5 : tpl == 2 ? 3 : 2) : (tpl == 2 ? 8 : 4);
+}
+__host__ __device__ constexpr int plan_warp_floats(int T, int tpl, bool self) {
+    return plan_dd_global(tpl, self) ? warp_smem_floats_nodd(T, self) : warp_smem_floats(T, self);
 }
 
 // ---------------------------------------------------------------- standalone L-BFGS
@@ -119,8 +126,8 @@ template <int TPL, bool SELF, bool SWEEP>
 __global__ void __launch_bounds__(plan_warps(TPL, SELF) * 32, plan_min_blocks(TPL, SELF))
     k_plan(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
            const __grid_constant__ KBatch kb, const float *seeds, float *__restrict__ hist_s,
-           float *__restrict__ hist_y, unsigned long long *__restrict__ best_key, float *traj,
-           float *__restrict__ cost, uint8_t *__restrict__ success, float *__restrict__ metrics) {
+           float *__restrict__ hist_y, float *__restrict__ dirs, unsigned long long *__restrict__ best_key,
+           float *traj, float *__restrict__ cost, uint8_t *__restrict__ success, float *__restrict__ metrics) {
     constexpr int NPL = 7 * TPL;
     extern __shared__ float smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -129,7 +136,8 @@ __global__ void __launch_bounds__(plan_warps(TPL, SELF) * 32, plan_min_blocks(TP
     if (b >= B) return;
     const int T = kb.T, n = 7 * T, m = ko.m;
     const int p = (int)(b / kb.S);
-    WarpSmem ws = carve(smem + wid * warp_smem_floats(T, SELF), T);
+    constexpr bool kDdGlobal = plan_dd_global(TPL, SELF);
+    WarpSmem ws = carve(smem + wid * plan_warp_floats(T, TPL, SELF), T, kDdGlobal ? dirs + (size_t)b * n : nullptr);
     float *xt = ws.xs + kPad * 7;
     const int si = kb.scene_of_problem[p];
     const bool in_table = si >= 0 && si < kb.n_scenes;
@@ -197,6 +205,9 @@ __global__ void k_best(int P, const unsigned long long *__restrict__ key, int *_
 static size_t plan_smem_bytes(int T, bool self = false, int warps = kPlanWarps) {
     return (size_t)warps * warp_smem_floats(T, self) * sizeof(float);
 }
+static size_t fused_plan_smem_bytes(int T, int tpl, bool self, int warps) {
+    return (size_t)warps * plan_warp_floats(T, tpl, self) * sizeof(float);
+}
 
 template <typename K>
 static int set_smem(K kern, size_t smem) {
@@ -229,7 +240,7 @@ int launch_lbfgs_step(const KOpt &ko, int B, int T, const float *f_trial, const 
 }
 
 int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch &kb, const float *seeds,
-                float *hist_s, float *hist_y, unsigned long long *best_key, float *traj, float *cost,
+                float *hist_s, float *hist_y, float *dirs, unsigned long long *best_key, float *traj, float *cost,
                 uint8_t *success, float *metrics, int *best, cudaStream_t st) {
     if (kb.P == 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(best_key, 0xff, sizeof(unsigned long long) * kb.P, st);
@@ -239,12 +250,12 @@ int launch_plan(const KRobot &rb, const KCost &kc, const KOpt &ko, const KBatch 
     const int tpl = kb.T <= 32 ? 1 : kb.T <= 64 ? 2 : 4;
     const int warps = self ? plan_warps(tpl, true) : plan_warps(tpl, false);
     const unsigned blocks = (unsigned)((B + warps - 1) / warps);
-    const size_t smem = plan_smem_bytes(kb.T, self, warps);
+    const size_t smem = fused_plan_smem_bytes(kb.T, tpl, self, warps);
     auto go = [&](auto kern) {
         int r = set_smem(kern, smem);
         if (r) return r;
-        kern<<<blocks, warps * 32, smem, st>>>(rb, kc, ko, kb, seeds, hist_s, hist_y, best_key, traj, cost, success,
-                                               metrics);
+        kern<<<blocks, warps * 32, smem, st>>>(rb, kc, ko, kb, seeds, hist_s, hist_y, dirs, best_key, traj, cost,
+                                               success, metrics);
         return (int)cudaGetLastError();
     };
     // variants: waypoints per lane x self-collision term x swept check
