@@ -21,6 +21,18 @@
 // w reading TMEM lanes 32 (w % 4) .. +31 and column part (w - 2) / 4.  Every wait is
 // bounded (2 s); one that gives up sets *err and the CTA still releases its
 // tensor memory.
+//
+// Wide outputs (128 and 256 channels) run in clusters of two CTAs that share the
+// weight tile of every stage: each CTA loads one half of it with a multicast
+// TMA copy that lands in both CTAs' shared memory, so the pair reads the weight
+// bytes from L2 once (the weights are most of a wide layer's operand bytes).
+// Each SM still takes in the whole tile, and that intake, not L2, bounds the
+// wide layers: the multicast halves their L2 reads (which the optimiser kernels
+// sharing L2 in a serving loop feel) without changing their own time.  A stage may then be refilled only
+// once both CTAs' MMAs have read it: each MMA commit arrives on the stage's
+// empty barrier in both CTAs.  The two CTAs walk the same number of tiles (an
+// odd last tile is paired with a tile past the end, whose rows are read as the
+// TMA fill value and never stored).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -43,7 +55,7 @@ constexpr unsigned long long kWaitNs = 2000000000ull;
 enum { kEpiF32 = 0, kEpiBF16 = 1, kEpiGN = 2 };
 
 struct TcParams {
-    CUtensorMap a0, a1, w;
+    CUtensorMap a0, a1, w, w_half;    // w_half: box of half the output rows (cluster multicast)
     int M, L, taps, pad, c0_blocks, c_blocks;
     int cout, rows_per_sample;
     float gn_eps;
@@ -99,6 +111,27 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, u
         : "memory");
 }
 
+// The same copy multicast to the CTAs of cta_mask: the data lands at the same
+// shared-memory offset in each, and each one's mbarrier at bar's offset counts it.
+__device__ __forceinline__ void tma_load_3d_mc(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y, int z,
+                                               uint16_t cta_mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1, {%2, "
+        "%3, %4}], [%5], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar)), "h"(cta_mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -128,6 +161,15 @@ __device__ __forceinline__ void umma_bf16(uint32_t tmem_d, uint64_t adesc, uint6
 
 __device__ __forceinline__ void umma_commit(uint64_t *bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// Arrive on the mbarrier at bar's offset in every CTA of cta_mask once this
+// thread's prior MMAs have completed.
+__device__ __forceinline__ void umma_commit_mc(uint64_t *bar, uint16_t cta_mask) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::
+                     "r"(smem_u32(bar)),
+                 "h"(cta_mask)
                  : "memory");
 }
 
@@ -385,7 +427,7 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int COUT, int STAGES, int MODE>
+template <int COUT, int STAGES, int MODE, int CL>
 __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(const __grid_constant__ TcParams p) {
     constexpr int A_BYTES = kTileM * kBlockK * 2;
     constexpr int B_BYTES = COUT * kBlockK * 2;
@@ -394,6 +436,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     constexpr uint32_t IDESC = bf16_idesc(kTileM, COUT);
     constexpr int kEpiWarps = EpiShape<COUT>::EW;
     static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= 256, "MMA N");
+    static_assert(CL == 1 || (CL == 2 && COUT >= 128), "clusters of two share wide weight tiles");
+    constexpr uint16_t kPair = 0x3;
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -405,11 +449,16 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = p.taps * p.c_blocks;
     const int n_tiles = (p.M + kTileM - 1) / kTileM;
+    // work units: single tiles, or with clusters pairs of adjacent tiles, this CTA
+    // taking tile CL u + rank of unit u (past the end for the odd last unit)
+    const int crank = CL > 1 ? (int)cluster_rank() : 0;
+    const int n_units = (n_tiles + CL - 1) / CL;
+    const int unit0 = blockIdx.x / CL, unit_step = gridDim.x / CL;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full_bar[s], 1);
-            mbar_init(&empty_bar[s], 1);
+            mbar_init(&empty_bar[s], CL);           // every CTA of the cluster reads the stage
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accf_bar[b], 1);
@@ -429,6 +478,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();               // the partner's barriers exist before any multicast
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
     volatile int *fail = &s_fail;
@@ -437,7 +487,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
         if (lane == 0) {
             // producer
             int g = 0;
-            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x) {
+            for (int u = unit0; u < n_units && !*fail; u += unit_step) {
+                const int tile = CL * u + crank;
                 const int sample0 = tile * kTileM / p.L;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int s = g % STAGES;
@@ -453,7 +504,11 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
                         tma_load_3d(sa, &p.a0, &full_bar[s], cblk * kBlockK, tap - p.pad, sample0);
                     else
                         tma_load_3d(sa, &p.a1, &full_bar[s], (cblk - p.c0_blocks) * kBlockK, tap - p.pad, sample0);
-                    tma_load_3d(sa + A_BYTES, &p.w, &full_bar[s], cblk * kBlockK, tap, 0);
+                    if (CL > 1)
+                        tma_load_3d_mc(sa + A_BYTES + crank * (B_BYTES / 2), &p.w_half, &full_bar[s],
+                                       cblk * kBlockK, tap, crank * (COUT / 2), kPair);
+                    else
+                        tma_load_3d(sa + A_BYTES, &p.w, &full_bar[s], cblk * kBlockK, tap, 0);
                 }
             }
             s_issued = g;
@@ -462,7 +517,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
         if (lane == 0) {
             // MMA issuer
             int g = 0, it = 0;
-            for (int tile = blockIdx.x; tile < n_tiles && !*fail; tile += gridDim.x, ++it) {
+            for (int u = unit0; u < n_units && !*fail; u += unit_step, ++it) {
                 const int b = it & 1;
                 if (it >= 2 && !mbar_wait(&acce_bar[b], ((it >> 1) - 1) & 1)) {
                     record_failure(p.err, 4);
@@ -483,7 +538,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
 #pragma unroll
                     for (int k = 0; k < kBlockK / 16; ++k)
                         umma_bf16(d, sw128_desc(a + 32 * k), sw128_desc(bb + 32 * k), IDESC, (kb | k) != 0);
-                    umma_commit(&empty_bar[s]);
+                    if (CL > 1) umma_commit_mc(&empty_bar[s], kPair);
+                    else umma_commit(&empty_bar[s]);
                 }
                 umma_commit(&accf_bar[b]);     // arrives once this tile's MMAs have completed
             }
@@ -499,7 +555,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // epilogue warps only
         int it = 0;
-        for (int tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+        for (int u = unit0; u < n_units; u += unit_step, ++it) {
+            const int tile = CL * u + crank;
             const int b = it & 1;
             if (!mbar_wait(&accf_bar[b], (it >> 1) & 1)) {
                 record_failure(p.err, 3);
@@ -522,6 +579,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     }
     tc_fence_before();
     __syncthreads();
+    if (CL > 1) cluster_sync_all();               // neither CTA leaves while the other may still reach it
     tc_fence_after();
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
@@ -559,26 +617,59 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int COUT, int STAGES, int MODE>
+template <int COUT, int STAGES, int MODE, int CL>
 int launch_tc(const TcParams &p, cudaStream_t st) {
     constexpr int smem = STAGES * (kTileM + COUT) * kBlockK * 2 + 1024;
+    constexpr int threads = 32 * (2 + EpiShape<COUT>::EW);
+    auto kern = k_conv_tc<COUT, STAGES, MODE, CL>;
     static bool configured = false;       // the attribute is per function; setting it twice is harmless
+    static int max_units = 0;             // work units (CTAs, or clusters) resident at once
     if (!configured) {
-        const cudaError_t e =
-            cudaFuncSetAttribute(k_conv_tc<COUT, STAGES, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return (int)e;
-        configured = true;
-    }
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
+        max_units = sms;
+        if (CL > 1) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr;
+            attr.id = cudaLaunchAttributeClusterDimension;
+            attr.val.clusterDim.x = CL;
+            attr.val.clusterDim.y = 1;
+            attr.val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)(CL * (sms / CL)));
+            cfg.blockDim = dim3(threads);
+            cfg.dynamicSmemBytes = smem;
+            cfg.attrs = &attr;
+            cfg.numAttrs = 1;
+            int clusters = 0;
+            e = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg);
+            if (e != cudaSuccess) return (int)e;
+            max_units = clusters > 0 ? clusters : 1;
+        }
+        configured = true;
     }
     const int tiles = (p.M + kTileM - 1) / kTileM;
-    const unsigned grid = (unsigned)(tiles < sms ? tiles : sms);
-    k_conv_tc<COUT, STAGES, MODE><<<grid, 32 * (2 + EpiShape<COUT>::EW), smem, st>>>(p);
-    return (int)cudaGetLastError();
+    const int units = (tiles + CL - 1) / CL;
+    const unsigned grid = (unsigned)(CL * (units < max_units ? units : max_units));
+    if (CL == 1) {
+        kern<<<grid, threads, smem, st>>>(p);
+        return (int)cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = CL;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return (int)cudaLaunchKernelEx(&cfg, kern, p);
 }
 
 template <int MODE>
@@ -586,10 +677,10 @@ int launch_mode(int cout_pad, const TcParams &p, cudaStream_t st) {
     switch (cout_pad) {
         case 16:
             if constexpr (MODE == kEpiGN) return (int)cudaErrorInvalidValue;
-            else return launch_tc<16, 8, MODE>(p, st);
-        case 64: return launch_tc<64, 8, MODE>(p, st);
-        case 128: return launch_tc<128, 6, MODE>(p, st);
-        case 256: return launch_tc<256, 4, MODE>(p, st);
+            else return launch_tc<16, 8, MODE, 1>(p, st);
+        case 64: return launch_tc<64, 8, MODE, 1>(p, st);
+        case 128: return launch_tc<128, 6, MODE, 2>(p, st);
+        case 256: return launch_tc<256, 4, MODE, 2>(p, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
@@ -616,6 +707,10 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
         p.a1 = p.a0;
     }
     if (!make_map(&p.w, d.w_dev, (uint64_t)cin, (uint64_t)d.taps, (uint64_t)d.cout_pad, 1u, (uint32_t)d.cout_pad))
+        return -1;
+    if (d.cout_pad >= 128 &&
+        !make_map(&p.w_half, d.w_dev, (uint64_t)cin, (uint64_t)d.taps, (uint64_t)d.cout_pad, 1u,
+                  (uint32_t)(d.cout_pad / 2)))
         return -1;
     p.M = d.n_samples * d.L;
     p.L = d.L;

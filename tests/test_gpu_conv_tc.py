@@ -59,7 +59,9 @@ def test_plain_gemm(gpu_lib, M, K, cout, cout_pad):
 
 
 @pytest.mark.parametrize("N,L,C0,C1,k,cout", [(9, 32, 64, 0, 5, 64), (20, 16, 128, 0, 5, 128), (33, 8, 256, 256, 5, 256),
-                                              (5, 16, 128, 128, 3, 128), (7, 32, 64, 0, 1, 256)])
+                                              (5, 16, 128, 128, 3, 128), (7, 32, 64, 0, 1, 256),
+                                              # wide outputs run in CTA pairs: several units per CTA, odd tile count
+                                              (4001, 8, 64, 0, 3, 256), (4001, 16, 128, 0, 3, 128)])
 def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout):
     rng = np.random.default_rng(N * L + C0)
     pad = k // 2
