@@ -51,7 +51,20 @@ HBM_BYTES_PER_ST_NO_REUSE = 50 * 8 * 4 + 56
 # and the raw figures are in profiles/k_plan_<workload>.md.
 KERNEL_SOURCES = ("paper_2410_16727_gb300/csrc/device.cuh", "paper_2410_16727_gb300/csrc/kernels_plan.cu",
                   "paper_2410_16727_gb300/csrc/internal.h")
-NCU_COUNTERS = {}
+NCU_COUNTERS = {
+    # k_plan<2,0,0>, 128 of the 1024 stress problems (all 16 scenes), 200 iterations:
+    # 2483.64 MB read + 2392.08 MB written over 128*128*64*200 evaluations; L2 hit 97.58%
+    "stress": {"dram_bytes_per_st": (2483.641e6 + 2392.077e6) / (128 * 128 * 64 * 200), "l2_hit_pct": 97.58,
+               "kernel_hash": "496efaee5e6d6c43",
+               "capture": "ncu dram__bytes_read/write.sum, lts__t_sector_hit_rate.pct of one k_plan launch, "
+                          "128 stress problems, scaled by evaluations (profiles/k_plan_stress.md)"},
+    # k_plan<1,0,0>, the full 256-problem batched launch: 369.81 MB read + 69.39 MB written;
+    # L2 hit rate 98.38% from the 64-problem launch
+    "batched": {"dram_bytes_per_st": (369.805e6 + 69.388e6) / (256 * 64 * 32 * 100), "l2_hit_pct": 98.38,
+                "kernel_hash": "496efaee5e6d6c43",
+                "capture": "ncu dram__bytes_read/write.sum of the full batched k_plan launch, "
+                           "lts__t_sector_hit_rate.pct of a 64-problem launch (profiles/k_plan_batched.md)"},
+}
 
 
 def kernel_hash() -> str:
