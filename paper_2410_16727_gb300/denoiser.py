@@ -514,9 +514,34 @@ class Denoiser:
                 pk[name + ".r.b"] = f32(name + ".r.b")
             for t in ("c1.b", "c2.b", "g1.w", "g1.b", "g2.w", "g2.b"):
                 pk[name + "." + t] = f32(name + "." + t)
-        for name in ("down1", "down2", "up2", "up1", "fin.c"):
+        for name in ("fin.c",):
             pk[name] = packed(name)
             pk[name + ".b"] = f32(name + ".b")
+        for name in ("down1", "down2"):
+            # stride-2, 3-tap convolution as a 2-tap one over row pairs [x(2o), x(2o+1)]:
+            # tap 0 (the pair o - 1) carries w0 on its second row, tap 1 (pair o) w1, w2
+            co, _, ci = self.offsets[name + ".w"][1]
+            w = self.P(name + ".w").view(co, 3, ci)
+            w2 = torch.zeros((co, 2, 2 * ci), dtype=torch.float32, device=self.dev)
+            w2[:, 0, ci:] = w[:, 0]
+            w2[:, 1, :ci] = w[:, 1]
+            w2[:, 1, ci:] = w[:, 2]
+            pk[name + ".s2"] = w2.to(torch.bfloat16).reshape(co, 4 * ci).contiguous()
+            pk[name + ".b"] = f32(name + ".b")
+        for name in ("up2", "up1"):
+            # nearest x2 upsampling then a 3-tap convolution, as one 3-tap convolution of
+            # the input with 2 C outputs: channels [0, C) are output row 2m (taps w0,
+            # w1 + w2, 0), channels [C, 2C) output row 2m + 1 (taps 0, w0 + w1, w2)
+            co, _, ci = self.offsets[name + ".w"][1]
+            w = self.P(name + ".w").view(co, 3, ci)
+            wu = torch.zeros((2 * co, 3, ci), dtype=torch.float32, device=self.dev)
+            wu[:co, 0] = w[:, 0]
+            wu[:co, 1] = w[:, 1] + w[:, 2]
+            wu[co:, 1] = w[:, 0] + w[:, 1]
+            wu[co:, 2] = w[:, 2]
+            pk[name + ".u2"] = wu.to(torch.bfloat16).reshape(2 * co, 3 * ci).contiguous()
+            b = f32(name + ".b")
+            pk[name + ".u2.b"] = torch.cat([b, b]).contiguous()
         # every block's FiLM linear stacked: rows [sum 2 cout], columns split into the
         # time-embedding part and the problem/occupancy part of the condition
         ft_rows = sum(2 * co for _, _, co in NS.res_blocks(s))
@@ -572,28 +597,23 @@ class Denoiser:
                   res=r, **gn)
         return out
 
-    def _tc_conv(self, W, x, N, L, name, k, pad, cout):
-        y = torch.empty((N, L, cout), dtype=torch.bfloat16, device=self.dev)
-        cin = x.shape[-1]
-        B.conv_tc(x, W[name].view(cout, k, cin), y, n_samples=N, L=L, taps=k, pad=pad, cout=cout,
-                  bias=W[name + ".b"], epilogue=B.EPI_BF16, err=self._tc_err)
-        return y
-
     def _tc_down(self, W, x, N, L, name, cout):
-        """Stride-2 convolution (k = 3, pad 1): BF16 im2col rows, then one plain GEMM."""
+        """Stride-2 convolution (k = 3, pad 1) as a 2-tap convolution of the
+        input's row pairs (the input viewed as [N][L/2][2 C]): no im2col buffer."""
         cin = x.shape[-1]
         Lo = L // 2
-        cols = torch.empty((N * Lo, 3 * cin), dtype=torch.bfloat16, device=self.dev)
-        _nn("im2col1d_bf16", x, N, L, cin, 3, 2, 1, Lo, 3 * cin, cols)
         y = torch.empty((N, Lo, cout), dtype=torch.bfloat16, device=self.dev)
-        B.conv_tc(cols, W[name], y, n_samples=N * Lo, L=1, cout=cout, bias=W[name + ".b"], epilogue=B.EPI_BF16,
-                  err=self._tc_err)
+        B.conv_tc(x.view(N, Lo, 2 * cin), W[name + ".s2"], y, n_samples=N, L=Lo, taps=2, pad=1, cout=cout,
+                  bias=W[name + ".b"], epilogue=B.EPI_BF16, err=self._tc_err)
         return y, Lo
 
-    def _tc_up(self, x, N, L):
-        C = x.shape[-1]
-        y = torch.empty((N, 2 * L, C), dtype=torch.bfloat16, device=self.dev)
-        _nn("upsample2_bf16", x, N, L, C, y)
+    def _tc_upconv(self, W, x, N, L, name, cout):
+        """Nearest x2 upsampling followed by a 3-tap convolution, as one 3-tap
+        convolution of x with 2 cout outputs whose halves are the even and odd
+        output rows ([N][L][2 cout] is the memory of [N][2 L][cout])."""
+        y = torch.empty((N, 2 * L, cout), dtype=torch.bfloat16, device=self.dev)
+        B.conv_tc(x, W[name + ".u2"], y.view(N, L, 2 * cout), n_samples=N, L=L, taps=3, pad=1, cout=2 * cout,
+                  bias=W[name + ".u2.b"], epilogue=B.EPI_BF16, err=self._tc_err)
         return y
 
     def unet_tc(self, x, N, film: torch.Tensor, rows: torch.Tensor,
@@ -627,10 +647,10 @@ class Denoiser:
         h = blk([s3], L3, "mid", c3, c3)
         h = blk([h, s3], L3, "u2a", 2 * c3, c2)
         h = blk([h], L3, "u2b", c2, c2)
-        h = self._tc_conv(W, self._tc_up(h, N, L3), N, L2, "up2", 3, 1, c2)
+        h = self._tc_upconv(W, h, N, L3, "up2", c2)
         h = blk([h, s2], L2, "u1a", 2 * c2, c1)
         h = blk([h], L2, "u1b", c1, c1)
-        h = self._tc_conv(W, self._tc_up(h, N, L2), N, T, "up1", 3, 1, c1)
+        h = self._tc_upconv(W, h, N, L2, "up1", c1)
         g = torch.empty((N, T, c1), dtype=torch.bfloat16, device=self.dev)
         B.conv_tc(h, W["fin.c"].view(c1, s.kernel, c1), g, n_samples=N, L=T, taps=s.kernel, pad=s.kernel // 2,
                   cout=c1, bias=W["fin.c.b"], epilogue=B.EPI_GN, rows_per_sample=T, gn_eps=s.gn_eps,

@@ -58,13 +58,15 @@ def test_plain_gemm(gpu_lib, M, K, cout, cout_pad):
     assert np.all(_f64(out16)[:, cout:] == 0)            # columns past cout untouched
 
 
-@pytest.mark.parametrize("N,L,C0,C1,k,cout", [(9, 32, 64, 0, 5, 64), (20, 16, 128, 0, 5, 128), (33, 8, 256, 256, 5, 256),
-                                              (5, 16, 128, 128, 3, 128), (7, 32, 64, 0, 1, 256),
-                                              # wide outputs run in CTA pairs: several units per CTA, odd tile count
-                                              (4001, 8, 64, 0, 3, 256), (4001, 16, 128, 0, 3, 128)])
-def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout):
-    rng = np.random.default_rng(N * L + C0)
-    pad = k // 2
+@pytest.mark.parametrize("N,L,C0,C1,k,cout,pad", [
+    (9, 32, 64, 0, 5, 64, 2), (20, 16, 128, 0, 5, 128, 2), (33, 8, 256, 256, 5, 256, 2),
+    (5, 16, 128, 128, 3, 128, 1), (7, 32, 64, 0, 1, 256, 0),
+    # wide outputs run in CTA pairs: several units per CTA, odd tile count
+    (4001, 8, 64, 0, 3, 256, 1), (4001, 16, 128, 0, 3, 128, 1),
+    # two taps over row pairs (the stride-2 convolution), one-sided padding
+    (301, 16, 128, 0, 2, 64, 1), (77, 8, 256, 0, 2, 128, 1), (50, 32, 64, 0, 3, 64, 0), (50, 16, 64, 0, 3, 64, 2)])
+def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout, pad):
+    rng = np.random.default_rng(N * L + C0 + k)
     x0 = _bf(rng.normal(size=(N, L, C0)))
     x1 = _bf(rng.normal(size=(N, L, C1))) if C1 else None
     cin = C0 + C1
