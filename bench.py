@@ -297,19 +297,22 @@ def measure_plain(args, spec: I.WorkloadSpec, rank: int, world: int, with_e2e: b
             e2e_step()
         torch.cuda.synchronize()
         e_ms = []
-        for _ in range(max(2, args.steps)):
-            flush.zero_()
-            torch.cuda.synchronize()
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            e2e_step()
-            b.record(stream)
-            b.synchronize()
-            e_ms.append(a.elapsed_time(b))
+        e_sampler = ClockSampler(local)
+        with e_sampler:
+            for _ in range(max(2, args.steps)):
+                flush.zero_()
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                e2e_step()
+                b.record(stream)
+                b.synchronize()
+                e_ms.append(a.elapsed_time(b))
         e2e_ms = D.max_over_ranks(sum(e_ms) / len(e_ms), dev)
         e2e = {"value": D.job_throughput(st_evals, e2e_ms, world), "unit": UNIT, "ms_per_step": e2e_ms,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "ms_per_step_min": D.max_over_ranks(min(e_ms), dev), "clocks": e_sampler.summary()}
 
     plan_avg = sum(plan_ms) / len(plan_ms)
     esdf_avg = sum(esdf_ms) / len(esdf_ms)

@@ -138,6 +138,25 @@ def test_cost_and_terms_match_oracle(gpu_lib, T):
     assert (np.abs(to_np(terms) - want_t) / sc).max() <= TOL_COST
 
 
+@pytest.mark.parametrize("T", [7, 64])
+def test_kinematic_terms_periodic_in_joint_angles(gpu_lib, T):
+    """The world and goal terms depend on the joints only through the chain's
+    sines and cosines: shifting every joint angle by up to three whole turns
+    leaves them at the oracle's values for the unshifted trajectories."""
+    wl, orc, x = _random_batch(T, seed=200 + T)
+    rng = np.random.default_rng(T)
+    turns = rng.integers(-3, 4, size=x.shape)
+    xs = (x + 2.0 * math.pi * turns).astype(np.float32)
+    planner, batch = gpu_side(wl)
+    _, terms = B.cost(planner.robot, batch.desc, batch.pr, _cuda(xs), terms=True)
+    want_c, want_t = _oracle_cost(orc, wl, x.astype(np.float64), grad=False, terms=True)
+    sc = np.maximum(np.abs(want_c)[..., None], 1e-6)
+    got = to_np(terms)
+    for j in (0, 2):                            # world, goal
+        assert (np.abs(got[..., j] - want_t[..., j]) / sc[..., 0]).max() <= TOL_COST, j
+    assert (want_t[..., 0] > 0).any() and (want_t[..., 2] > 0).any()
+
+
 @pytest.mark.parametrize("T", [1, 5, 32, 47, 64, 128])
 def test_gradient_matches_oracle(gpu_lib, T):
     wl, orc, x = _random_batch(T, seed=100 + T)
