@@ -22,26 +22,30 @@ constexpr int GB = 64, GK = 16;
 // SPLIT: blockIdx.z takes K-range [z * kchunk, (z + 1) * kchunk) and adds
 // alpha * partial into C atomically (used for accumulating weight gradients,
 // where M x N is small and K = batch x length is large).
-template <bool TA, bool TB, bool SPLIT>
+// TILE: output tile edge (64, or 32 for products with few tiles and a long K:
+// four times the blocks; every output still sums its K terms in the same order,
+// so both tilings give the same bits).
+template <bool TA, bool TB, bool SPLIT, int TILE = GB>
 __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alpha, const float *__restrict__ A,
                                                  int lda, const float *__restrict__ B, int ldb, float beta,
                                                  float *__restrict__ C, int ldc, const float *__restrict__ bias,
                                                  int kchunk) {
-    __shared__ float As[GK][GB + 4];
-    __shared__ float Bs[GK][GB + 4];
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, 4 x 4 outputs each
-    const int m0 = blockIdx.x * GB, n0 = blockIdx.y * GB;     // row tiles in x: up to 2^31 - 1 of them
+    constexpr int TT = TILE / 16;                             // outputs per thread along each axis
+    __shared__ float As[GK][TILE + 4];
+    __shared__ float Bs[GK][TILE + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;   // 16 x 16 threads, TT x TT outputs each
+    const int m0 = blockIdx.x * TILE, n0 = blockIdx.y * TILE; // row tiles in x: up to 2^31 - 1 of them
     const int kb = SPLIT ? blockIdx.z * kchunk : 0;
     const int ke = SPLIT ? min(K, kb + kchunk) : K;
-    float acc[4][4] = {};
+    float acc[TT][TT] = {};
     for (int k0 = kb; k0 < ke; k0 += GK) {
-        for (int t = threadIdx.x; t < GB * GK; t += 256) {
+        for (int t = threadIdx.x; t < TILE * GK; t += 256) {
             const int kk = t % GK, mm = t / GK;                    // A tile: [mm][kk]
             const int gm = m0 + mm, gk = k0 + kk;
             float a = 0.f;
             if (gm < M && gk < ke) a = TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
             As[kk][mm] = a;
-            const int nn = t % GB, kr = t / GB;                    // B tile: [kr][nn]
+            const int nn = t % TILE, kr = t / TILE;                // B tile: [kr][nn]
             const int gn = n0 + nn, gk2 = k0 + kr;
             float b = 0.f;
             if (gn < N && gk2 < ke) b = TB ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn];
@@ -50,25 +54,25 @@ __global__ void __launch_bounds__(256) k_gemm_f32(int M, int N, int K, float alp
         __syncthreads();
 #pragma unroll
         for (int kk = 0; kk < GK; ++kk) {
-            float a[4], b[4];
+            float a[TT], b[TT];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty * 4 + i];
+            for (int i = 0; i < TT; ++i) a[i] = As[kk][ty * TT + i];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx * 4 + j];
+            for (int j = 0; j < TT; ++j) b[j] = Bs[kk][tx * TT + j];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < TT; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+                for (int j = 0; j < TT; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int gm = m0 + ty * 4 + i;
+    for (int i = 0; i < TT; ++i) {
+        const int gm = m0 + ty * TT + i;
         if (gm >= M) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int gn = n0 + tx * 4 + j;
+        for (int j = 0; j < TT; ++j) {
+            const int gn = n0 + tx * TT + j;
             if (gn >= N) continue;
             if (SPLIT) {
                 atomicAdd(C + (size_t)gm * ldc + gn, alpha * acc[i][j]);
@@ -186,28 +190,33 @@ __global__ void k_im2col1d(const float *__restrict__ x, int N, int L, int C, int
     }
 }
 
-// BF16 rows of 8-column chunks (16-byte stores): FP32 input, any C
+// BF16 rows of 8-column chunks (16-byte stores): FP32 input, any C.  IDX: the
+// index type (32-bit when the chunk count fits, which keeps the row / chunk
+// divisions cheap); the chunk's (tap, channel) pairs are stepped, not divided.
+template <typename IDX>
 __global__ void k_im2col1d_v8(const float *__restrict__ x, int N, int L, int C, int k, int s, int p, int Lo,
                               int kc_pad, __nv_bfloat16 *__restrict__ cols) {
-    const int chunks = kc_pad / 8;
-    const long long total = (long long)N * Lo * chunks;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+    const IDX chunks = (IDX)(kc_pad / 8);
+    const IDX total = (IDX)N * (IDX)Lo * chunks;
+    const int kC = k * C;
+    for (IDX i = (IDX)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (IDX)gridDim.x * blockDim.x) {
         const int ch = (int)(i % chunks);
-        const long long row = i / chunks;
-        const int lo = (int)(row % Lo), n = (int)(row / Lo);
+        const IDX row = i / chunks;
+        const int lo = (int)(row % (IDX)Lo), n = (int)(row / (IDX)Lo);
+        const int col0 = ch * 8;
+        int j = col0 / C, c = col0 - j * C;
         __align__(16) __nv_bfloat16 v[8];
 #pragma unroll
         for (int e = 0; e < 8; ++e) {
-            const int col = ch * 8 + e;
             float f = 0.f;
-            if (col < k * C) {
-                const int j = col / C, c = col - j * C;
+            if (col0 + e < kC) {
                 const int li = lo * s - p + j;
                 if (li >= 0 && li < L) f = x[((size_t)n * L + li) * C + c];
             }
             v[e] = __float2bfloat16_rn(f);
+            if (++c == C) { c = 0; ++j; }
         }
-        *reinterpret_cast<uint4 *>(cols + row * kc_pad + ch * 8) = *reinterpret_cast<const uint4 *>(v);
+        *reinterpret_cast<uint4 *>(cols + (size_t)row * kc_pad + ch * 8) = *reinterpret_cast<const uint4 *>(v);
     }
 }
 
@@ -570,14 +579,14 @@ static unsigned grid_for(long long n, int block = 256) {
     return (unsigned)(g < 1 ? 1 : g);
 }
 
-template <bool SPLIT>
+template <bool SPLIT, int TILE = GB>
 static void gemm_go(int ta, int tb, dim3 grid, int M, int N, int K, float alpha, const float *A, int lda,
                     const float *B, int ldb, float beta, float *C, int ldc, const float *bias, int kchunk,
                     cudaStream_t st) {
-    if (!ta && !tb) k_gemm_f32<false, false, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
-    else if (!ta && tb) k_gemm_f32<false, true, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
-    else if (ta && !tb) k_gemm_f32<true, false, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
-    else k_gemm_f32<true, true, SPLIT><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    if (!ta && !tb) k_gemm_f32<false, false, SPLIT, TILE><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else if (!ta && tb) k_gemm_f32<false, true, SPLIT, TILE><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else if (ta && !tb) k_gemm_f32<true, false, SPLIT, TILE><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
+    else k_gemm_f32<true, true, SPLIT, TILE><<<grid, 256, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk);
 }
 
 int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A, int lda, const float *B, int ldb,
@@ -592,6 +601,12 @@ int nn_gemm_f32(int ta, int tb, int M, int N, int K, float alpha, const float *A
         splits = (K + kchunk - 1) / kchunk;
         dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB, splits);
         gemm_go<true>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, kchunk, st);
+    } else if (tiles < 152 / 2 && K >= 256) {
+        // few 64 x 64 tiles and a long K (e.g. a flattened-feature linear layer of a
+        // few hundred rows): 32 x 32 tiles put four times as many blocks to work
+        constexpr int S = 32;
+        dim3 grid((M + S - 1) / S, (N + S - 1) / S);
+        gemm_go<false, S>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, K, st);
     } else {
         dim3 grid((M + GB - 1) / GB, (N + GB - 1) / GB);
         gemm_go<false>(ta, tb, grid, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, bias, K, st);
@@ -609,8 +624,14 @@ int nn_gemm_bf16(int M, int N, int K, const void *A, const void *W, float *C, co
 int nn_im2col1d(const float *x, int N, int L, int C, int k, int s, int p, int Lo, int kc_pad, void *cols, int bf16,
                 cudaStream_t st) {
     const long long total = (long long)N * Lo * kc_pad;
-    if (bf16 && kc_pad % 8 == 0 && ((uintptr_t)cols & 15) == 0)
-        k_im2col1d_v8<<<grid_for(total / 8), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
+    if (bf16 && kc_pad % 8 == 0 && ((uintptr_t)cols & 15) == 0) {
+        if (total / 8 + 152LL * 64 * 256 < (1LL << 32))
+            k_im2col1d_v8<unsigned><<<grid_for(total / 8), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad,
+                                                                          (__nv_bfloat16 *)cols);
+        else
+            k_im2col1d_v8<unsigned long long><<<grid_for(total / 8), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad,
+                                                                                    (__nv_bfloat16 *)cols);
+    }
     else if (bf16) k_im2col1d<__nv_bfloat16><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (__nv_bfloat16 *)cols);
     else k_im2col1d<float><<<grid_for(total), 256, 0, st>>>(x, N, L, C, k, s, p, Lo, kc_pad, (float *)cols);
     return (int)cudaGetLastError();
