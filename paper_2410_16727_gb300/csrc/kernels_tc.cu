@@ -33,6 +33,11 @@
 // empty barrier in both CTAs.  The two CTAs walk the same number of tiles (an
 // odd last tile is paired with a tile past the end, whose rows are read as the
 // TMA fill value and never stored).
+//
+// Units of two tiles (MT = 2, 128-output layers with long K): a CTA loads the A
+// rows of two adjacent tiles in one TMA box and issues both tiles' MMAs against
+// each stage's weight tile, so a weight tile feeds 256 output rows; the two
+// accumulators (2 x 128 columns) stay double-buffered.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -427,16 +432,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int COUT, int STAGES, int MODE, int CL>
+template <int COUT, int STAGES, int MODE, int CL, int MT>
 __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(const __grid_constant__ TcParams p) {
-    constexpr int A_BYTES = kTileM * kBlockK * 2;
+    constexpr int TILE_A_BYTES = kTileM * kBlockK * 2;
+    constexpr int A_BYTES = MT * TILE_A_BYTES;                 // MT tiles of one unit, one TMA box
     constexpr int B_BYTES = COUT * kBlockK * 2;
     constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    constexpr uint32_t TMEM_COLS = 2 * COUT < 32 ? 32 : 2 * COUT;    // two accumulator buffers
+    // a unit's accumulators: MT tiles x COUT columns; two buffers when they fit
+    constexpr int UNIT_COLS = MT * COUT;
+    constexpr int NBUF = 2 * UNIT_COLS <= 512 ? 2 : 1;
+    constexpr uint32_t TMEM_COLS = NBUF * UNIT_COLS < 32 ? 32 : NBUF * UNIT_COLS;
     constexpr uint32_t IDESC = bf16_idesc(kTileM, COUT);
     constexpr int kEpiWarps = EpiShape<COUT>::EW;
     static_assert(COUT % 16 == 0 && COUT >= 16 && COUT <= 256, "MMA N");
     static_assert(CL == 1 || (CL == 2 && COUT >= 128), "clusters of two share wide weight tiles");
+    static_assert((MT == 1 || MT == 2) && NBUF * UNIT_COLS <= 512, "tensor memory holds 512 columns");
     constexpr uint16_t kPair = 0x3;
 
     extern __shared__ uint8_t smem_raw[];
@@ -449,10 +459,10 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = p.taps * p.c_blocks;
     const int n_tiles = (p.M + kTileM - 1) / kTileM;
-    // work units: single tiles, or with clusters pairs of adjacent tiles, this CTA
-    // taking tile CL u + rank of unit u (past the end for the odd last unit)
+    // work units of CL x MT adjacent tiles: this CTA takes the MT tiles from
+    // (CL u + rank) MT of unit u (past the end for a short last unit)
     const int crank = CL > 1 ? (int)cluster_rank() : 0;
-    const int n_units = (n_tiles + CL - 1) / CL;
+    const int n_units = (n_tiles + CL * MT - 1) / (CL * MT);
     const int unit0 = blockIdx.x / CL, unit_step = gridDim.x / CL;
 
     if (threadIdx.x == 0) {
@@ -488,7 +498,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
             // producer
             int g = 0;
             for (int u = unit0; u < n_units && !*fail; u += unit_step) {
-                const int tile = CL * u + crank;
+                const int tile = (CL * u + crank) * MT;
                 const int sample0 = tile * kTileM / p.L;
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int s = g % STAGES;
@@ -518,14 +528,15 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
             // MMA issuer
             int g = 0, it = 0;
             for (int u = unit0; u < n_units && !*fail; u += unit_step, ++it) {
-                const int b = it & 1;
-                if (it >= 2 && !mbar_wait(&acce_bar[b], ((it >> 1) - 1) & 1)) {
+                const int b = NBUF == 2 ? (it & 1) : 0;
+                const int use = NBUF == 2 ? (it >> 1) : it;      // earlier units in buffer b
+                if (use >= 1 && !mbar_wait(&acce_bar[b], (use - 1) & 1)) {
                     record_failure(p.err, 4);
                     *fail = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d = tmem + (uint32_t)(b * COUT);
+                const uint32_t d = tmem + (uint32_t)(b * UNIT_COLS);
                 for (int kb = 0; kb < nk; ++kb, ++g) {
                     const int s = g % STAGES;
                     if (!mbar_wait(&full_bar[s], (g / STAGES) & 1)) {
@@ -535,9 +546,13 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
                     }
                     tc_fence_after();
                     const uint32_t a = smem_u32(smem + s * STAGE_BYTES), bb = a + A_BYTES;
+                    // the MT tiles of the unit share the stage's weight tile
 #pragma unroll
                     for (int k = 0; k < kBlockK / 16; ++k)
-                        umma_bf16(d, sw128_desc(a + 32 * k), sw128_desc(bb + 32 * k), IDESC, (kb | k) != 0);
+#pragma unroll
+                        for (int t = 0; t < MT; ++t)
+                            umma_bf16(d + (uint32_t)(t * COUT), sw128_desc(a + t * TILE_A_BYTES + 32 * k),
+                                      sw128_desc(bb + 32 * k), IDESC, (kb | k) != 0);
                     if (CL > 1) umma_commit_mc(&empty_bar[s], kPair);
                     else umma_commit(&empty_bar[s]);
                 }
@@ -556,16 +571,21 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // epilogue warps only
         int it = 0;
         for (int u = unit0; u < n_units; u += unit_step, ++it) {
-            const int tile = CL * u + crank;
-            const int b = it & 1;
-            if (!mbar_wait(&accf_bar[b], (it >> 1) & 1)) {
+            const int tile = (CL * u + crank) * MT;
+            const int b = NBUF == 2 ? (it & 1) : 0;
+            const int use = NBUF == 2 ? (it >> 1) : it;
+            if (!mbar_wait(&accf_bar[b], use & 1)) {
                 record_failure(p.err, 3);
                 *fail = 1;
                 break;
             }
             __syncwarp();                      // the tensor-memory loads are warp-collective
             tc_fence_after();
-            if (!*fail) epilogue<COUT, MODE>(p, s_const, tmem + (uint32_t)(b * COUT), tile * kTileM, q, half, lane);
+            if (!*fail)
+#pragma unroll 1
+                for (int t = 0; t < MT; ++t)
+                    epilogue<COUT, MODE>(p, s_const, tmem + (uint32_t)(b * UNIT_COLS + t * COUT), (tile + t) * kTileM,
+                                         q, half, lane);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[b]);
@@ -617,11 +637,11 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int COUT, int STAGES, int MODE, int CL>
+template <int COUT, int STAGES, int MODE, int CL, int MT>
 int launch_tc(const TcParams &p, cudaStream_t st) {
-    constexpr int smem = STAGES * (kTileM + COUT) * kBlockK * 2 + 1024;
+    constexpr int smem = STAGES * (MT * kTileM + COUT) * kBlockK * 2 + 1024;
     constexpr int threads = 32 * (2 + EpiShape<COUT>::EW);
-    auto kern = k_conv_tc<COUT, STAGES, MODE, CL>;
+    auto kern = k_conv_tc<COUT, STAGES, MODE, CL, MT>;
     static bool configured = false;       // the attribute is per function; setting it twice is harmless
     static int max_units = 0;             // work units (CTAs, or clusters) resident at once
     if (!configured) {
@@ -651,7 +671,7 @@ int launch_tc(const TcParams &p, cudaStream_t st) {
         configured = true;
     }
     const int tiles = (p.M + kTileM - 1) / kTileM;
-    const int units = (tiles + CL - 1) / CL;
+    const int units = (tiles + CL * MT - 1) / (CL * MT);
     const unsigned grid = (unsigned)(CL * (units < max_units ? units : max_units));
     if (CL == 1) {
         kern<<<grid, threads, smem, st>>>(p);
@@ -672,18 +692,29 @@ int launch_tc(const TcParams &p, cudaStream_t st) {
     return (int)cudaLaunchKernelEx(&cfg, kern, p);
 }
 
+// mt2: units of two tiles per CTA sharing each weight tile, which halves the
+// weight bytes per output row.  Measured at the sampling size (32768
+// trajectories): 1.3-1.4x faster for 128 outputs over 1280-2560 input values
+// per row (the skip-concatenation layers), neutral at 640, and slower for 256
+// outputs, whose two 256-column accumulators fill the tensor memory, so the
+// epilogue of one unit can no longer overlap the next unit's MMAs.
 template <int MODE>
-int launch_mode(int cout_pad, const TcParams &p, cudaStream_t st) {
+int launch_mode(int cout_pad, bool mt2, const TcParams &p, cudaStream_t st) {
     switch (cout_pad) {
         case 16:
             if constexpr (MODE == kEpiGN) return (int)cudaErrorInvalidValue;
-            else return launch_tc<16, 8, MODE, 1>(p, st);
-        case 64: return launch_tc<64, 8, MODE, 1>(p, st);
-        case 128: return launch_tc<128, 6, MODE, 2>(p, st);
-        case 256: return launch_tc<256, 4, MODE, 2>(p, st);
+            else return launch_tc<16, 8, MODE, 1, 1>(p, st);
+        case 64: return launch_tc<64, 8, MODE, 1, 1>(p, st);
+        case 128: return mt2 ? launch_tc<128, 4, MODE, 2, 2>(p, st) : launch_tc<128, 6, MODE, 2, 1>(p, st);
+        case 256: return launch_tc<256, 4, MODE, 2, 1>(p, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }
+
+// Two-tile units: 128 outputs, at least 20 K blocks (1280 input values per
+// row), and enough tiles for three rounds of two-tile units over the SMs.
+constexpr int kMt2MinKBlocks = 20;
+constexpr int kMt2MinTiles = 6 * 152;
 
 }  // namespace
 
@@ -695,7 +726,9 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     TcParams p;
     memset(&p, 0, sizeof(p));
     const int cin = d.c0 + d.c1;
-    const int spt = kTileM / d.L;      // samples per tile
+    const long long n_tiles = ((long long)d.n_samples * d.L + kTileM - 1) / kTileM;
+    const bool mt2 = d.cout_pad == 128 && d.taps * (cin / kBlockK) >= kMt2MinKBlocks && n_tiles >= kMt2MinTiles;
+    const int spt = (mt2 ? 2 : 1) * kTileM / d.L;      // samples per A box (the tiles of one unit)
     if (!make_map(&p.a0, d.a0_dev, (uint64_t)d.c0, (uint64_t)d.L, (uint64_t)d.n_samples, (uint32_t)d.L,
                   (uint32_t)spt))
         return -1;
@@ -734,9 +767,9 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     p.err = d.err_dev;
     if (p.M == 0) return cudaSuccess;
     switch (d.epilogue) {
-        case kEpiF32: return launch_mode<kEpiF32>(d.cout_pad, p, st);
-        case kEpiBF16: return launch_mode<kEpiBF16>(d.cout_pad, p, st);
-        case kEpiGN: return launch_mode<kEpiGN>(d.cout_pad, p, st);
+        case kEpiF32: return launch_mode<kEpiF32>(d.cout_pad, mt2, p, st);
+        case kEpiBF16: return launch_mode<kEpiBF16>(d.cout_pad, mt2, p, st);
+        case kEpiGN: return launch_mode<kEpiGN>(d.cout_pad, mt2, p, st);
         default: return (int)cudaErrorInvalidValue;
     }
 }

@@ -36,7 +36,9 @@ def _mish(v):
 
 
 @pytest.mark.parametrize("M,K,cout,cout_pad", [(300, 64, 7, 16), (128, 192, 64, 64), (1000, 128, 128, 128),
-                                               (77, 512, 256, 256), (4096, 64, 64, 64)])
+                                               (77, 512, 256, 256), (4096, 64, 64, 64),
+                                               # two-tile units (128 outputs, K >= 1280; ragged last unit)
+                                               (120001, 1280, 128, 128), (117000, 192, 256, 256)])
 def test_plain_gemm(gpu_lib, M, K, cout, cout_pad):
     rng = np.random.default_rng(M + K)
     a = _bf(rng.normal(size=(M, K)))
@@ -64,7 +66,10 @@ def test_plain_gemm(gpu_lib, M, K, cout, cout_pad):
     # wide outputs run in CTA pairs: several units per CTA, odd tile count
     (4001, 8, 64, 0, 3, 256, 1), (4001, 16, 128, 0, 3, 128, 1),
     # two taps over row pairs (the stride-2 convolution), one-sided padding
-    (301, 16, 128, 0, 2, 64, 1), (77, 8, 256, 0, 2, 128, 1), (50, 32, 64, 0, 3, 64, 0), (50, 16, 64, 0, 3, 64, 2)])
+    (301, 16, 128, 0, 2, 64, 1), (77, 8, 256, 0, 2, 128, 1), (50, 32, 64, 0, 3, 64, 0), (50, 16, 64, 0, 3, 64, 2),
+    # two-tile units (128 outputs over at least 20 K blocks, at least 912 tiles; the last unit ragged)
+    (7403, 16, 256, 256, 3, 128, 1), (14799, 8, 256, 0, 5, 128, 2), (3701, 32, 128, 128, 5, 128, 2),
+    (14799, 8, 128, 128, 5, 256, 2)])
 def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout, pad):
     rng = np.random.default_rng(N * L + C0 + k)
     x0 = _bf(rng.normal(size=(N, L, C0)))
@@ -83,7 +88,9 @@ def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout, pad):
 
 
 @pytest.mark.parametrize("N,L,C,cout,film,res", [(13, 32, 64, 64, True, False), (10, 16, 128, 128, False, True),
-                                                 (21, 8, 256, 256, True, True), (6, 32, 64, 64, False, False)])
+                                                 (21, 8, 256, 256, True, True), (6, 32, 64, 64, False, False),
+                                                 # 256 outputs at 925 tiles; 128 outputs in two-tile units
+                                                 (14799, 8, 256, 256, True, True), (14799, 8, 256, 128, True, True)])
 def test_group_norm_epilogue(gpu_lib, N, L, C, cout, film, res):
     rng = np.random.default_rng(7 * N + L)
     k, pad, G = 5, 2, 8
