@@ -277,8 +277,21 @@ __device__ __forceinline__ float mish_fast(float x) {
     return x * __fdividef(n, n + 2.f);
 }
 
-// Per-layer constants, staged in shared memory once per CTA.
-struct EpiConst {
+// Mish of a channel pair: the same n / (n + 2) form, with the adds and
+// multiplies packed (exp and the reciprocal stay per element).
+__device__ __forceinline__ float2 mish2(float2 x) {
+    const float2 e = make_float2(__expf(x.x), __expf(x.y));
+    const float2 n = __fmul2_rn(e, __fadd2_rn(e, make_float2(2.f, 2.f)));
+    const float2 dn = __fadd2_rn(n, make_float2(2.f, 2.f));
+    float2 y = __fmul2_rn(x, make_float2(__fdividef(n.x, dn.x), __fdividef(n.y, dn.y)));
+    if (x.x > 15.f) y.x = x.x;                // n / (n + 2) = 1 to FP32 precision
+    if (x.y > 15.f) y.y = x.y;
+    return y;
+}
+
+// Per-layer constants, staged in shared memory once per CTA (16-byte aligned:
+// the epilogue reads channel pairs as float2).
+struct __align__(16) EpiConst {
     float bias[256], gamma[256], beta[256];
 };
 
@@ -317,22 +330,30 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
 #pragma unroll 1
         for (int c0 = cb; c0 < cb + HALF; c0 += CH) {
             // FiLM rows and the residual do not depend on the accumulator: issue
-            // their loads first so their latency hides behind the statistics
-            float4 fsc[CH / 4], fsh[CH / 4];
+            // their loads first so their latency hides behind the statistics.
+            // The element-wise chain runs on channel pairs (packed FP32x2 adds,
+            // multiplies and fused multiply-adds: one instruction per pair).
+            float2 fsc[CH / 2], fsh[CH / 2];
             uint4 rr[CH / 8];
             if (film) {
 #pragma unroll
                 for (int j = 0; j < CH / 4; ++j) {
-                    fsc[j] = *reinterpret_cast<const float4 *>(film + c0 + 4 * j);
-                    fsh[j] = *reinterpret_cast<const float4 *>(film + COUT + c0 + 4 * j);
+                    const float4 a = *reinterpret_cast<const float4 *>(film + c0 + 4 * j);
+                    const float4 b = *reinterpret_cast<const float4 *>(film + COUT + c0 + 4 * j);
+                    fsc[2 * j] = make_float2(a.x, a.y);
+                    fsc[2 * j + 1] = make_float2(a.z, a.w);
+                    fsh[2 * j] = make_float2(b.x, b.y);
+                    fsh[2 * j + 1] = make_float2(b.z, b.w);
                 }
                 if (p.film_add) {
 #pragma unroll
                     for (int j = 0; j < CH / 4; ++j) {
                         const float4 a = *reinterpret_cast<const float4 *>(p.film_add + c0 + 4 * j);
                         const float4 b = *reinterpret_cast<const float4 *>(p.film_add + COUT + c0 + 4 * j);
-                        fsc[j].x += a.x; fsc[j].y += a.y; fsc[j].z += a.z; fsc[j].w += a.w;
-                        fsh[j].x += b.x; fsh[j].y += b.y; fsh[j].z += b.z; fsh[j].w += b.w;
+                        fsc[2 * j] = __fadd2_rn(fsc[2 * j], make_float2(a.x, a.y));
+                        fsc[2 * j + 1] = __fadd2_rn(fsc[2 * j + 1], make_float2(a.z, a.w));
+                        fsh[2 * j] = __fadd2_rn(fsh[2 * j], make_float2(b.x, b.y));
+                        fsh[2 * j + 1] = __fadd2_rn(fsh[2 * j + 1], make_float2(b.z, b.w));
                     }
                 }
             }
@@ -342,58 +363,60 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
             }
             float v[CH];
             tmem_ld<CH>(trow + c0, v);
+            float2 w[CH / 2];
 #pragma unroll
-            for (int i = 0; i < CH; ++i) v[i] += kc.bias[c0 + i];
+            for (int i = 0; i < CH / 2; ++i)
+                w[i] = __fadd2_rn(make_float2(v[2 * i], v[2 * i + 1]),
+                                  *reinterpret_cast<const float2 *>(&kc.bias[c0 + 2 * i]));
             float mean[GPC], rstd[GPC];
 #pragma unroll
             for (int g = 0; g < GPC; ++g) {
-                float s = 0.f;
+                float2 s2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < CG; ++i) s += v[g * CG + i];
+                for (int i = 0; i < CG / 2; ++i) s2 = __fadd2_rn(s2, w[g * (CG / 2) + i]);
+                float s = s2.x + s2.y;
                 for (int off = 1; off < Lg; off <<= 1) s += __shfl_xor_sync(0xffffffffu, s, off);
                 mean[g] = s * inv_n;
-                float t = 0.f;
+                const float2 nm = make_float2(-mean[g], -mean[g]);
+                float2 t2 = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int i = 0; i < CG; ++i) {
-                    const float d = v[g * CG + i] - mean[g];
-                    t += d * d;
+                for (int i = 0; i < CG / 2; ++i) {
+                    const float2 d = __fadd2_rn(w[g * (CG / 2) + i], nm);
+                    t2 = __ffma2_rn(d, d, t2);
                 }
+                float t = t2.x + t2.y;
                 for (int off = 1; off < Lg; off <<= 1) t += __shfl_xor_sync(0xffffffffu, t, off);
                 rstd[g] = rsqrtf(t * inv_n + p.gn_eps);
             }
 #pragma unroll
-            for (int i = 0; i < CH; ++i) {
-                const int g = i / CG;
-                v[i] = mish_fast((v[i] - mean[g]) * rstd[g] * kc.gamma[c0 + i] + kc.beta[c0 + i]);
-            }
-            if (film) {
-#pragma unroll
-                for (int j = 0; j < CH / 4; ++j) {
-                    v[4 * j] = v[4 * j] * fsc[j].x + fsh[j].x;
-                    v[4 * j + 1] = v[4 * j + 1] * fsc[j].y + fsh[j].y;
-                    v[4 * j + 2] = v[4 * j + 2] * fsc[j].z + fsh[j].z;
-                    v[4 * j + 3] = v[4 * j + 3] * fsc[j].w + fsh[j].w;
-                }
+            for (int i = 0; i < CH / 2; ++i) {
+                const int g = (2 * i) / CG;
+                const float2 d = __fadd2_rn(w[i], make_float2(-mean[g], -mean[g]));
+                const float2 nrm = __fmul2_rn(d, make_float2(rstd[g], rstd[g]));
+                float2 y = mish2(__ffma2_rn(nrm, *reinterpret_cast<const float2 *>(&kc.gamma[c0 + 2 * i]),
+                                            *reinterpret_cast<const float2 *>(&kc.beta[c0 + 2 * i])));
+                if (film) y = __ffma2_rn(y, fsc[i], fsh[i]);
+                w[i] = y;
             }
             if (res) {
 #pragma unroll
                 for (int j = 0; j < CH / 8; ++j) {
                     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&rr[j]);
 #pragma unroll
-                    for (int e = 0; e < 4; ++e) {
-                        const float2 f = __bfloat1622float2(h[e]);
-                        v[8 * j + 2 * e] += f.x;
-                        v[8 * j + 2 * e + 1] += f.y;
-                    }
+                    for (int e = 0; e < 4; ++e) w[4 * j + e] = __fadd2_rn(w[4 * j + e], __bfloat1622float2(h[e]));
                 }
             }
             if (valid) {
 #pragma unroll
                 for (int j = 0; j < CH / 8; ++j) {
-                    float y[8];
-#pragma unroll
-                    for (int e = 0; e < 8; ++e) y[e] = v[8 * j + e];
-                    store8_bf16(out + c0 + 8 * j, y);
+                    uint4 u;
+                    __nv_bfloat162 h0 = __float22bfloat162_rn(w[4 * j]), h1 = __float22bfloat162_rn(w[4 * j + 1]);
+                    __nv_bfloat162 h2 = __float22bfloat162_rn(w[4 * j + 2]), h3 = __float22bfloat162_rn(w[4 * j + 3]);
+                    u.x = *reinterpret_cast<uint32_t *>(&h0);
+                    u.y = *reinterpret_cast<uint32_t *>(&h1);
+                    u.z = *reinterpret_cast<uint32_t *>(&h2);
+                    u.w = *reinterpret_cast<uint32_t *>(&h3);
+                    *reinterpret_cast<uint4 *>(out + c0 + 8 * j) = u;
                 }
             }
         }
