@@ -455,12 +455,17 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-template <int COUT, int STAGES, int MODE, int CL, int MT>
+// RESW: the layer's whole weight matrix (at most kMaxResK K blocks) is loaded
+// once per CTA and stays resident; the ring then carries only A tiles.
+constexpr int kMaxResK = 8;
+
+template <int COUT, int STAGES, int MODE, int CL, int MT, bool RESW = false>
 __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(const __grid_constant__ TcParams p) {
     constexpr int TILE_A_BYTES = kTileM * kBlockK * 2;
     constexpr int A_BYTES = MT * TILE_A_BYTES;                 // MT tiles of one unit, one TMA box
     constexpr int B_BYTES = COUT * kBlockK * 2;
-    constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    constexpr int STAGE_BYTES = RESW ? A_BYTES : A_BYTES + B_BYTES;
+    static_assert(!RESW || (CL == 1 && MT == 1), "resident weights: single CTAs");
     // a unit's accumulators: MT tiles x COUT columns; two buffers when they fit
     constexpr int UNIT_COLS = MT * COUT;
     constexpr int NBUF = 2 * UNIT_COLS <= 512 ? 2 : 1;
@@ -474,10 +479,11 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
 
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], wfull_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int s_issued, s_consumed, s_fail;
+    __shared__ int s_issued, s_consumed, s_fail, s_wissued;
     __shared__ EpiConst s_const;
+    uint8_t *const wres = smem + STAGES * STAGE_BYTES;          // resident weight tiles (RESW)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = p.taps * p.c_blocks;
@@ -497,9 +503,11 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
             mbar_init(&accf_bar[b], 1);
             mbar_init(&acce_bar[b], kEpiWarps);
         }
+        mbar_init(&wfull_bar, 1);
         s_issued = 0;
         s_consumed = 0;
         s_fail = 0;
+        s_wissued = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -519,6 +527,14 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     if (warp == 0) {
         if (lane == 0) {
             // producer
+            if (RESW && nk <= kMaxResK) {
+                mbar_expect_tx(&wfull_bar, nk * B_BYTES);
+                for (int kb = 0; kb < nk; ++kb) {
+                    const int tap = kb / p.c_blocks, cblk = kb - tap * p.c_blocks;
+                    tma_load_3d(wres + kb * B_BYTES, &p.w, &wfull_bar, cblk * kBlockK, tap, 0);
+                }
+                s_wissued = 1;
+            }
             int g = 0;
             for (int u = unit0; u < n_units && !*fail; u += unit_step) {
                 const int tile = (CL * u + crank) * MT;
@@ -537,11 +553,13 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
                         tma_load_3d(sa, &p.a0, &full_bar[s], cblk * kBlockK, tap - p.pad, sample0);
                     else
                         tma_load_3d(sa, &p.a1, &full_bar[s], (cblk - p.c0_blocks) * kBlockK, tap - p.pad, sample0);
-                    if (CL > 1)
+                    if (RESW) {
+                    } else if (CL > 1) {
                         tma_load_3d_mc(sa + A_BYTES + crank * (B_BYTES / 2), &p.w_half, &full_bar[s],
                                        cblk * kBlockK, tap, crank * (COUT / 2), kPair);
-                    else
+                    } else {
                         tma_load_3d(sa + A_BYTES, &p.w, &full_bar[s], cblk * kBlockK, tap, 0);
+                    }
                 }
             }
             s_issued = g;
@@ -549,6 +567,10 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     } else if (warp == 1) {
         if (lane == 0) {
             // MMA issuer
+            if (RESW && (nk > kMaxResK || !mbar_wait(&wfull_bar, 0))) {
+                record_failure(p.err, 2);
+                *fail = 1;
+            }
             int g = 0, it = 0;
             for (int u = unit0; u < n_units && !*fail; u += unit_step, ++it) {
                 const int b = NBUF == 2 ? (it & 1) : 0;
@@ -568,7 +590,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t a = smem_u32(smem + s * STAGE_BYTES), bb = a + A_BYTES;
+                    const uint32_t a = smem_u32(smem + s * STAGE_BYTES);
+                    const uint32_t bb = RESW ? smem_u32(wres + kb * B_BYTES) : a + A_BYTES;
                     // the MT tiles of the unit share the stage's weight tile
 #pragma unroll
                     for (int k = 0; k < kBlockK / 16; ++k)
@@ -619,6 +642,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
         // loads issued but never consumed: let them land before the CTA leaves
         for (int g = *(volatile int *)&s_consumed; g < *(volatile int *)&s_issued; ++g)
             if (!mbar_wait(&full_bar[g % STAGES], (g / STAGES) & 1)) break;
+        if (RESW && *(volatile int *)&s_wissued) mbar_wait(&wfull_bar, 0);
     }
     tc_fence_before();
     __syncthreads();
@@ -660,11 +684,12 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int COUT, int STAGES, int MODE, int CL, int MT>
+template <int COUT, int STAGES, int MODE, int CL, int MT, bool RESW = false>
 int launch_tc(const TcParams &p, cudaStream_t st) {
-    constexpr int smem = STAGES * (MT * kTileM + COUT) * kBlockK * 2 + 1024;
+    constexpr int smem = RESW ? STAGES * kTileM * kBlockK * 2 + kMaxResK * COUT * kBlockK * 2 + 1024
+                              : STAGES * (MT * kTileM + COUT) * kBlockK * 2 + 1024;
     constexpr int threads = 32 * (2 + EpiShape<COUT>::EW);
-    auto kern = k_conv_tc<COUT, STAGES, MODE, CL, MT>;
+    auto kern = k_conv_tc<COUT, STAGES, MODE, CL, MT, RESW>;
     static bool configured = false;       // the attribute is per function; setting it twice is harmless
     static int max_units = 0;             // work units (CTAs, or clusters) resident at once
     if (!configured) {
@@ -727,7 +752,10 @@ int launch_mode(int cout_pad, bool mt2, const TcParams &p, cudaStream_t st) {
         case 16:
             if constexpr (MODE == kEpiGN) return (int)cudaErrorInvalidValue;
             else return launch_tc<16, 8, MODE, 1, 1>(p, st);
-        case 64: return launch_tc<64, 8, MODE, 1, 1>(p, st);
+        case 64:
+            // 64-output layers with at most kMaxResK K blocks keep their weights resident
+            if (p.taps * p.c_blocks <= kMaxResK) return launch_tc<64, 9, MODE, 1, 1, true>(p, st);
+            return launch_tc<64, 8, MODE, 1, 1>(p, st);
         case 128: return mt2 ? launch_tc<128, 4, MODE, 2, 2>(p, st) : launch_tc<128, 6, MODE, 2, 1>(p, st);
         case 256: return launch_tc<256, 4, MODE, 2, 1>(p, st);
         default: return (int)cudaErrorInvalidValue;

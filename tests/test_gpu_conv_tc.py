@@ -69,7 +69,9 @@ def test_plain_gemm(gpu_lib, M, K, cout, cout_pad):
     (301, 16, 128, 0, 2, 64, 1), (77, 8, 256, 0, 2, 128, 1), (50, 32, 64, 0, 3, 64, 0), (50, 16, 64, 0, 3, 64, 2),
     # two-tile units (128 outputs over at least 20 K blocks, at least 912 tiles; the last unit ragged)
     (7403, 16, 256, 256, 3, 128, 1), (14799, 8, 256, 0, 5, 128, 2), (3701, 32, 128, 128, 5, 128, 2),
-    (14799, 8, 128, 128, 5, 256, 2)])
+    (14799, 8, 128, 128, 5, 256, 2),
+    # 64 outputs with resident weights (<= 8 K blocks) over many tiles per CTA; and with streamed weights
+    (4001, 32, 64, 0, 5, 64, 2), (1001, 32, 64, 64, 5, 64, 2)])
 def test_conv_taps_and_concat(gpu_lib, N, L, C0, C1, k, cout, pad):
     rng = np.random.default_rng(N * L + C0 + k)
     x0 = _bf(rng.normal(size=(N, L, C0)))
