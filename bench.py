@@ -528,6 +528,51 @@ def conv_tc_roofline() -> dict:
             "peak_source": src, "traffic": None}
 
 
+def conv_tc_shapes() -> list:
+    """The denoiser's tensor-core convolution classes at the sampling size
+    (32768 trajectories), each timed alone with CUDA events: the group-norm
+    epilogue (no FiLM or residual) against the plain BF16 epilogue of the same
+    product, so the epilogue's share of each class is visible.  A profiling aid,
+    not part of the benchmark line."""
+    import torch
+    from paper_2410_16727_gb300 import binding as B
+
+    cases = [("256 -> 256, 5 taps, L = 8, group norm", 8, 256, 0, 256, 5, B.EPI_GN),
+             ("256 -> 256, 5 taps, L = 8, plain", 8, 256, 0, 256, 5, B.EPI_BF16),
+             ("128 -> 128, 5 taps, L = 16, group norm", 16, 128, 0, 128, 5, B.EPI_GN),
+             ("128 -> 128, 5 taps, L = 16, plain", 16, 128, 0, 128, 5, B.EPI_BF16),
+             ("256 + 256 -> 128, 5 taps, L = 8, group norm (two-tile units)", 8, 256, 256, 128, 5, B.EPI_GN),
+             ("64 -> 64, 5 taps, L = 32, group norm (resident weights)", 32, 64, 0, 64, 5, B.EPI_GN),
+             ("64 -> 64, 5 taps, L = 32, plain (resident weights)", 32, 64, 0, 64, 5, B.EPI_BF16)]
+    N = 32768
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    rows = []
+    for name, L, C0, C1, cout, k, epi in cases:
+        x0 = torch.randn((N, L, C0), device="cuda", generator=g).to(torch.bfloat16)
+        x1 = torch.randn((N, L, C1), device="cuda", generator=g).to(torch.bfloat16) if C1 else None
+        w = (torch.randn((cout, k, C0 + C1), device="cuda", generator=g) / (k * (C0 + C1)) ** 0.5).to(torch.bfloat16)
+        zeros, ones = torch.zeros(cout, device="cuda"), torch.ones(cout, device="cuda")
+        out = torch.empty((N * L, cout), dtype=torch.bfloat16, device="cuda")
+        err = torch.zeros(1, dtype=torch.int32, device="cuda")
+        kw = dict(a1=x1, n_samples=N, L=L, taps=k, pad=k // 2, cout=cout, bias=zeros, epilogue=epi, err=err)
+        if epi == B.EPI_GN:
+            kw.update(rows_per_sample=L, gamma=ones, beta=zeros)
+        for _ in range(3):
+            B.conv_tc(x0, w, out, **kw)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(20):
+            B.conv_tc(x0, w, out, **kw)
+        b.record()
+        b.synchronize()
+        if int(err.item()) != 0:
+            raise RuntimeError("conv_tc reported a pipeline wait that gave up")
+        us = a.elapsed_time(b) / 20 * 1e3
+        rows.append({"layer": name, "us": us, "tflops": 2.0 * N * L * cout * k * (C0 + C1) / us / 1e6})
+    return rows
+
+
 # ---------------------------------------------------------------------------- learned proposal
 
 def run_learned(args) -> dict:
