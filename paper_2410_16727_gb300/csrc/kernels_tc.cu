@@ -61,6 +61,8 @@ enum { kEpiF32 = 0, kEpiBF16 = 1, kEpiGN = 2 };
 
 struct TcParams {
     CUtensorMap a0, a1, w, w_half;    // w_half: box of half the output rows (cluster multicast)
+    CUtensorMap out_map;              // BF16 output rows, box {CH, 32} (staged TMA stores; out_tma)
+    int out_tma;
     int M, L, taps, pad, c0_blocks, c_blocks;
     int cout, rows_per_sample;
     float gn_eps;
@@ -219,6 +221,45 @@ __device__ __forceinline__ void load8_bf16(const __nv_bfloat16 *p, float (&v)[8]
     }
 }
 
+// Staged output rows: each epilogue warp writes its 32 rows x CH columns (BF16)
+// into a shared-memory buffer in the tensor map's swizzled layout (16-byte units
+// XORed with address bits 7-8 for 64-byte rows, bit 7 for 32-byte rows), then one
+// lane stores the box with TMA (rows and columns outside the tensor are dropped).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, const void *src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_u32(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+template <int CH>
+__device__ __forceinline__ uint32_t stage_offset(int row, int unit) {
+    static_assert(CH == 16 || CH == 32, "32- or 64-byte rows");
+    if constexpr (CH == 32) return (uint32_t)(row * 64 + ((unit ^ ((row >> 1) & 3)) << 4));
+    else return (uint32_t)(row * 32 + ((unit ^ ((row >> 2) & 1)) << 4));
+}
+
+// Write this lane's row of the chunk (8-channel units u as uint4) and store the
+// warp's box at (column c0, row r0).
+template <int CH>
+__device__ __forceinline__ void staged_store(const TcParams &p, uint8_t *stage, int lane, const uint4 (&u)[CH / 8],
+                                             int c0, int r0) {
+    if (lane == 0) bulk_wait_read_all();      // the previous box has left the buffer
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < CH / 8; ++j) *reinterpret_cast<uint4 *>(stage + stage_offset<CH>(lane, j)) = u[j];
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        tma_store_2d(&p.out_map, stage, c0, r0);
+        bulk_commit();
+    }
+}
+
 __device__ __forceinline__ void record_failure(int *err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
@@ -307,7 +348,7 @@ struct EpiShape {
 
 template <int COUT, int MODE>
 __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, uint32_t tmem, int m0, int q,
-                                         int part, int lane) {
+                                         int part, int lane, uint8_t *stage) {
     constexpr int HALF = EpiShape<COUT>::PART;
     constexpr int CH = EpiShape<COUT>::CH;
     const int gm = m0 + q * 32 + lane;
@@ -406,18 +447,21 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
                     for (int e = 0; e < 4; ++e) w[4 * j + e] = __fadd2_rn(w[4 * j + e], __bfloat1622float2(h[e]));
                 }
             }
-            if (valid) {
+            uint4 u[CH / 8];
 #pragma unroll
-                for (int j = 0; j < CH / 8; ++j) {
-                    uint4 u;
-                    __nv_bfloat162 h0 = __float22bfloat162_rn(w[4 * j]), h1 = __float22bfloat162_rn(w[4 * j + 1]);
-                    __nv_bfloat162 h2 = __float22bfloat162_rn(w[4 * j + 2]), h3 = __float22bfloat162_rn(w[4 * j + 3]);
-                    u.x = *reinterpret_cast<uint32_t *>(&h0);
-                    u.y = *reinterpret_cast<uint32_t *>(&h1);
-                    u.z = *reinterpret_cast<uint32_t *>(&h2);
-                    u.w = *reinterpret_cast<uint32_t *>(&h3);
-                    *reinterpret_cast<uint4 *>(out + c0 + 8 * j) = u;
-                }
+            for (int j = 0; j < CH / 8; ++j) {
+                __nv_bfloat162 h0 = __float22bfloat162_rn(w[4 * j]), h1 = __float22bfloat162_rn(w[4 * j + 1]);
+                __nv_bfloat162 h2 = __float22bfloat162_rn(w[4 * j + 2]), h3 = __float22bfloat162_rn(w[4 * j + 3]);
+                u[j].x = *reinterpret_cast<uint32_t *>(&h0);
+                u[j].y = *reinterpret_cast<uint32_t *>(&h1);
+                u[j].z = *reinterpret_cast<uint32_t *>(&h2);
+                u[j].w = *reinterpret_cast<uint32_t *>(&h3);
+            }
+            if (p.out_tma) {
+                staged_store<CH>(p, stage, lane, u, c0, m0 + q * 32);
+            } else if (valid) {
+#pragma unroll
+                for (int j = 0; j < CH / 8; ++j) *reinterpret_cast<uint4 *>(out + c0 + 8 * j) = u[j];
             }
         }
     } else {
@@ -425,6 +469,25 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
         for (int c0 = cb; c0 < cb + HALF; c0 += CH) {
             float v[CH];
             tmem_ld<CH>(trow + c0, v);
+            if constexpr (MODE == kEpiBF16 && (CH == 16 || CH == 32)) {
+                if (p.out_tma) {
+                    uint4 u[CH / 8];
+#pragma unroll
+                    for (int j = 0; j < CH / 8; ++j) {
+                        float y[8];
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) y[e] = v[8 * j + e] + kc.bias[c0 + 8 * j + e];
+                        __nv_bfloat162 h0 = __floats2bfloat162_rn(y[0], y[1]), h1 = __floats2bfloat162_rn(y[2], y[3]);
+                        __nv_bfloat162 h2 = __floats2bfloat162_rn(y[4], y[5]), h3 = __floats2bfloat162_rn(y[6], y[7]);
+                        u[j].x = *reinterpret_cast<uint32_t *>(&h0);
+                        u[j].y = *reinterpret_cast<uint32_t *>(&h1);
+                        u[j].z = *reinterpret_cast<uint32_t *>(&h2);
+                        u[j].w = *reinterpret_cast<uint32_t *>(&h3);
+                    }
+                    staged_store<CH>(p, stage, lane, u, c0, m0 + q * 32);
+                    continue;
+                }
+            }
 #pragma unroll
             for (int i = 0; i < CH && valid; i += 8) {
                 const int c = c0 + i;
@@ -484,6 +547,9 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     __shared__ int s_issued, s_consumed, s_fail, s_wissued;
     __shared__ EpiConst s_const;
     uint8_t *const wres = smem + STAGES * STAGE_BYTES;          // resident weight tiles (RESW)
+    // output staging of the epilogue warps (32 rows x CH BF16 each), after the ring
+    constexpr int kStageWarpBytes = 32 * EpiShape<COUT>::CH * 2;
+    uint8_t *const stage_base = wres + (RESW ? kMaxResK * B_BYTES : 0);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = p.taps * p.c_blocks;
@@ -631,11 +697,12 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
 #pragma unroll 1
                 for (int t = 0; t < MT; ++t)
                     epilogue<COUT, MODE>(p, s_const, tmem + (uint32_t)(b * UNIT_COLS + t * COUT), (tile + t) * kTileM,
-                                         q, half, lane);
+                                         q, half, lane, stage_base + (warp - 2) * kStageWarpBytes);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[b]);
         }
+        if (lane == 0) bulk_wait_all();        // this warp's staged output boxes have been written
     }
     __syncthreads();
     if (threadIdx.x == 0 && *fail) {
@@ -684,10 +751,25 @@ bool make_map(CUtensorMap *m, const void *base, uint64_t d0, uint64_t d1, uint64
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// BF16 output rows [rows][ld] seen as a 2-D tensor {cols, rows}, box {box_cols, 32},
+// swizzled to match the epilogue's staging layout (64- or 32-byte rows).
+bool make_out_map(CUtensorMap *m, const void *base, uint64_t cols, uint64_t rows, uint64_t ld, uint32_t box_cols) {
+    EncodeTiledFn enc = encode_fn();
+    if (!enc || (box_cols != 16 && box_cols != 32)) return false;
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {ld * 2};
+    const cuuint32_t box[2] = {box_cols, 32u};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, box_cols == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B,
+               CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int COUT, int STAGES, int MODE, int CL, int MT, bool RESW = false>
 int launch_tc(const TcParams &p, cudaStream_t st) {
-    constexpr int smem = RESW ? STAGES * kTileM * kBlockK * 2 + kMaxResK * COUT * kBlockK * 2 + 1024
-                              : STAGES * (MT * kTileM + COUT) * kBlockK * 2 + 1024;
+    constexpr int stage_out = EpiShape<COUT>::EW * 32 * EpiShape<COUT>::CH * 2;      // output staging
+    constexpr int smem = (RESW ? STAGES * kTileM * kBlockK * 2 + kMaxResK * COUT * kBlockK * 2
+                               : STAGES * (MT * kTileM + COUT) * kBlockK * 2) + stage_out + 1024;
     constexpr int threads = 32 * (2 + EpiShape<COUT>::EW);
     auto kern = k_conv_tc<COUT, STAGES, MODE, CL, MT, RESW>;
     static bool configured = false;       // the attribute is per function; setting it twice is harmless
@@ -754,7 +836,7 @@ int launch_mode(int cout_pad, bool mt2, const TcParams &p, cudaStream_t st) {
             else return launch_tc<16, 8, MODE, 1, 1>(p, st);
         case 64:
             // 64-output layers with at most kMaxResK K blocks keep their weights resident
-            if (p.taps * p.c_blocks <= kMaxResK) return launch_tc<64, 9, MODE, 1, 1, true>(p, st);
+            if (p.taps * p.c_blocks <= kMaxResK) return launch_tc<64, 8, MODE, 1, 1, true>(p, st);
             return launch_tc<64, 8, MODE, 1, 1>(p, st);
         case 128: return mt2 ? launch_tc<128, 4, MODE, 2, 2>(p, st) : launch_tc<128, 6, MODE, 2, 1>(p, st);
         case 256: return launch_tc<256, 4, MODE, 2, 1>(p, st);
@@ -814,6 +896,13 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     p.res = reinterpret_cast<const __nv_bfloat16 *>(d.res_dev);
     p.out = d.out_dev;
     p.out_ld = d.out_ld;
+    // staged TMA stores of BF16 rows (chunks of 16 or 32 columns: outputs of 64 or more)
+    p.out_tma = 0;
+    if (d.epilogue >= 1 && d.cout_pad >= 64 && ((uintptr_t)d.out_dev & 15) == 0) {
+        const uint32_t ch = d.cout_pad == 256 ? 32u : 16u;
+        if (make_out_map(&p.out_map, d.out_dev, (uint64_t)d.cout, (uint64_t)d.n_samples * d.L, (uint64_t)d.out_ld, ch))
+            p.out_tma = 1;
+    }
     p.film_ld = d.film_ld > 0 ? d.film_ld : 2 * d.cout;
     p.err = d.err_dev;
     if (p.M == 0) return cudaSuccess;
