@@ -62,7 +62,8 @@ enum { kEpiF32 = 0, kEpiBF16 = 1, kEpiGN = 2 };
 struct TcParams {
     CUtensorMap a0, a1, w, w_half;    // w_half: box of half the output rows (cluster multicast)
     CUtensorMap out_map;              // BF16 output rows, box {CH, 32} (staged TMA stores; out_tma)
-    int out_tma;
+    CUtensorMap res_map;              // BF16 residual rows, the same boxes (TMA loads; res_tma)
+    int out_tma, res_tma;
     int M, L, taps, pad, c0_blocks, c_blocks;
     int cout, rows_per_sample;
     float gn_eps;
@@ -236,6 +237,14 @@ __device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bu
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
 template <int CH>
 __device__ __forceinline__ uint32_t stage_offset(int row, int unit) {
     static_assert(CH == 16 || CH == 32, "32- or 64-byte rows");
@@ -346,9 +355,11 @@ struct EpiShape {
     static constexpr int CH = EW == 16 ? 16 : (PART < 32 ? PART : 32);
 };
 
+// stage: this warp's staging buffer; res_bar / res_phase: its mbarrier for the
+// residual box loads and the number of loads it has completed so far.
 template <int COUT, int MODE>
 __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, uint32_t tmem, int m0, int q,
-                                         int part, int lane, uint8_t *stage) {
+                                         int part, int lane, uint8_t *stage, uint64_t *res_bar, int &res_phase) {
     constexpr int HALF = EpiShape<COUT>::PART;
     constexpr int CH = EpiShape<COUT>::CH;
     const int gm = m0 + q * 32 + lane;
@@ -398,7 +409,16 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
                     }
                 }
             }
-            if (res) {
+            const bool res_box = p.res && p.res_tma;
+            if (res_box) {
+                // the residual box of the warp's 32 rows lands in the staging buffer
+                // (once the previous output box has left it) while the statistics run
+                if (lane == 0) {
+                    bulk_wait_read_all();
+                    mbar_expect_tx(res_bar, 32 * CH * 2);
+                    tma_load_2d(stage, &p.res_map, res_bar, c0, m0 + q * 32);
+                }
+            } else if (res) {
 #pragma unroll
                 for (int j = 0; j < CH / 8; ++j) rr[j] = *reinterpret_cast<const uint4 *>(res + c0 + 8 * j);
             }
@@ -439,7 +459,14 @@ __device__ __forceinline__ void epilogue(const TcParams &p, const EpiConst &kc, 
                 if (film) y = __ffma2_rn(y, fsc[i], fsh[i]);
                 w[i] = y;
             }
-            if (res) {
+            if (res_box) {
+                if (!mbar_wait(res_bar, res_phase & 1)) record_failure(p.err, 7);
+                ++res_phase;
+#pragma unroll
+                for (int j = 0; j < CH / 8; ++j) rr[j] = *reinterpret_cast<const uint4 *>(stage + stage_offset<CH>(lane, j));
+                __syncwarp();                  // every lane has its residual row before the buffer is rewritten
+            }
+            if (res_box || res) {
 #pragma unroll
                 for (int j = 0; j < CH / 8; ++j) {
                     const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&rr[j]);
@@ -543,6 +570,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], accf_bar[2], acce_bar[2], wfull_bar;
+    __shared__ __align__(8) uint64_t res_bar[kEpiWarps];     // residual box loads, one per epilogue warp
     __shared__ uint32_t tmem_slot;
     __shared__ int s_issued, s_consumed, s_fail, s_wissued;
     __shared__ EpiConst s_const;
@@ -570,6 +598,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
             mbar_init(&acce_bar[b], kEpiWarps);
         }
         mbar_init(&wfull_bar, 1);
+        for (int w = 0; w < kEpiWarps; ++w) mbar_init(&res_bar[w], 1);
         s_issued = 0;
         s_consumed = 0;
         s_fail = 0;
@@ -681,7 +710,7 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
             s_const.beta[c] = p.beta ? p.beta[c] : 0.f;
         }
         asm volatile("bar.sync 1, %0;" ::"n"(32 * kEpiWarps) : "memory");     // epilogue warps only
-        int it = 0;
+        int it = 0, res_phase = 0;
         for (int u = unit0; u < n_units; u += unit_step, ++it) {
             const int tile = (CL * u + crank) * MT;
             const int b = NBUF == 2 ? (it & 1) : 0;
@@ -697,7 +726,8 @@ __global__ void __launch_bounds__(32 * (2 + EpiShape<COUT>::EW), 1) k_conv_tc(co
 #pragma unroll 1
                 for (int t = 0; t < MT; ++t)
                     epilogue<COUT, MODE>(p, s_const, tmem + (uint32_t)(b * UNIT_COLS + t * COUT), (tile + t) * kTileM,
-                                         q, half, lane, stage_base + (warp - 2) * kStageWarpBytes);
+                                         q, half, lane, stage_base + (warp - 2) * kStageWarpBytes, &res_bar[warp - 2],
+                                         res_phase);
             tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&acce_bar[b]);
@@ -898,10 +928,17 @@ int nn_conv_tc(const DseedConvTc &d, cudaStream_t st) {
     p.out_ld = d.out_ld;
     // staged TMA stores of BF16 rows (chunks of 16 or 32 columns: outputs of 64 or more)
     p.out_tma = 0;
+    p.res_tma = 0;
     if (d.epilogue >= 1 && d.cout_pad >= 64 && ((uintptr_t)d.out_dev & 15) == 0) {
         const uint32_t ch = d.cout_pad == 256 ? 32u : 16u;
-        if (make_out_map(&p.out_map, d.out_dev, (uint64_t)d.cout, (uint64_t)d.n_samples * d.L, (uint64_t)d.out_ld, ch))
+        const uint64_t rows = (uint64_t)d.n_samples * d.L;
+        if (make_out_map(&p.out_map, d.out_dev, (uint64_t)d.cout, rows, (uint64_t)d.out_ld, ch)) {
             p.out_tma = 1;
+            // the residual [rows][cout_pad] in the same boxes, read through the same staging buffer
+            if (d.epilogue == kEpiGN && d.res_dev && ((uintptr_t)d.res_dev & 15) == 0 &&
+                make_out_map(&p.res_map, d.res_dev, (uint64_t)d.cout_pad, rows, (uint64_t)d.cout_pad, ch))
+                p.res_tma = 1;
+        }
     }
     p.film_ld = d.film_ld > 0 ? d.film_ld : 2 * d.cout;
     p.err = d.err_dev;
