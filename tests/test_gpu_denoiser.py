@@ -140,7 +140,9 @@ def test_ddim_sampling_paths_agree(gpu_lib, net):
 
 def test_gemm_kernels_against_float64():
     rng = np.random.default_rng(4)
-    for (M, N, K, ta, tb) in [(37, 65, 29, 0, 0), (130, 3, 71, 1, 0), (5, 200, 16, 0, 1), (64, 64, 64, 1, 1)]:
+    # the last three have few 64 x 64 output tiles and a long K: the 32 x 32 tiling
+    for (M, N, K, ta, tb) in [(37, 65, 29, 0, 0), (130, 3, 71, 1, 0), (5, 200, 16, 0, 1), (64, 64, 64, 1, 1),
+                              (512, 128, 2048, 0, 1), (100, 70, 300, 1, 0), (257, 33, 1031, 1, 1)]:
         A = rng.normal(size=(K, M) if ta else (M, K)).astype(np.float32)
         Bm = rng.normal(size=(N, K) if tb else (K, N)).astype(np.float32)
         C0 = rng.normal(size=(M, N)).astype(np.float32)
