@@ -9,6 +9,8 @@
 // plan computes for it, whichever requests share its rounds.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "device.cuh"
 
 namespace dseed {
@@ -23,9 +25,15 @@ constexpr int kServeWarps = 4;
 
 // Resident blocks the registers are sized for: five (96 registers) for T <= 32
 // without the swept check, whose round fits them with a few spilled bytes;
-// four (128) otherwise, where the round's bookkeeping would spill more.
-template <int TPL, bool SWEEP>
-__global__ void __launch_bounds__(kServeWarps * 32, (TPL == 1 && !SWEEP) ? DSEED_SERVE_MINBLOCKS_T32 : DSEED_SERVE_MINBLOCKS)
+// four (128) otherwise, where the round's bookkeeping would spill more; with the
+// self-collision term (its pair loops and the per-lane frame transforms in shared
+// memory) shared memory limits the blocks, so the registers are left free.
+constexpr int serve_min_blocks(int tpl, bool self, bool sweep) {
+    return self ? 1 : (tpl == 1 && !sweep) ? DSEED_SERVE_MINBLOCKS_T32 : DSEED_SERVE_MINBLOCKS;
+}
+
+template <int TPL, bool SELF, bool SWEEP>
+__global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, SWEEP))
     k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
             float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
     constexpr int NPL = 7 * TPL;
@@ -48,7 +56,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, (TPL == 1 && !SWEEP) ? DSEED
     float *g_ga = R + L.ga + (size_t)s * n, *g_dd = R + L.dd + (size_t)s * n;
     float *S_ = R + L.hs + (size_t)s * m * n, *Y_ = R + L.hy + (size_t)s * m * n;
     float *sc = R + L.sc + (size_t)s * 16;
-    WarpSmem ws = carve(smem + wid * warp_smem_floats(32 * TPL), T);
+    WarpSmem ws = carve(smem + wid * warp_smem_floats(32 * TPL, SELF), T);
     float *xt = ws.xs + kPad * 7;
     SceneView sv;
     {
@@ -89,7 +97,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, (TPL == 1 && !SWEEP) ? DSEED
     const Goal G = make_goal(R + L.goal);
     __syncwarp();
     for (int it = 0; it < E.iters_round; ++it) {
-        const EvalOut o = warp_eval<TPL, MODE_GRAD, false, SWEEP>(rb, kc, sv, T, G, ws, false);
+        const EvalOut o = warp_eval<TPL, MODE_GRAD, SELF, SWEEP>(rb, kc, sv, T, G, ws, false);
         __syncwarp();
         lbfgs_update<NPL>(ko, n, st, xt, ws.gs, o.cost, ws, S_, Y_, xt);
     }
@@ -115,7 +123,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, (TPL == 1 && !SWEEP) ? DSEED
     // last round: success test of the accepted point, outputs
     for (int e = lane; e < n; e += 32) xt[e] = ws.xa[e];
     __syncwarp();
-    const EvalOut o = warp_eval<TPL, MODE_EVAL, false, SWEEP>(rb, kc, sv, T, G, ws, false);
+    const EvalOut o = warp_eval<TPL, MODE_EVAL, SELF, SWEEP>(rb, kc, sv, T, G, ws, false);
     for (int e = lane; e < n; e += 32) g_xa[e] = ws.xa[e];
     const bool ok = o.min_clear >= 0.0f && o.pos_err < delta_t && o.rot_err < delta_r && o.lim_viol == 0.0f;
     if (lane == 0) {
@@ -132,7 +140,8 @@ int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_
                  const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st) {
     if (n_entries == 0 || total_warps == 0) return cudaSuccess;
     const unsigned blocks = (unsigned)((total_warps + kServeWarps - 1) / kServeWarps);
-    const size_t smem = (size_t)kServeWarps * warp_smem_floats(32 * tpl) * sizeof(float);
+    const bool self = kc.w_s > 0.f;
+    const size_t smem = (size_t)kServeWarps * warp_smem_floats(32 * tpl, self) * sizeof(float);
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -141,14 +150,17 @@ int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_
         kern<<<blocks, kServeWarps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
         return (int)cudaGetLastError();
     };
-    if (kc.n_sweep > 0) {
-        if (tpl == 1) return go(k_serve<1, true>);
-        if (tpl == 2) return go(k_serve<2, true>);
-        return go(k_serve<4, true>);
-    }
-    if (tpl == 1) return go(k_serve<1, false>);
-    if (tpl == 2) return go(k_serve<2, false>);
-    return go(k_serve<4, false>);
+    // variants: waypoints per lane x self-collision term x swept check
+    auto by_t = [&](auto self_c, auto sweep_c) {
+        constexpr bool kSelf = decltype(self_c)::value, kSweep = decltype(sweep_c)::value;
+        if (tpl == 1) return go(k_serve<1, kSelf, kSweep>);
+        if (tpl == 2) return go(k_serve<2, kSelf, kSweep>);
+        return go(k_serve<4, kSelf, kSweep>);
+    };
+    using T_ = std::true_type;
+    using F_ = std::false_type;
+    const bool sweep = kc.n_sweep > 0;
+    return self ? (sweep ? by_t(T_{}, T_{}) : by_t(T_{}, F_{})) : (sweep ? by_t(F_{}, T_{}) : by_t(F_{}, F_{}));
 }
 
 }  // namespace dseed

@@ -375,7 +375,6 @@ extern "C" int dseed_server_create(const DseedRobot *robot, const DseedServerDes
     if (desc->max_requests < 1 || desc->round_iters < 1) return set_error(DSEED_EINVAL, "max_requests and round_iters must be >= 1");
     int r = dseed::check_cost_opt(desc->cost, desc->opt, desc->delta_t, desc->delta_r);
     if (r) return r;
-    if (desc->cost.w_self != 0.f) return set_error(DSEED_EINVAL, "the server does not evaluate the self-collision cost");
     if (reinterpret_cast<uintptr_t>(arena_dev) % 256 != 0) return set_error(DSEED_EINVAL, "arena not 256-byte aligned");
     const size_t table_bytes = round_up(sizeof(dseed::ServeEntry) * kClasses * (size_t)desc->max_requests);
     if (desc->arena_bytes < table_bytes + kUnit)

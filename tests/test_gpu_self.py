@@ -1,7 +1,7 @@
 """GPU parity of the self-collision term (C_self) against the FP64 oracle:
 the checked-pair set, a two-sphere closed form, cost and gradient on
 trajectories with self contact (one and two waypoints per lane), the success
-metrics, and plans; the serving loop refuses the term."""
+metrics, plans, and the serving loop with the term."""
 import dataclasses
 
 import numpy as np
@@ -152,8 +152,38 @@ def test_plan_agrees_with_oracle(gpu_lib, tiny32):
         assert np.array_equal(ok[p][far], want[far])
 
 
-def test_server_refuses_self_term(gpu_lib, tiny):
-    wl, _ = tiny
+def test_server_serves_self_term(gpu_lib, tiny):
+    """Served requests with the self-collision term compute what the one-shot
+    plan computes for them (one and two waypoints per lane, rounds of 7 of 30
+    iterations), and the term is active on them."""
+    wl, orc = tiny
     from paper_2410_16727_gb300 import serving as SV
-    with pytest.raises(B.DseedError, match="self-collision"):
-        SV.Server(wl.robot, 1 << 26, cost=COST)
+    opt = I.OptParams(iters=30)
+    planner = api.Planner(wl.robot, COST, opt)
+    planner.set_scenes(wl.cuboids, wl.grids)
+    sv = SV.Server(wl.robot, 256 << 20, max_requests=16, round_iters=7, cost=COST, opt=opt)
+    for s, (c, g) in enumerate(zip(wl.cuboids, wl.grids)):
+        sv.add_scene(s, c, g)
+    rng = np.random.default_rng(11)
+    cases, tickets = [], []
+    for p, (S, T) in enumerate([(8, 32), (4, 48), (6, 64)]):
+        x = I.random_trajectories(rng, wl.q_start[p], S, T, wl.robot.limits, spread=1.5).astype(np.float32)
+        cases.append((p, x))
+        tickets.append(sv.submit(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], x))
+    sv.drain(tickets)
+    n_self = 0
+    for t, (p, x) in zip(tickets, cases):
+        assert sv.poll(t)[0] == 2
+        got = sv.result(t)
+        batch = planner.batch(wl.q_start[p:p + 1], wl.goal[p:p + 1], np.array([wl.scene_of_problem[p]], np.int32),
+                              x.shape[0], x.shape[1])
+        want = {k: to_np(v)[0] for k, v in planner.plan(batch, x[None]).items()}
+        np.testing.assert_allclose(got["traj"].numpy(), want["traj"], rtol=1e-5, atol=1e-5)
+        np.testing.assert_allclose(got["cost"].numpy(), want["cost"], rtol=1e-5, atol=1e-5)
+        assert (got["success"].numpy() == want["success"]).all()
+        assert int(got["best"][0]) == int(want["best"])
+        # the seeds start with an active collision term (world and self)
+        _, _, terms = orc.cost(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], x, grad=True, terms=True)
+        n_self += int((terms[:, 0] > 0).sum())
+    assert n_self > 0
+    sv.close()
