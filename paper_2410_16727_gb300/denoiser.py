@@ -329,8 +329,9 @@ class Denoiser:
         t1 = self.mish(self.linear(te, "t.l1", tape), tape)
         return self.linear(t1, "t.l2", tape)
 
-    def problem_embed(self, qs, qg, goal, occ, tape):
-        """Problem MLP (q_start, q_goal, goal pose) and occupancy encoder -> [P][p_dim], [P][o_dim]."""
+    def problem_embed(self, qs, qg, goal, occ, tape, last_linear=None):
+        """Problem MLP (q_start, q_goal, goal pose) and occupancy encoder -> [P][p_dim], [P][o_dim].
+        last_linear(x, R) (inference only) replaces the encoder's flattened last linear."""
         s = self.spec
         N = qs.shape[0]
         pin = self.concat([qs, qg, goal], N, tape)
@@ -340,7 +341,10 @@ class Denoiser:
         o1 = self.mish(self.linear(o0, "o.c1", tape, R=N * s.occ_g1 ** 3), tape)     # [N*8^3][c1]
         o2 = self.gather(o1, self.map2, N, s.occ_g1 ** 3 * s.occ_c1, tape)           # [N][4^3][2^3 c1]
         o3 = self.mish(self.linear(o2, "o.c2", tape, R=N * s.occ_g2 ** 3), tape)     # [N*4^3][c2]
-        o4 = self.linear(o3, "o.l", tape, R=N)                                       # flattened per sample
+        if last_linear is not None:
+            o4 = last_linear(o3, N)
+        else:
+            o4 = self.linear(o3, "o.l", tape, R=N)                                   # flattened per sample
         return p2, o4
 
     def condition(self, k, qs, qg, goal, occ, tape):
@@ -517,6 +521,10 @@ class Denoiser:
         for name in ("fin.c",):
             pk[name] = packed(name)
             pk[name + ".b"] = f32(name + ".b")
+        # the occupancy encoder's flattened linear [out][in] (in a multiple of 64)
+        o_out, o_in = self.offsets["o.l.w"][1]
+        pk["o.l"] = self.P("o.l.w").view(o_out, o_in).to(torch.bfloat16).contiguous()
+        pk["o.l.b"] = f32("o.l.b")
         for name in ("down1", "down2"):
             # stride-2, 3-tap convolution as a 2-tap one over row pairs [x(2o), x(2o+1)]:
             # tap 0 (the pair o - 1) carries w0 on its second row, tap 1 (pair o) w1, w2
@@ -597,6 +605,18 @@ class Denoiser:
                   res=r, **gn)
         return out
 
+    def _tc_linear(self, W, x, R, name):
+        """x FP32 [R][in] -> FP32 [R][out] on the tensor cores (BF16 operands, FP32
+        accumulation): the occupancy encoder's flattened 2048 -> 128 linear, a
+        few hundred rows with a long K."""
+        out_f, in_f = W[name].shape
+        xb = torch.empty((R, in_f), dtype=torch.bfloat16, device=self.dev)
+        _nn("to_bf16", x, xb, R * in_f)
+        y = torch.empty((R, out_f), dtype=torch.float32, device=self.dev)
+        B.conv_tc(xb, W[name], y, n_samples=R, L=1, cout=out_f, bias=W[name + ".b"], epilogue=B.EPI_F32,
+                  err=self._tc_err)
+        return y
+
     def _tc_down(self, W, x, N, L, name, cout):
         """Stride-2 convolution (k = 3, pad 1) as a 2-tap convolution of the
         input's row pairs (the input viewed as [N][L/2][2 C]): no im2col buffer."""
@@ -668,7 +688,7 @@ class Denoiser:
         s = self.spec
         W = self._tc_weights()
         P = qs.shape[0]
-        p2, o4 = self.problem_embed(qs, qg, goal, occ, None)
+        p2, o4 = self.problem_embed(qs, qg, goal, occ, None, last_linear=lambda x, R: self._tc_linear(W, x, R, "o.l"))
         po = self.mish(self.concat([p2, o4], P, None), None)
         F = torch.empty((P, W["film_rows"]), dtype=torch.float32, device=self.dev)
         K = s.cond_dim - s.t_dim
