@@ -607,7 +607,7 @@ def run_learned(args) -> dict:
                        "seconds": round(time.perf_counter() - t0, 1), "loss": [round(l, 4) for _, l in losses]}
     net_fk = None
     if args.learned_fk:
-        # the same data and schedule, the error measured on the robot's sphere centres (Eq. 2)
+        # the same data and schedule, the error measured on points on the robot's sphere surfaces (Eq. 2)
         net_fk = DN.Denoiser(NS.NetSpec(), seed=0)
         t0 = time.perf_counter()
         losses = L.train(net_fk, data, args.learned_steps, batch=256, lr=3e-4,

@@ -20,12 +20,14 @@ of eps-free DDIM, the descent direction against central differences of the cost
 in the diffused space, the per-entry cap, and the guided-step count of the
 schedule).
 
-Also Eq. 2's loss measured on the robot (fk_mse): the drawn and the predicted
-noise are decoded to the joint configurations they stand for and placed by a
-forward-kinematics chain of 4x4 modified-DH products written here (pins in
-tests/test_oracle_fk_loss.py: zero at pred = eps, a base-joint rotation's closed
-form, per-sample weights, sphere centres against the C oracle's, central
-differences).
+Also Eq. 2's loss measured on the robot (fk_mse, Sec. 4.3: points sampled on
+the robot's geometry across all links): the drawn and the predicted noise are
+decoded to the joint configurations they stand for, and the points on the
+collision spheres' surfaces at the six axis directions of each sphere's frame
+are placed by a forward-kinematics chain of 4x4 modified-DH products written
+here (pins in tests/test_oracle_fk_loss.py: zero at pred = eps, a base-joint
+rotation's closed form, per-sample weights, the points against the C oracle's
+chain, central differences).
 """
 from __future__ import annotations
 
@@ -163,11 +165,26 @@ def ddim_step(xk, eps, ab_k, ab_prev, clip):
 
 # ------------------------------------------------------------------ Eq. 2 on the robot
 
-def robot_points(robot, q: torch.Tensor) -> torch.Tensor:
-    """Collision-sphere centres [..., N_s, 3] of joint configurations q [..., 7]:
-    frame i = frame i-1 RotX(alpha_i) TransX(a_i) RotZ(q_i + offset_i) TransZ(d_i)
-    (modified DH, rows (a, d, alpha, offset) of robot.dh; the eighth row, the
-    flange, has no joint), sphere k at its offset in frame sph_frame[k]."""
+# The six axis directions of a sphere's frame, in this order for every sphere.
+SURFACE_DIRS = np.array([[1, 0, 0], [-1, 0, 0], [0, 1, 0], [0, -1, 0], [0, 0, 1], [0, 0, -1]], np.float64)
+
+
+def surface_offsets(robot):
+    """Frame offsets [6 N_s][3] and frames [6 N_s] of the points of Eq. 2: for
+    sphere k (offset o_k, radius r_k in frame sph_frame[k]) the points
+    o_k + r_k u for the six axis directions u, sphere-major."""
+    o = np.asarray(robot.sph_o, np.float64)
+    r = np.asarray(robot.sph_r, np.float64)
+    pts = (o[:, None, :] + r[:, None, None] * SURFACE_DIRS[None]).reshape(-1, 3)
+    return pts, np.repeat(np.asarray(robot.sph_frame, np.int64), len(SURFACE_DIRS))
+
+
+def robot_points(robot, q: torch.Tensor, offsets=None, frames=None) -> torch.Tensor:
+    """Points [..., N_p, 3] of joint configurations q [..., 7]: frame i = frame
+    i-1 RotX(alpha_i) TransX(a_i) RotZ(q_i + offset_i) TransZ(d_i) (modified DH,
+    rows (a, d, alpha, offset) of robot.dh; the eighth row, the flange, has no
+    joint), point k at offsets[k] in frame frames[k] (default: the collision
+    spheres' centres)."""
     dh = torch.as_tensor(np.asarray(robot.dh, np.float64))
     lead = q.shape[:-1]
     one = torch.ones(lead, dtype=DT)
@@ -176,7 +193,7 @@ def robot_points(robot, q: torch.Tensor) -> torch.Tensor:
     def mat(rows):
         return torch.stack([torch.stack(r, -1) for r in rows], -2)
 
-    frames = [torch.eye(4, dtype=DT).expand(*lead, 4, 4)]
+    chain = [torch.eye(4, dtype=DT).expand(*lead, 4, 4)]
     for i in range(8):
         a, d, al, off = (float(v) for v in dh[i])
         th = (q[..., i] if i < 7 else zero) + off
@@ -187,12 +204,12 @@ def robot_points(robot, q: torch.Tensor) -> torch.Tensor:
         rz = mat([[torch.cos(th), -torch.sin(th), zero, zero], [torch.sin(th), torch.cos(th), zero, zero],
                   [zero, zero, one, zero], [zero, zero, zero, one]])
         tz = mat([[one, zero, zero, zero], [zero, one, zero, zero], [zero, zero, one, d * one], [zero, zero, zero, one]])
-        frames.append(frames[-1] @ rx @ tx @ rz @ tz)
-    F = torch.stack(frames, -3)                                           # [..., 9, 4, 4]
-    o = torch.as_tensor(np.asarray(robot.sph_o, np.float64))
-    oh = torch.cat([o, torch.ones(o.shape[0], 1, dtype=DT)], 1)           # [N_s, 4]
-    fr = torch.as_tensor(np.asarray(robot.sph_frame, np.int64))
-    Fk = F[..., fr, :, :]                                                 # [..., N_s, 4, 4]
+        chain.append(chain[-1] @ rx @ tx @ rz @ tz)
+    F = torch.stack(chain, -3)                                            # [..., 9, 4, 4]
+    o = torch.as_tensor(np.asarray(robot.sph_o if offsets is None else offsets, np.float64))
+    oh = torch.cat([o, torch.ones(o.shape[0], 1, dtype=DT)], 1)           # [N_p, 4]
+    fr = torch.as_tensor(np.asarray(robot.sph_frame if frames is None else frames, np.int64))
+    Fk = F[..., fr, :, :]                                                 # [..., N_p, 4, 4]
     return (Fk @ oh[..., None])[..., :3, 0]
 
 
@@ -206,16 +223,17 @@ def decode(robot, lin, v, res_scale: float) -> torch.Tensor:
 
 
 def fk_mse(robot, lin, eps, pred, res_scale: float, weights=None):
-    """Eq. 2 measured on the robot: with c_k(q) the sphere centres,
-    loss = sum_n w_n sum_{t,k} |c_k(q(pred_nt)) - c_k(q(eps_nt))|^2 / (N T N_s 3).
+    """Eq. 2 measured on the robot: with c_k(q) the points of surface_offsets,
+    loss = sum_n w_n sum_{t,k} |c_k(q(pred_nt)) - c_k(q(eps_nt))|^2 / (N T N_p 3).
     lin, eps, pred [N][T][7]; returns (loss, dloss/dpred [N][T][7])."""
     t = lambda a: torch.as_tensor(np.asarray(a), dtype=DT)
     lin, eps = t(lin), t(eps)
     pr = t(pred).clone().requires_grad_(True)
     N = lin.shape[0]
     w = torch.ones(N, dtype=DT) if weights is None else t(weights)
-    cl = robot_points(robot, decode(robot, lin, eps, res_scale))
-    cp = robot_points(robot, decode(robot, lin, pr, res_scale))
+    offs, frs = surface_offsets(robot)
+    cl = robot_points(robot, decode(robot, lin, eps, res_scale), offs, frs)
+    cp = robot_points(robot, decode(robot, lin, pr, res_scale), offs, frs)
     loss = (w.view(-1, 1, 1, 1) * (cp - cl) ** 2).sum() / cp.numel()
     loss.backward()
     return float(loss.detach()), pr.grad.detach().numpy()

@@ -176,13 +176,14 @@ int launch_fk(const KRobot &rb, const float *q, int N, float *pose, float *spher
 // noise pred stand for the joint configurations q(v) = mid + half (lin + v / res)
 // (lin: the normalised straight start-goal path; mid, half: centre and
 // half-width of each joint's limits); both are placed by the kinematic chain
-// and the squared distances between the predicted and the drawn sphere
-// centres are summed, weighted per trajectory.  The derivative with respect
-// to pred runs back through the predicted chain by Jacobian-transpose
-// accumulation: each sphere pushes with g = dloss/dc at its predicted centre,
-// joint i receives z_i . (M - M_<i) - (z_i x p_i) . (F - F_<i) with F, M the
-// sum of the pushes and of their moments about the origin (the _<i parts are
-// the spheres met before frame i), times half / res.
+// and the squared distances between the predicted and the drawn points on the
+// robot (on each collision sphere's surface, at the six axis directions of its
+// frame: c_k + r_k u in frame coordinates) are summed, weighted per trajectory.
+// The derivative with respect to pred runs back through the predicted chain by
+// Jacobian-transpose accumulation: each point pushes with g = dloss/dc at its
+// predicted position, joint i receives z_i . (M - M_<i) - (z_i x p_i) . (F -
+// F_<i) with F, M the sum of the pushes and of their moments about the origin
+// (the _<i parts are the points met before frame i), times half / res.
 __global__ void __launch_bounds__(256) k_fk_mse(const __grid_constant__ KRobot rb, const float *__restrict__ lin,
                                                 const float *__restrict__ eps, const float *__restrict__ pred,
                                                 const float *__restrict__ w, int N, int T, float inv_res,
@@ -222,21 +223,28 @@ __global__ void __launch_bounds__(256) k_fk_mse(const __grid_constant__ KRobot r
                 wj[j][2] = Rp[2] * pp[1] - Rp[5] * pp[0];
                 bj[j] = (zj[j][0] * Mx + zj[j][1] * My + zj[j][2] * Mz) - (wj[j][0] * Fx + wj[j][1] * Fy + wj[j][2] * Fz);
             }
-            for (int k = rb.frame_begin[L - 1]; k < rb.frame_begin[L]; ++k) {
-                const float4 s = rb.sph[k];
-                const float cx = fmaf(Rp[0], s.x, fmaf(Rp[1], s.y, fmaf(Rp[2], s.z, pp[0])));
-                const float cy = fmaf(Rp[3], s.x, fmaf(Rp[4], s.y, fmaf(Rp[5], s.z, pp[1])));
-                const float cz = fmaf(Rp[6], s.x, fmaf(Rp[7], s.y, fmaf(Rp[8], s.z, pp[2])));
-                const float dx = cx - fmaf(Rl[0], s.x, fmaf(Rl[1], s.y, fmaf(Rl[2], s.z, pl[0])));
-                const float dy = cy - fmaf(Rl[3], s.x, fmaf(Rl[4], s.y, fmaf(Rl[5], s.z, pl[1])));
-                const float dz = cz - fmaf(Rl[6], s.x, fmaf(Rl[7], s.y, fmaf(Rl[8], s.z, pl[2])));
-                dsum += dx * dx + dy * dy + dz * dz;
-                const float gx = gs * dx, gy = gs * dy, gz = gs * dz;
-                Fx += gx; Fy += gy; Fz += gz;
-                Mx += cy * gz - cz * gy;
-                My += cz * gx - cx * gz;
-                Mz += cx * gy - cy * gx;
-            }
+            for (int k = rb.frame_begin[L - 1]; k < rb.frame_begin[L]; ++k)
+#pragma unroll 1
+                for (int u = 0; u < 6; ++u) {
+                    // the point on sphere k's surface along axis u / 2 of its frame, sign by u % 2
+                    const float4 sk = rb.sph[k];
+                    const float sgn = (u & 1) ? -sk.w : sk.w;
+                    const float ox = sk.x + (u >> 1 == 0 ? sgn : 0.f);
+                    const float oy = sk.y + (u >> 1 == 1 ? sgn : 0.f);
+                    const float oz = sk.z + (u >> 1 == 2 ? sgn : 0.f);
+                    const float cx = fmaf(Rp[0], ox, fmaf(Rp[1], oy, fmaf(Rp[2], oz, pp[0])));
+                    const float cy = fmaf(Rp[3], ox, fmaf(Rp[4], oy, fmaf(Rp[5], oz, pp[1])));
+                    const float cz = fmaf(Rp[6], ox, fmaf(Rp[7], oy, fmaf(Rp[8], oz, pp[2])));
+                    const float dx = cx - fmaf(Rl[0], ox, fmaf(Rl[1], oy, fmaf(Rl[2], oz, pl[0])));
+                    const float dy = cy - fmaf(Rl[3], ox, fmaf(Rl[4], oy, fmaf(Rl[5], oz, pl[1])));
+                    const float dz = cz - fmaf(Rl[6], ox, fmaf(Rl[7], oy, fmaf(Rl[8], oz, pl[2])));
+                    dsum += dx * dx + dy * dy + dz * dz;
+                    const float gx = gs * dx, gy = gs * dy, gz = gs * dz;
+                    Fx += gx; Fy += gy; Fz += gz;
+                    Mx += cy * gz - cz * gy;
+                    My += cz * gx - cx * gz;
+                    Mz += cx * gy - cy * gx;
+                }
         }
         acc = fmaf(wn, dsum, acc);
 #pragma unroll
@@ -258,7 +266,7 @@ __global__ void __launch_bounds__(256) k_fk_mse(const __grid_constant__ KRobot r
 
 int launch_fk_mse(const KRobot &rb, const float *lin, const float *eps, const float *pred, const float *w, int N,
                   int T, float res_scale, float *dpred, float *loss_partial, int blocks, cudaStream_t st) {
-    const double norm = (double)N * T * rb.n_spheres * 3.0;
+    const double norm = (double)N * T * rb.n_spheres * 6.0 * 3.0;     // six surface points per sphere
     const float inv_norm = norm > 0.0 ? (float)(1.0 / norm) : 0.f;
     k_fk_mse<<<blocks, 256, 0, st>>>(rb, lin, eps, pred, w, N, T, (float)(1.0 / (double)res_scale), inv_norm, dpred,
                                      loss_partial);

@@ -319,7 +319,7 @@ def train(net: DN.Denoiser, data: Dataset, steps: int, batch: int = 256, lr: flo
           log_every: int = 0, weighted: bool = True, graph: bool = True, fk_robot: Optional[B.Robot] = None):
     """DDPM training (Eq. 1 / Eq. 2 weights) with Adam and a cosine learning
     rate; returns the loss curve [(step, loss)].  With fk_robot the error is
-    measured on that robot's sphere centres (Eq. 2), else on the joints (Eq. 1)."""
+    measured on points on that robot's sphere surfaces (Eq. 2), else on the joints (Eq. 1)."""
     g = torch.Generator(device=data.x0.device)
     g.manual_seed(seed)
     M = data.x0.shape[0]

@@ -39,7 +39,7 @@ def test_fk_mse_matches_oracle(gpu_lib, N, T, blocks, weighted):
     assert rel_l2(g, wg) <= 1e-3
     for n in range(0, N, max(1, N // 8)):
         assert rel_l2(g[n], wg[n]) <= 1e-3, n
-    # joint by joint: the wrist columns are 50-2000x smaller than the base's and must hold too
+    # joint by joint: the wrist columns are far smaller than the base's and must hold too
     for j in range(7):
         assert rel_l2(g[..., j], wg[..., j]) <= 1e-3, j
 
