@@ -514,7 +514,16 @@ class Denoiser:
             pk[name + ".c1"] = packed(name + ".c1", cols_pad=64 if first else None)
             pk[name + ".c2"] = packed(name + ".c2")
             if cin != cout:
-                pk[name + ".r"] = packed(name + ".r", cols_pad=64 if first else None)
+                if first:
+                    # the first block's 1x1 residual reads the 5-tap im2col rows of the
+                    # input: its weights sit at the centre tap's columns, zeros elsewhere
+                    co, _, ci = self.offsets[name + ".r.w"][1]
+                    wr = torch.zeros((co, 64), dtype=torch.float32, device=self.dev)
+                    c0 = (s.kernel // 2) * ci
+                    wr[:, c0:c0 + ci] = self.P(name + ".r.w").view(co, ci)
+                    pk[name + ".r"] = wr.to(torch.bfloat16).contiguous()
+                else:
+                    pk[name + ".r"] = packed(name + ".r")
                 pk[name + ".r.b"] = f32(name + ".r.b")
             for t in ("c1.b", "c2.b", "g1.w", "g1.b", "g2.w", "g2.b"):
                 pk[name + "." + t] = f32(name + "." + t)
@@ -649,14 +658,12 @@ class Denoiser:
         W = self._tc_weights()
         cols = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
         _nn("im2col1d", x, N, T, D, s.kernel, 1, s.kernel // 2, T, 64, cols, 1)
-        x64 = torch.empty((N * T, 64), dtype=torch.bfloat16, device=self.dev)
-        _nn("im2col1d", x, N, T, D, 1, 1, 0, T, 64, x64, 1)
         FT, offs = W["film_rows"], W["film_off"]
         fa = (lambda name: film_add[offs[name]:]) if film_add is not None else (lambda name: None)
         blk = lambda srcs, L, name, ci, co, plain=None: self._tc_block(W, srcs, N, L, name, ci, co,
                                                                         film[:, offs[name]:], rows, plain, FT,
                                                                         fa(name))
-        h = blk([None], T, "d1a", D, c1, (cols, x64))
+        h = blk([None], T, "d1a", D, c1, (cols, cols))
         h = blk([h], T, "d1b", c1, c1)
         h, L2 = self._tc_down(W, h, N, T, "down1", c1)
         h = blk([h], L2, "d2a", c1, c2)
