@@ -141,3 +141,53 @@ def device_workload_fns(planner: Planner):
         return planner.fk(q).cpu().numpy()
 
     return clearance, pose
+
+
+def plan_attempts(plan_fn, seed_fn, P: int, n_attempts: int) -> dict:
+    """The attempts loop (Sec. 5.2: up to N_atp attempts, each with a new batch of
+    seeds, until a problem has a successful trajectory).  plan_fn(problems,
+    seeds) plans the problems (a host int64 index array) from seeds
+    [len(problems)][S][T][7] and returns the plan outputs of those problems
+    ("traj", "cost", "success", "best", tensors of any device); seed_fn(attempt,
+    problems) draws the attempt's seeds.  Attempt a plans only the problems no
+    earlier attempt solved.  Returns per problem the best trajectory of the
+    attempt that solved it ("traj" [P][T][7], NaN where none did), its cost,
+    "attempts" (1-based attempt that solved it, 0: none) and "solved"."""
+    if P < 0 or n_attempts < 1:
+        raise ValueError("P must be >= 0 and n_attempts >= 1")
+    todo = np.arange(P, dtype=np.int64)
+    attempts = np.zeros(P, np.int32)
+    traj, cost = None, np.full(P, np.nan, np.float32)
+    for a in range(1, n_attempts + 1):
+        if todo.size == 0:
+            break
+        out = plan_fn(todo, seed_fn(a, todo))
+        best = out["best"].cpu().numpy().astype(np.int64)
+        tr = out["traj"].cpu().numpy()
+        cs = out["cost"].cpu().numpy()
+        if traj is None:
+            traj = np.full((P,) + tr.shape[2:], np.nan, np.float32)
+        ok = best >= 0
+        idx = todo[ok]
+        traj[idx] = tr[np.nonzero(ok)[0], best[ok]]
+        cost[idx] = cs[np.nonzero(ok)[0], best[ok]]
+        attempts[idx] = a
+        todo = todo[~ok]
+    if traj is None:
+        traj = np.zeros((0,), np.float32)
+    return {"traj": traj, "cost": cost, "attempts": attempts, "solved": attempts > 0}
+
+
+def planner_attempts(planner: "Planner", q_start, goal, scene_of_problem, seed_fn, S: int, T: int,
+                     n_attempts: int) -> dict:
+    """plan_attempts with a Planner: each attempt is one dseed_plan_batch of the
+    problems still unsolved (q_start [P][7], goal [P][7], scene_of_problem [P]
+    host arrays)."""
+    q_start, goal = np.asarray(q_start), np.asarray(goal)
+    sc = np.asarray(scene_of_problem, np.int32)
+
+    def plan_fn(problems, seeds):
+        batch = planner.batch(q_start[problems], goal[problems], sc[problems], S, T)
+        return planner.plan(batch, seeds)
+
+    return plan_attempts(plan_fn, seed_fn, int(q_start.shape[0]), n_attempts)
