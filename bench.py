@@ -105,7 +105,7 @@ def parse():
     ap.add_argument("--learned-steps", type=int, default=24000,
                     help="shelf denoiser training steps (batch 256; 6000 leave it under-trained, most visibly with "
                          "Eq. 2's loss measured on the robot)")
-    ap.add_argument("--clutter-steps", type=int, default=6000, help="dense-clutter denoiser training steps (batch 256)")
+    ap.add_argument("--clutter-steps", type=int, default=24000, help="dense-clutter denoiser training steps (batch 256)")
     ap.add_argument("--learned-requests", type=int, default=2000, help="requests of the seeded serving runs")
     ap.add_argument("--no-learned-stress", action="store_true",
                     help="skip the learned proposal on the stress workload and the serving mix")
