@@ -26,9 +26,9 @@
 // weight tile of every stage: each CTA loads one half of it with a multicast
 // TMA copy that lands in both CTAs' shared memory, so the pair reads the weight
 // bytes from L2 once (the weights are most of a wide layer's operand bytes).
-// Each SM still takes in the whole tile, and that intake, not L2, bounds the
-// wide layers: the multicast halves their L2 reads (which the optimiser kernels
-// sharing L2 in a serving loop feel) without changing their own time.  A stage may then be refilled only
+// Each SM still takes in the whole tile; the multicast halves the pair's L2
+// reads (which the optimiser kernels sharing L2 in a serving loop feel) without
+// changing the layer's own time.  A stage may then be refilled only
 // once both CTAs' MMAs have read it: each MMA commit arrives on the stage's
 // empty barrier in both CTAs.  The two CTAs walk the same number of tiles (an
 // odd last tile is paired with a tile past the end, whose rows are read as the
@@ -38,6 +38,17 @@
 // rows of two adjacent tiles in one TMA box and issues both tiles' MMAs against
 // each stage's weight tile, so a weight tile feeds 256 output rows; the two
 // accumulators (2 x 128 columns) stay double-buffered.
+//
+// Resident weights (RESW, 64-output layers of at most 8 K blocks): the layer's
+// whole weight matrix is loaded once per CTA and the ring carries only A tiles.
+//
+// Epilogue memory traffic.  The element-wise chain runs on channel pairs with
+// packed FP32x2 arithmetic.  Each epilogue warp owns 32 output rows (one per
+// lane), so per-lane global accesses would touch 32 rows per instruction:
+// instead the warp writes its rows x one column chunk (BF16) into a swizzled
+// shared-memory buffer and stores it with one TMA box, and the residual rows
+// of the chunk arrive the same way (a TMA box into the same buffer) before the
+// output overwrites it.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
