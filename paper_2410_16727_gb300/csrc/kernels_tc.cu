@@ -206,11 +206,6 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, float (&v)[8]) {
     for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void load8(const float *p, float (&v)[8]) {
-    const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
-    v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-}
-
 __device__ __forceinline__ void store8_bf16(__nv_bfloat16 *p, const float (&v)[8]) {
     uint4 u;
     __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
@@ -220,17 +215,6 @@ __device__ __forceinline__ void store8_bf16(__nv_bfloat16 *p, const float (&v)[8
     u.z = *reinterpret_cast<uint32_t *>(&h2);
     u.w = *reinterpret_cast<uint32_t *>(&h3);
     *reinterpret_cast<uint4 *>(p) = u;
-}
-
-__device__ __forceinline__ void load8_bf16(const __nv_bfloat16 *p, float (&v)[8]) {
-    const uint4 u = *reinterpret_cast<const uint4 *>(p);
-    const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float2 f = __bfloat1622float2(h[i]);
-        v[2 * i] = f.x;
-        v[2 * i + 1] = f.y;
-    }
 }
 
 // Staged output rows: each epilogue warp writes its 32 rows x CH columns (BF16)
@@ -330,16 +314,9 @@ __device__ __forceinline__ void tmem_ld<32>(uint32_t taddr, float (&v)[32]) {
 }
 
 // Mish(x) = x tanh(softplus(x)); with e = exp(x), tanh(log(1 + e)) =
-// ((1 + e)^2 - 1) / ((1 + e)^2 + 1) = n / (n + 2), n = e (e + 2).
-__device__ __forceinline__ float mish_fast(float x) {
-    if (x > 15.f) return x;                   // n / (n + 2) = 1 to FP32 precision
-    const float e = __expf(x);
-    const float n = e * (e + 2.f);
-    return x * __fdividef(n, n + 2.f);
-}
-
-// Mish of a channel pair: the same n / (n + 2) form, with the adds and
-// multiplies packed (exp and the reciprocal stay per element).
+// ((1 + e)^2 - 1) / ((1 + e)^2 + 1) = n / (n + 2), n = e (e + 2).  Here on a
+// channel pair, with the adds and multiplies packed (exp and the reciprocal
+// stay per element).
 __device__ __forceinline__ float2 mish2(float2 x) {
     const float2 e = make_float2(__expf(x.x), __expf(x.y));
     const float2 n = __fmul2_rn(e, __fadd2_rn(e, make_float2(2.f, 2.f)));
