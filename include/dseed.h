@@ -361,7 +361,10 @@ typedef struct {
 /* One planning request.  Host buffers (pinned memory recommended; they must
  * stay valid until the request is done): q_start [7], goal [7], seeds
  * [S][T][7]; outputs traj [S][T][7], cost [S], success [S], best (index of the
- * lowest-cost successful seed or -1). */
+ * lowest-cost successful seed or -1).  When all six array buffers are pinned
+ * (page-locked, so the device can address them), the request's inputs and
+ * outputs move with the other requests' in one batched copy kernel per round
+ * instead of separate copies; any other buffer is copied with cudaMemcpyAsync. */
 typedef struct {
     int scene_id;
     int S, T;                /* S >= 1, 1 <= T <= DSEED_MAX_T */

@@ -127,4 +127,16 @@ struct ServeEntry {
 int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_t, float delta_r, int tpl,
                  const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st);
 
+// One copy of the serving loop's request traffic: `bytes` from src to dst, both
+// addresses the device can dereference (device memory, or pinned host memory
+// through its mapped device address).
+struct IoCopy {
+    const void *src;
+    void *dst;
+    unsigned long long bytes;
+};
+
+// All copies of table_dev [n] in one launch (a block per copy).
+int launch_io_copies(const IoCopy *table_dev, int n, cudaStream_t st);
+
 }  // namespace dseed

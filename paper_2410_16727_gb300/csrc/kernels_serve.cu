@@ -136,6 +136,37 @@ __global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, 
     }
 }
 
+// Request traffic of a serving round (the seeds and problem of each admitted
+// request in, the outputs of each finishing request out) as one launch instead
+// of four small copies per request: block b copies entry b, 16 bytes a thread
+// per step when source, destination and size allow, else 4 or 1.
+__global__ void __launch_bounds__(256) k_io_copies(const IoCopy *__restrict__ table, int n) {
+    const int b = blockIdx.x;
+    if (b >= n) return;
+    const IoCopy c = table[b];
+    const uintptr_t s = reinterpret_cast<uintptr_t>(c.src), d = reinterpret_cast<uintptr_t>(c.dst);
+    const unsigned long long bytes = c.bytes;
+    if (((s | d | bytes) & 15) == 0) {
+        const uint4 *src = reinterpret_cast<const uint4 *>(c.src);
+        uint4 *dst = reinterpret_cast<uint4 *>(c.dst);
+        for (unsigned long long i = threadIdx.x; i < bytes / 16; i += blockDim.x) dst[i] = src[i];
+    } else if (((s | d | bytes) & 3) == 0) {
+        const unsigned *src = reinterpret_cast<const unsigned *>(c.src);
+        unsigned *dst = reinterpret_cast<unsigned *>(c.dst);
+        for (unsigned long long i = threadIdx.x; i < bytes / 4; i += blockDim.x) dst[i] = src[i];
+    } else {
+        const unsigned char *src = reinterpret_cast<const unsigned char *>(c.src);
+        unsigned char *dst = reinterpret_cast<unsigned char *>(c.dst);
+        for (unsigned long long i = threadIdx.x; i < bytes; i += blockDim.x) dst[i] = src[i];
+    }
+}
+
+int launch_io_copies(const IoCopy *table_dev, int n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_io_copies<<<(unsigned)n, 256, 0, st>>>(table_dev, n);
+    return (int)cudaGetLastError();
+}
+
 int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_t, float delta_r, int tpl,
                  const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st) {
     if (n_entries == 0 || total_warps == 0) return cudaSuccess;

@@ -151,6 +151,11 @@ struct Req {
     int iters_done = 0;
     double t_submit = 0, t_done = 0;
     unsigned long long *key_host = nullptr;   // pinned slot for the best-seed key
+    int key_slot = -1;
+    // every host buffer pinned: the device addresses of q_start, goal, seeds,
+    // traj, cost, success, used by the batched copy kernel instead of copies
+    bool mapped = false;
+    void *dev[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 };
 
 struct Round {
@@ -179,7 +184,16 @@ struct DseedServer {
     cudaEvent_t stage_free[2] = {nullptr, nullptr};
     int stage_half = 0;
     unsigned long long *keys = nullptr;
+    unsigned long long *keys_dev = nullptr;   // the keys' mapped device address
     std::vector<int> free_keys;
+    // request traffic through k_io_copies: pinned staging of the copy tables
+    // (two halves with the round tables, uploads then downloads, 4 copies a
+    // request each), their device copies at io_off in the arena, 16 bytes of
+    // 0xff there (a fresh best-seed key), and the uploads of requests admitted
+    // since the last round
+    dseed::IoCopy *io_stage = nullptr;
+    size_t io_off = 0;
+    std::vector<dseed::IoCopy> up;
     std::unordered_map<int, SceneRec> scenes;
     std::deque<Req *> queue;
     std::vector<Req *> active;
@@ -260,6 +274,18 @@ int retire(DseedServer *sv, bool wait_oldest, int *n_done) {
     return DSEED_OK;
 }
 
+// Device address of pinned host memory, nullptr for any other pointer.
+void *mapped_address(const void *h) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, h) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+constexpr int kIoPerRequest = 4;
+
 int admit(DseedServer *sv) {
     while (!sv->queue.empty() && (int)sv->active.size() < sv->max_requests && !sv->free_keys.empty()) {
         Req *q = sv->queue.front();
@@ -285,6 +311,17 @@ int admit(DseedServer *sv) {
         const dseed::ServeLayout L = dseed::serve_layout(q->r.S, q->r.T, sv->ko.m);
         float *R = reinterpret_cast<float *>(sv->arena_dev + off);
         const size_t n = 7 * (size_t)q->r.T;
+        q->key_slot = slot;
+        if (q->mapped) {
+            const char *ff = sv->arena_dev + sv->io_off + 2 * sizeof(dseed::IoCopy) * kIoPerRequest * sv->max_requests;
+            sv->up.push_back({q->dev[0], R + L.qs, 7 * sizeof(float)});
+            sv->up.push_back({q->dev[1], R + L.goal, 7 * sizeof(float)});
+            sv->up.push_back({q->dev[2], R + L.xt, (unsigned long long)q->r.S * n * sizeof(float)});
+            sv->up.push_back({ff, R + L.key, sizeof(unsigned long long)});
+            sv->active.push_back(q);
+            sv->stats.admitted += 1;
+            continue;
+        }
         int r = cuda_err(cudaMemcpyAsync(R + L.qs, q->r.q_start_host, 7 * sizeof(float), cudaMemcpyHostToDevice,
                                          sv->stream), "request upload");
         if (!r) r = cuda_err(cudaMemcpyAsync(R + L.goal, q->r.goal_host, 7 * sizeof(float), cudaMemcpyHostToDevice,
@@ -299,11 +336,31 @@ int admit(DseedServer *sv) {
     return DSEED_OK;
 }
 
+// Copy `n` entries of a copy table through staging half `half`, direction
+// `dir` (0: uploads, 1: downloads), and launch the batched copy kernel.
+int run_io(DseedServer *sv, int half, int dir, const dseed::IoCopy *entries, size_t n) {
+    if (n == 0) return DSEED_OK;
+    const size_t cap = (size_t)kIoPerRequest * sv->max_requests;
+    if (n > cap) return set_error(DSEED_EINVAL, "%zu request copies exceed the table of %zu", n, cap);
+    dseed::IoCopy *stage = sv->io_stage + ((size_t)half * 2 + dir) * cap;
+    std::copy(entries, entries + n, stage);
+    dseed::IoCopy *table = reinterpret_cast<dseed::IoCopy *>(sv->arena_dev + sv->io_off) + (size_t)dir * cap;
+    int r = cuda_err(cudaMemcpyAsync(table, stage, n * sizeof(dseed::IoCopy), cudaMemcpyHostToDevice, sv->stream),
+                     "copy table upload");
+    if (!r) r = cuda_err((cudaError_t)dseed::launch_io_copies(table, (int)n, sv->stream), "request copies");
+    return r;
+}
+
 int launch_round(DseedServer *sv) {
     // the staging half we fill must no longer be read by an earlier upload
-    int r = bounded_wait(sv, sv->stage_free[sv->stage_half], "staging wait");
+    const int half = sv->stage_half;
+    int r = bounded_wait(sv, sv->stage_free[half], "staging wait");
     if (r) return r;
-    dseed::ServeEntry *st = sv->stage + (size_t)sv->stage_half * kClasses * sv->max_requests;
+    // inputs of the requests admitted since the last round
+    r = run_io(sv, half, 0, sv->up.data(), sv->up.size());
+    if (r) return r;
+    sv->up.clear();
+    dseed::ServeEntry *st = sv->stage + (size_t)half * kClasses * sv->max_requests;
     int counts[kClasses] = {0, 0, 0};
     long long warps[kClasses] = {0, 0, 0};
     Round rd;
@@ -331,9 +388,7 @@ int launch_round(DseedServer *sv) {
     dseed::ServeEntry *table_dev = reinterpret_cast<dseed::ServeEntry *>(sv->arena_dev + sv->table_off);
     r = cuda_err(cudaMemcpyAsync(table_dev, st, sizeof(dseed::ServeEntry) * kClasses * sv->max_requests,
                                  cudaMemcpyHostToDevice, sv->stream), "round table upload");
-    if (!r) r = cuda_err(cudaEventRecord(sv->stage_free[sv->stage_half], sv->stream), "event");
     if (r) return r;
-    sv->stage_half ^= 1;
     for (int c = 0; c < kClasses; ++c) {
         if (!counts[c]) continue;
         r = cuda_err((cudaError_t)dseed::launch_serve(sv->rb, sv->kc, sv->ko, sv->delta_t, sv->delta_r, 1 << c,
@@ -343,10 +398,18 @@ int launch_round(DseedServer *sv) {
         if (r) return r;
     }
     // outputs of the requests that finish in this round
+    std::vector<dseed::IoCopy> down;
     for (Req *q : rd.finishing) {
         const dseed::ServeLayout L = dseed::serve_layout(q->r.S, q->r.T, sv->ko.m);
         const float *R = reinterpret_cast<const float *>(sv->arena_dev + q->off);
         const size_t n = 7 * (size_t)q->r.T, S = q->r.S;
+        if (q->mapped) {
+            down.push_back({R + L.xa, q->dev[3], (unsigned long long)S * n * sizeof(float)});
+            down.push_back({R + L.cost, q->dev[4], (unsigned long long)S * sizeof(float)});
+            down.push_back({R + L.succ, q->dev[5], (unsigned long long)S});
+            down.push_back({R + L.key, sv->keys_dev + q->key_slot, sizeof(unsigned long long)});
+            continue;
+        }
         r = cuda_err(cudaMemcpyAsync(q->r.traj_host, R + L.xa, S * n * sizeof(float), cudaMemcpyDeviceToHost,
                                      sv->stream), "output copy");
         if (!r) r = cuda_err(cudaMemcpyAsync(q->r.cost_host, R + L.cost, S * sizeof(float), cudaMemcpyDeviceToHost,
@@ -357,6 +420,11 @@ int launch_round(DseedServer *sv) {
                                              cudaMemcpyDeviceToHost, sv->stream), "output copy");
         if (r) return r;
     }
+    r = run_io(sv, half, 1, down.data(), down.size());
+    // this half's staging has been read once the copies above are done
+    if (!r) r = cuda_err(cudaEventRecord(sv->stage_free[half], sv->stream), "event");
+    if (r) return r;
+    sv->stage_half ^= 1;
     r = cuda_err(cudaEventCreateWithFlags(&rd.done, cudaEventDisableTiming), "event");
     if (!r) r = cuda_err(cudaEventRecord(rd.done, sv->stream), "event");
     if (r) return r;
@@ -376,7 +444,9 @@ extern "C" int dseed_server_create(const DseedRobot *robot, const DseedServerDes
     int r = dseed::check_cost_opt(desc->cost, desc->opt, desc->delta_t, desc->delta_r);
     if (r) return r;
     if (reinterpret_cast<uintptr_t>(arena_dev) % 256 != 0) return set_error(DSEED_EINVAL, "arena not 256-byte aligned");
-    const size_t table_bytes = round_up(sizeof(dseed::ServeEntry) * kClasses * (size_t)desc->max_requests);
+    const size_t round_table_bytes = round_up(sizeof(dseed::ServeEntry) * kClasses * (size_t)desc->max_requests);
+    const size_t io_bytes = round_up(sizeof(dseed::IoCopy) * 2 * kIoPerRequest * (size_t)desc->max_requests + 256);
+    const size_t table_bytes = round_table_bytes + io_bytes;
     if (desc->arena_bytes < table_bytes + kUnit)
         return set_error(DSEED_ENOMEM, "arena of %zu bytes is smaller than the %zu-byte round tables", desc->arena_bytes,
                          table_bytes);
@@ -395,6 +465,7 @@ extern "C" int dseed_server_create(const DseedRobot *robot, const DseedServerDes
     size_t off;
     arena_take(&sv->arena, table_bytes, &off);
     sv->table_off = off;
+    sv->io_off = off + round_table_bytes;
     r = cuda_err(cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking), "stream");
     if (!r) r = cuda_err(cudaMallocHost(reinterpret_cast<void **>(&sv->stage),
                                         sizeof(dseed::ServeEntry) * 2 * kClasses * (size_t)desc->max_requests),
@@ -402,6 +473,16 @@ extern "C" int dseed_server_create(const DseedRobot *robot, const DseedServerDes
     if (!r) r = cuda_err(cudaMallocHost(reinterpret_cast<void **>(&sv->keys),
                                         sizeof(unsigned long long) * (size_t)desc->max_requests * 2),
                          "pinned keys");
+    if (!r) r = cuda_err(cudaHostGetDevicePointer(reinterpret_cast<void **>(&sv->keys_dev), sv->keys, 0),
+                         "mapped keys");
+    if (!r) r = cuda_err(cudaMallocHost(reinterpret_cast<void **>(&sv->io_stage),
+                                        sizeof(dseed::IoCopy) * 2 * 2 * kIoPerRequest * (size_t)desc->max_requests),
+                         "pinned copy tables");
+    // the 0xff bytes a fresh best-seed key is copied from
+    if (!r) r = cuda_err(cudaMemsetAsync(sv->arena_dev + sv->io_off +
+                                             sizeof(dseed::IoCopy) * 2 * kIoPerRequest * (size_t)desc->max_requests,
+                                         0xff, 16, sv->stream),
+                         "key constant");
     for (int h = 0; h < 2 && !r; ++h) {
         r = cuda_err(cudaEventCreateWithFlags(&sv->stage_free[h], cudaEventDisableTiming), "event");
         if (!r) r = cuda_err(cudaEventRecord(sv->stage_free[h], sv->stream), "event");
@@ -424,6 +505,7 @@ extern "C" void dseed_server_destroy(DseedServer *sv) {
         if (sv->stage_free[h]) cudaEventDestroy(sv->stage_free[h]);
     if (sv->stage) cudaFreeHost(sv->stage);
     if (sv->keys) cudaFreeHost(sv->keys);
+    if (sv->io_stage) cudaFreeHost(sv->io_stage);
     if (sv->stream) cudaStreamDestroy(sv->stream);
     delete sv;
 }
@@ -496,6 +578,14 @@ extern "C" int dseed_server_submit(DseedServer *sv, const DseedRequest *req, lon
     q->ticket = sv->next_ticket++;
     q->r = *req;
     q->t_submit = now_s();
+    // with every host buffer pinned the request's traffic goes through the batched copy kernel
+    const void *host[6] = {req->q_start_host, req->goal_host, req->seeds_host, req->traj_host, req->cost_host,
+                           req->success_host};
+    q->mapped = true;
+    for (int i = 0; i < 6 && q->mapped; ++i) {
+        q->dev[i] = mapped_address(host[i]);
+        q->mapped = q->dev[i] != nullptr;
+    }
     auto it = sv->scenes.find(req->scene_id);
     if (it != sv->scenes.end()) it->second.users += 1;
     sv->queue.push_back(q.get());
