@@ -28,18 +28,28 @@ constexpr int kServeWarps = 4;
 // four (128) otherwise, where the round's bookkeeping would spill more; with the
 // self-collision term (its pair loops and the per-lane frame transforms in shared
 // memory) shared memory limits the blocks, so the registers are left free.
+// With several waypoints per lane (and no self term) the search direction stays
+// in the request's arena region instead of shared memory, as in the one-shot
+// plan: two-warp blocks, sixteen resident warps at T <= 64 instead of twelve.
+constexpr bool serve_dd_global(int tpl, bool self) { return tpl >= 2 && !self; }
+constexpr int serve_warps(int tpl, bool self) { return serve_dd_global(tpl, self) ? 2 : kServeWarps; }
 constexpr int serve_min_blocks(int tpl, bool self, bool sweep) {
-    return self ? 1 : (tpl == 1 && !sweep) ? DSEED_SERVE_MINBLOCKS_T32 : DSEED_SERVE_MINBLOCKS;
+    return self ? 1 : serve_dd_global(tpl, self) ? (tpl == 2 ? 8 : 4)
+                    : (tpl == 1 && !sweep) ? DSEED_SERVE_MINBLOCKS_T32 : DSEED_SERVE_MINBLOCKS;
+}
+constexpr int serve_warp_floats(int tpl, bool self) {
+    return serve_dd_global(tpl, self) ? warp_smem_floats_nodd(32 * tpl, self) : warp_smem_floats(32 * tpl, self);
 }
 
 template <int TPL, bool SELF, bool SWEEP>
-__global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, SWEEP))
+__global__ void __launch_bounds__(serve_warps(TPL, SELF) * 32, serve_min_blocks(TPL, SELF, SWEEP))
     k_serve(const __grid_constant__ KRobot rb, const __grid_constant__ KCost kc, const __grid_constant__ KOpt ko,
             float delta_t, float delta_r, const ServeEntry *__restrict__ table, int n_entries, long long total_warps) {
     constexpr int NPL = 7 * TPL;
     extern __shared__ float smem[];
     const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const long long w = (long long)blockIdx.x * kServeWarps + wid;
+    constexpr bool kDdGlobal = serve_dd_global(TPL, SELF);
+    const long long w = (long long)blockIdx.x * serve_warps(TPL, SELF) + wid;
     if (w >= total_warps) return;
     int lo = 0, hi = n_entries - 1;                 // last entry with warp_begin <= w
     while (lo < hi) {
@@ -56,7 +66,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, 
     float *g_ga = R + L.ga + (size_t)s * n, *g_dd = R + L.dd + (size_t)s * n;
     float *S_ = R + L.hs + (size_t)s * m * n, *Y_ = R + L.hy + (size_t)s * m * n;
     float *sc = R + L.sc + (size_t)s * 16;
-    WarpSmem ws = carve(smem + wid * warp_smem_floats(32 * TPL, SELF), T);
+    WarpSmem ws = carve(smem + wid * serve_warp_floats(TPL, SELF), T, kDdGlobal ? g_dd : nullptr);
     float *xt = ws.xs + kPad * 7;
     SceneView sv;
     {
@@ -83,7 +93,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, 
         for (int e = lane; e < n; e += 32) {
             ws.xa[e] = g_xa[e];
             ws.ga[e] = g_ga[e];
-            ws.dd[e] = g_dd[e];
+            if (!kDdGlobal) ws.dd[e] = g_dd[e];
         }
         if (lane < 9) ws.v[lane] = sc[3 + lane];     // rho[0..8) at v[0..8), y^T y at v[8]
         st.f = sc[0];
@@ -106,7 +116,7 @@ __global__ void __launch_bounds__(kServeWarps * 32, serve_min_blocks(TPL, SELF, 
             g_xt[e] = xt[e];
             g_xa[e] = ws.xa[e];
             g_ga[e] = ws.ga[e];
-            g_dd[e] = ws.dd[e];
+            if (!kDdGlobal) g_dd[e] = ws.dd[e];
         }
         if (lane < 9) sc[3 + lane] = ws.v[lane];
         if (lane == 0) {
@@ -170,15 +180,16 @@ int launch_io_copies(const IoCopy *table_dev, int n, cudaStream_t st) {
 int launch_serve(const KRobot &rb, const KCost &kc, const KOpt &ko, float delta_t, float delta_r, int tpl,
                  const ServeEntry *table, int n_entries, long long total_warps, cudaStream_t st) {
     if (n_entries == 0 || total_warps == 0) return cudaSuccess;
-    const unsigned blocks = (unsigned)((total_warps + kServeWarps - 1) / kServeWarps);
     const bool self = kc.w_s > 0.f;
-    const size_t smem = (size_t)kServeWarps * warp_smem_floats(32 * tpl, self) * sizeof(float);
+    const int warps = serve_warps(tpl, self);
+    const unsigned blocks = (unsigned)((total_warps + warps - 1) / warps);
+    const size_t smem = (size_t)warps * serve_warp_floats(tpl, self) * sizeof(float);
     auto go = [&](auto kern) {
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return (int)e;
         }
-        kern<<<blocks, kServeWarps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
+        kern<<<blocks, warps * 32, smem, st>>>(rb, kc, ko, delta_t, delta_r, table, n_entries, total_warps);
         return (int)cudaGetLastError();
     };
     // variants: waypoints per lane x self-collision term x swept check
