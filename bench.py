@@ -53,15 +53,15 @@ KERNEL_SOURCES = ("paper_2410_16727_gb300/csrc/device.cuh", "paper_2410_16727_gb
                   "paper_2410_16727_gb300/csrc/internal.h")
 NCU_COUNTERS = {
     # k_plan<2,0,0>, 128 of the 1024 stress problems (all 16 scenes), 200 iterations:
-    # 2483.64 MB read + 2392.08 MB written over 128*128*64*200 evaluations; L2 hit 97.58%
-    "stress": {"dram_bytes_per_st": (2483.641e6 + 2392.077e6) / (128 * 128 * 64 * 200), "l2_hit_pct": 97.58,
-               "kernel_hash": "496efaee5e6d6c43",
+    # 2479.99 MB read + 2392.27 MB written over 128*128*64*200 evaluations; L2 hit 97.57%
+    "stress": {"dram_bytes_per_st": (2479.985e6 + 2392.271e6) / (128 * 128 * 64 * 200), "l2_hit_pct": 97.57,
+               "kernel_hash": "7c0dbba8147b5a19",
                "capture": "ncu dram__bytes_read/write.sum, lts__t_sector_hit_rate.pct of one k_plan launch, "
                           "128 stress problems, scaled by evaluations (profiles/k_plan_stress.md)"},
-    # k_plan<1,0,0>, the full 256-problem batched launch: 369.81 MB read + 69.39 MB written;
-    # L2 hit rate 98.38% from the 64-problem launch
-    "batched": {"dram_bytes_per_st": (369.805e6 + 69.388e6) / (256 * 64 * 32 * 100), "l2_hit_pct": 98.38,
-                "kernel_hash": "496efaee5e6d6c43",
+    # k_plan<1,0,0>, the full 256-problem batched launch: 368.66 MB read + 69.44 MB written;
+    # L2 hit rate 98.36% from the 64-problem launch
+    "batched": {"dram_bytes_per_st": (368.663e6 + 69.440e6) / (256 * 64 * 32 * 100), "l2_hit_pct": 98.36,
+                "kernel_hash": "7c0dbba8147b5a19",
                 "capture": "ncu dram__bytes_read/write.sum of the full batched k_plan launch, "
                            "lts__t_sector_hit_rate.pct of a 64-problem launch (profiles/k_plan_batched.md)"},
 }
