@@ -3,7 +3,6 @@ autograd wrapper of the cost.  Argument marshalling only; the arithmetic runs
 in libdseed's kernels."""
 from __future__ import annotations
 
-import math
 from typing import List, Optional, Sequence
 
 import numpy as np

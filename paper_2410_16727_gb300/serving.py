@@ -10,7 +10,6 @@ dseed_server_step in a loop and reads the ticket states.
 from __future__ import annotations
 
 import dataclasses
-import math
 import time
 from typing import Callable, Dict, List, Optional, Sequence
 

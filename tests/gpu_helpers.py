@@ -2,10 +2,9 @@
 clearance and FK callbacks (no oracle input ever comes from the CUDA path), then
 both sides receive the same float32 arrays."""
 import numpy as np
-import torch
 
 import oracle
-from paper_2410_16727_gb300 import api, binding as B, inputs as I
+from paper_2410_16727_gb300 import api, inputs as I
 
 
 def oracle_workload(name, n_scenes=None, **kw):

@@ -11,7 +11,7 @@ import pytest
 import torch
 
 import oracle
-from gpu_helpers import check_success_agreement, gpu_side, oracle_workload, rel_l2, to_np
+from gpu_helpers import check_success_agreement, oracle_workload, rel_l2, to_np
 from paper_2410_16727_gb300 import api, binding as B, inputs as I, serving as SV
 
 pytestmark = pytest.mark.gpu

@@ -4,12 +4,11 @@ touch its host's allocator).  Its scratch is a fixed array inside the library,
 so it must give the same results as dseed_plan_batch with a caller workspace,
 call after call, without allocating.  This file sorts last so that a run that
 stops at the first failure has run every other test first."""
-import numpy as np
 import pytest
 import torch
 
 from gpu_helpers import gpu_side, oracle_workload
-from paper_2410_16727_gb300 import binding as B, inputs as I
+from paper_2410_16727_gb300 import binding as B
 
 pytestmark = pytest.mark.gpu
 
