@@ -285,7 +285,6 @@ def guided_ddim(spec, flat_params, noise, q_start, q_goal, goal, occ, limits, re
     noise = np.asarray(noise, np.float64)
     N, T = noise.shape[0], noise.shape[1]
     lim = np.asarray(limits, np.float64)
-    half = (lim[:, 1] - lim[:, 0]) / 2.0
     qs_n, qg_n = normalise_joints(lim, q_start), normalise_joints(lim, q_goal)
     lin = straight_path(qs_n, qg_n, T)
     ks = ddim_schedule(spec.K, steps)

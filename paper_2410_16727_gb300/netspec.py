@@ -94,7 +94,7 @@ def param_shapes(spec: NetSpec) -> "OrderedDict[str, tuple]":
         if ci != co:
             s[f"{name}.r.w"] = (co, 1, ci)
             s[f"{name}.r.b"] = (co,)
-    c1, c2, c3 = spec.chans
+    c1, c2, _ = spec.chans
     s["down1.w"] = (c1, 3, c1)
     s["down1.b"] = (c1,)
     s["down2.w"] = (c2, 3, c2)

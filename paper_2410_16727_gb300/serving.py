@@ -79,7 +79,7 @@ def build_serving_workload(n_requests: int, clearance_fn, pose_fn, n_scenes: int
         problems.append(ServingProblem(int(wl.scene_of_problem[p]), wl.q_start[p], wl.goal[p], {}, wl.q_goal[p]))
     rng = I._rng(4000 + seed, 0, 0)
     reqs = []
-    for i in range(n_requests):
+    for _ in range(n_requests):
         p = int(rng.integers(0, len(problems)))
         S = int(rng.choice(seed_counts))
         T = int(rng.choice(horizons))
