@@ -924,6 +924,31 @@ def run_learned_stress(args, wl) -> dict:
 
 # ---------------------------------------------------------------------------- CPU oracle
 
+def host_cpu_model() -> str:
+    """The host CPU's model name (x86 /proc/cpuinfo, else lscpu, which names Arm
+    cores), with the machine architecture."""
+    import platform
+    name = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not name:
+        try:
+            out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+            for line in out.splitlines():
+                if line.strip().lower().startswith("model name"):
+                    name = line.split(":", 1)[1].strip()
+                    break
+        except (OSError, subprocess.SubprocessError):
+            pass
+    return f"{name or 'unknown'} ({platform.machine()})"
+
+
 def _oracle_problems(spec, n: int, seed_offset: int = 0):
     """The first n problems of the workload exactly as the GPU arm draws them,
     with the oracle's own ESDFs of the scenes they use (inputs drawn with the
@@ -990,7 +1015,7 @@ def run_reference(args, rank: int, world: int):
                 vs_baseline=None, dtype="f64", data="synthetic", config=workload_config(spec, world),
                 extrapolated_ms_per_full_workload=full_ms,
                 cpu_baseline={"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
-                              "sample": sample},
+                              "cpu_model": host_cpu_model(), "sample": sample},
                 e2e={"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0})
 
 
@@ -1016,7 +1041,8 @@ def main():
             res["learned_stress"] = run_learned_stress(args, wl)
     if rank == 0 and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(workload_spec(args, args.workload))
-        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "cpu_model": host_cpu_model(), "sample": desc}
     if rank == 0:
         print(json.dumps(res), flush=True)
     if world > 1:
