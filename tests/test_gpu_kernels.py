@@ -170,6 +170,30 @@ def test_gradient_matches_oracle(gpu_lib, T):
     assert errs.max() <= TOL_GRAD, (errs.max(), np.sort(errs)[-5:])
 
 
+def test_goal_quaternion_sign_and_scale(gpu_lib):
+    """Goal quaternions are normalised on entry and q and -q name one rotation:
+    with the goal quaternions multiplied by -1, 2.5 or -0.3 the cost, its goal
+    term and the gradient stay at the oracle's values for the unit goals."""
+    wl, orc, x = _random_batch(32, S=8, seed=11)
+    want_c, want_g = _oracle_cost(orc, wl, x)
+    _, want_t = _oracle_cost(orc, wl, x, grad=False, terms=True)
+    assert (want_t[..., 2] > 0).all()
+    planner = api.Planner(wl.robot, wl.cost, wl.opt)
+    planner.set_scenes(wl.cuboids, wl.grids)
+    sc = np.maximum(np.abs(want_c), 1e-6)
+    for f in (-1.0, 2.5, -0.3):
+        goal = wl.goal.copy()
+        goal[:, 3:] *= f
+        batch = planner.batch(wl.q_start, goal, wl.scene_of_problem, wl.S, wl.T)
+        _, terms = B.cost(planner.robot, batch.desc, batch.pr, _cuda(x), terms=True)
+        assert (np.abs(to_np(terms)[..., 2] - want_t[..., 2]) / sc).max() <= TOL_COST, f
+        c, g = B.cost_grad(planner.robot, batch.desc, batch.pr, _cuda(x))
+        assert (np.abs(to_np(c) - want_c) / sc).max() <= TOL_COST, f
+        gg = to_np(g)
+        errs = [rel_l2(gg[p, s], want_g[p, s]) for p in range(wl.P) for s in range(wl.S)]
+        assert max(errs) <= TOL_GRAD, (f, max(errs))
+
+
 def test_gradient_scale_and_autograd(gpu_lib):
     wl, orc, x = _random_batch(32, S=8, seed=7)
     planner, batch = gpu_side(wl)

@@ -87,6 +87,14 @@ def test_goal_cost_zero_at_goal_and_closed_forms():
         _, met = orc.evaluate(0, qs, goal, x[None])
         assert abs(met[0, 1] - np.linalg.norm(d)) < 1e-12
         assert abs(met[0, 2] - min(theta, 2 * math.pi - theta)) < 1e-7
+        # goal quaternions are taken up to sign and scale (normalised on entry,
+        # q and -q one rotation): the same closed forms hold for -2.5 q and 0.3 q
+        for f in (-2.5, 0.3):
+            goal_f = np.concatenate([goal[:3], f * goal[3:]])
+            _, terms_f = orc.cost(0, qs, goal_f, x[None], grad=False, terms=True)
+            assert abs(terms_f[0, 2] - want) < 1e-9 * max(1.0, want)
+            _, met_f = orc.evaluate(0, qs, goal_f, x[None])
+            assert abs(met_f[0, 2] - min(theta, 2 * math.pi - theta)) < 1e-7
 
 
 def test_world_hinge_on_affine_face_region():
