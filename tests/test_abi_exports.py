@@ -70,6 +70,19 @@ def test_host_argument_checks_without_gpu(libpath):
         assert f"n_sweep = {bad}" in BD.last_error()
     d = BD.plan_desc(2, 3, 32, dataclasses.replace(I.CostParams(), n_sweep=8), I.OptParams())
     assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == 0
+    # NaN or infinite descriptor entries are refused before any launch
+    for field in ("w_c", "eta", "w_R", "w_self"):
+        for v in (float("nan"), float("inf")):
+            d = BD.plan_desc(2, 3, 32, dataclasses.replace(I.CostParams(), **{field: v}), I.OptParams())
+            assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1, (field, v)
+            assert "non-finite cost" in BD.last_error()
+    d = BD.plan_desc(2, 3, 32, I.CostParams(), I.OptParams(), delta_r=float("nan"))
+    assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1
+    for field, v, msg in (("c1", float("nan"), "non-finite optimiser"), ("max_step", float("inf"), "non-finite"),
+                          ("max_step", 0.0, "max_step"), ("alpha_min", -1e-4, "alpha_min"), ("iters", 0, "iters")):
+        d = BD.plan_desc(2, 3, 32, I.CostParams(), dataclasses.replace(I.OptParams(), **{field: v}))
+        assert lib.dseed_plan_workspace_bytes(ctypes.byref(d), ctypes.byref(n)) == -1, (field, v)
+        assert msg in BD.last_error(), (field, BD.last_error())
     r = I.make_robot()
     r.sph_r = r.sph_r.copy()
     r.sph_r[3] = -1.0
