@@ -118,6 +118,18 @@ def normalise(robot, q: torch.Tensor, inverse: bool = False) -> torch.Tensor:
     return out
 
 
+def linear_path_weights(T: int, D: int) -> np.ndarray:
+    """Interpolation matrix [2D][T*D] of the straight start-goal path:
+    [q_s, q_g] @ W puts waypoint t (t = 1..T) at q_s + (t/T)(q_g - q_s)."""
+    tau = np.arange(1, T + 1, dtype=np.float64) / T
+    W = np.zeros((2 * D, T * D), np.float32)
+    for t in range(T):
+        for d in range(D):
+            W[d, t * D + d] = 1.0 - tau[t]
+            W[D + d, t * D + d] = tau[t]
+    return W
+
+
 def linear_path(qs_n: torch.Tensor, qg_n: torch.Tensor, T: int) -> torch.Tensor:
     """Straight start-goal joint path [N][T][7] (waypoint t at fraction t/T,
     t = 1..T, the start itself excluded like the optimiser's waypoints), from
@@ -127,17 +139,33 @@ def linear_path(qs_n: torch.Tensor, qg_n: torch.Tensor, T: int) -> torch.Tensor:
     key = ("lin", T, D, str(qs_n.device))
     W = _AFFINE_CACHE.get(key)
     if W is None:
-        tau = np.arange(1, T + 1, dtype=np.float64) / T
-        Wh = np.zeros((2 * D, T * D), np.float32)
-        for t in range(T):
-            for d in range(D):
-                Wh[d, t * D + d] = 1.0 - tau[t]
-                Wh[D + d, t * D + d] = tau[t]
-        W = _AFFINE_CACHE[key] = torch.from_numpy(Wh).to(qs_n.device)
+        W = _AFFINE_CACHE[key] = torch.from_numpy(linear_path_weights(T, D)).to(qs_n.device)
     A = torch.cat([qs_n, qg_n], 1).contiguous()
     out = torch.empty((N, T, D), dtype=torch.float32, device=qs_n.device)
     _nn("gemm_f32", 0, 0, N, T * D, 2 * D, 1.0, A, 2 * D, W, T * D, 0.0, out, T * D, None)
     return out
+
+
+def resample_weights(T0: int, T1: int, D: int):
+    """Interpolation weights of `resample`: (Wx [T0*D][T1*D], Wq [D][T1*D]) so
+    that x @ Wx + q0 @ Wq holds, at output waypoint j (fraction j / T1), the
+    linear interpolation in time between the input waypoints around it (input
+    waypoint k at fraction k / T0, the start q0 at fraction 0)."""
+    Wx = np.zeros((T0 * D, T1 * D), np.float32)
+    Wq = np.zeros((D, T1 * D), np.float32)
+    for j in range(1, T1 + 1):
+        u = j * T0 / T1                       # position in input waypoints (the start at 0)
+        k0 = min(int(math.floor(u)), T0)
+        f = u - k0
+        for d in range(D):
+            col = (j - 1) * D + d
+            if k0 == 0:
+                Wq[d, col] = 1.0 - f
+            else:
+                Wx[(k0 - 1) * D + d, col] += 1.0 - f
+            if f > 0.0:
+                Wx[k0 * D + d, col] += f
+    return Wx, Wq
 
 
 def resample(x: torch.Tensor, q0: torch.Tensor, T1: int) -> torch.Tensor:
@@ -152,20 +180,7 @@ def resample(x: torch.Tensor, q0: torch.Tensor, T1: int) -> torch.Tensor:
     key = ("resample", T0, T1, D, str(x.device))
     W = _AFFINE_CACHE.get(key)
     if W is None:
-        Wx = np.zeros((T0 * D, T1 * D), np.float32)
-        Wq = np.zeros((D, T1 * D), np.float32)
-        for j in range(1, T1 + 1):
-            u = j * T0 / T1                       # position in input waypoints (the start at 0)
-            k0 = min(int(math.floor(u)), T0)
-            f = u - k0
-            for d in range(D):
-                col = (j - 1) * D + d
-                if k0 == 0:
-                    Wq[d, col] = 1.0 - f
-                else:
-                    Wx[(k0 - 1) * D + d, col] += 1.0 - f
-                if f > 0.0:
-                    Wx[k0 * D + d, col] += f
+        Wx, Wq = resample_weights(T0, T1, D)
         W = _AFFINE_CACHE[key] = (torch.from_numpy(Wx).to(x.device), torch.from_numpy(Wq).to(x.device))
     out = torch.empty((N, T1, D), dtype=torch.float32, device=x.device)
     _nn("gemm_f32", 0, 0, N, T1 * D, T0 * D, 1.0, x.contiguous(), T0 * D, W[0], T1 * D, 0.0, out, T1 * D, None)
