@@ -51,3 +51,21 @@ def test_linear_path_weights(T):
     np.testing.assert_allclose(got, qs[:, None] + t * (qg - qs)[:, None], rtol=0, atol=1e-6)
     # the last waypoint is the goal configuration itself
     assert np.array_equal(W[D:, (T - 1) * D:], np.eye(D, dtype=np.float32))
+
+
+def test_limit_normalisation_maps_limits_to_unit_interval():
+    """App. A.4: joints scaled to [-1, 1] by their mechanical limits; the inverse
+    undoes it.  Checked on the (scale, shift) rows the FiLM kernel applies."""
+    import torch
+
+    from paper_2410_16727_gb300 import inputs as I
+    robot = I.make_robot()
+    fwd = L._limits_affine(robot, torch.device("cpu"), False).numpy().astype(np.float64)[0]
+    inv = L._limits_affine(robot, torch.device("cpu"), True).numpy().astype(np.float64)[0]
+    lo, hi = robot.limits[:, 0].astype(np.float64), robot.limits[:, 1].astype(np.float64)
+    f = lambda v, a: v * a[:7] + a[7:]
+    np.testing.assert_allclose(f(lo, fwd), -1.0, atol=1e-6)
+    np.testing.assert_allclose(f(hi, fwd), 1.0, atol=1e-6)
+    np.testing.assert_allclose(f((lo + hi) / 2, fwd), 0.0, atol=1e-6)
+    q = np.random.default_rng(0).uniform(lo, hi, size=(50, 7))
+    np.testing.assert_allclose(f(f(q, fwd), inv), q, atol=1e-5)
