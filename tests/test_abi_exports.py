@@ -168,3 +168,44 @@ def test_status_codes_match_header():
     from paper_2410_16727_gb300 import binding as BD
     text = open(os.path.join(ROOT, "include", "dseed.h")).read()
     assert int(re.search(r"#define DSEED_ETIMEOUT \((-\d+)\)", text).group(1)) == BD.ETIMEOUT
+
+
+# ctypes mirror in the binding -> the header's typedef
+_STRUCTS = {"RobotDesc": "DseedRobotDesc", "Grid": "DseedGrid", "EsdfJob": "DseedEsdfJob", "Scene": "DseedScene",
+            "CostParams": "DseedCostParams", "OptParams": "DseedOptParams", "PlanDesc": "DseedPlanDesc",
+            "Problems": "DseedProblems", "LbfgsLayout": "DseedLbfgsLayout", "ServerDesc": "DseedServerDesc",
+            "Request": "DseedRequest", "ConvTc": "DseedConvTc", "ServerStats": "DseedServerStats",
+            "DeviceInfo": "DseedDeviceInfo"}
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every ctypes structure of the binding has the size of its C typedef and
+    each of its fields sits at the C field's offset (a C program built with the
+    header prints sizeof / offsetof; a field name missing in C fails to compile)."""
+    import shutil
+
+    from paper_2410_16727_gb300 import binding as BD
+    cc = shutil.which("gcc") or shutil.which("cc")
+    cuda_inc = "/usr/local/cuda/include"
+    if cc is None or not os.path.exists(os.path.join(cuda_inc, "cuda_runtime_api.h")):
+        pytest.skip("needs a C compiler and the CUDA runtime header")
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "dseed.h"', "int main(void) {"]
+    want = []
+    for py, c in _STRUCTS.items():
+        cls = getattr(BD, py)
+        lines.append(f'    printf("%zu\\n", sizeof({c}));')
+        want.append((f"sizeof {c}", ctypes.sizeof(cls)))
+        for name, _ in cls._fields_:
+            lines.append(f'    printf("%zu\\n", offsetof({c}, {name}));')
+            want.append((f"{c}.{name}", getattr(cls, name).offset))
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), "-I", cuda_inc, str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    got = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert len(got) == len(want)
+    bad = [(k, w, g) for (k, w), g in zip(want, got) if w != g]
+    assert not bad, bad
