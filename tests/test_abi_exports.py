@@ -209,3 +209,42 @@ def test_binding_structs_match_the_header_layout(tmp_path):
     assert len(got) == len(want)
     bad = [(k, w, g) for (k, w), g in zip(want, got) if w != g]
     assert not bad, bad
+
+
+def _c_kind(param: str) -> str:
+    """Coarse kind of one C parameter declaration."""
+    p = " ".join(param.replace("\n", " ").split())
+    if "*" in p or "cudaStream_t" in p:
+        return "ptr"
+    words = p.split()
+    body = " ".join(w for w in words[:-1] if w not in ("const",)) if len(words) > 1 else p
+    return {"int": "int", "float": "float", "double": "double", "size_t": "size_t", "long long": "i64",
+            "int64_t": "i64", "unsigned long long": "u64", "uint64_t": "u64"}[body]
+
+
+def _ctypes_kind(t) -> str:
+    if t in (ctypes.c_void_p, ctypes.c_char_p) or (isinstance(t, type) and issubclass(t, ctypes._Pointer)):
+        return "ptr"
+    for k, ct in (("int", ctypes.c_int), ("float", ctypes.c_float), ("double", ctypes.c_double),
+                  ("size_t", ctypes.c_size_t), ("i64", ctypes.c_longlong), ("u64", ctypes.c_ulonglong)):
+        if t is ct:
+            return k
+    raise AssertionError(f"unexpected ctypes type {t}")
+
+
+def test_binding_signatures_match_the_header_prototypes():
+    """The binding's argument and result types of every entry point agree in
+    number and kind (pointer, int, float, double, size_t, 64-bit integer) with
+    the header's prototypes, and both name the same entry points."""
+    from paper_2410_16727_gb300 import binding as BD
+    text = open(os.path.join(ROOT, "include", "dseed.h")).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    protos = {m.group(2): (" ".join(m.group(1).split()), m.group(3))
+              for m in re.finditer(r"(int|void|const char \*)\s*\b(dseed_\w+)\s*\(([^;]*?)\)\s*;", text, re.S)}
+    assert set(protos) == set(BD._SIGS), set(protos) ^ set(BD._SIGS)
+    for name, (ret, params) in protos.items():
+        args, res = BD._SIGS[name]
+        ps = [p for p in params.split(",") if p.strip() and p.strip() != "void"]
+        assert [_c_kind(p) for p in ps] == [_ctypes_kind(a) for a in args], name
+        want_res = {"int": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p}[ret]
+        assert res is want_res, (name, ret, res)
