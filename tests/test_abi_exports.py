@@ -248,3 +248,17 @@ def test_binding_signatures_match_the_header_prototypes():
         assert [_c_kind(p) for p in ps] == [_ctypes_kind(a) for a in args], name
         want_res = {"int": ctypes.c_int, "void": None, "const char *": ctypes.c_char_p}[ret]
         assert res is want_res, (name, ret, res)
+
+
+def test_binding_constants_match_the_header():
+    from paper_2410_16727_gb300 import binding as BD
+    text = open(os.path.join(ROOT, "include", "dseed.h")).read()
+    defs = dict(re.findall(r"#define DSEED_(\w+) \(?(-?[0-9.]+)f?\)?", text))
+    for name in ("MAX_SPHERES", "MAX_T", "MAX_HISTORY", "N_METRICS", "ESDF_FAR", "ETIMEOUT"):
+        assert float(defs[name]) == float(getattr(BD, name)), name
+    # the cost fields the binding fills in order are the header's float fields of DseedCostParams
+    body = re.search(r"typedef struct \{([^{}]*)\} DseedCostParams;", re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+                     ).group(1)
+    floats = [n.strip() for decl in body.split(";") if decl.strip().startswith("float")
+              for n in decl.strip()[len("float"):].split(",")]
+    assert tuple(floats) == BD.COST_FIELDS
