@@ -177,7 +177,11 @@ typedef struct {
 
 /* ---------------------------------------------------------------- basics */
 
+/* DSEED_ABI_VERSION of the library: a binding written against this header
+ * checks it before use.  Never fails. */
 int dseed_abi_version(void);
+/* Message of the calling thread's last failed call ("" before any failure);
+ * owned by the library, valid until that thread's next failing call. */
 const char *dseed_last_error(void);
 
 /* What the roofline of the optimiser's FP32 kernels is computed from (no
@@ -231,32 +235,44 @@ int dseed_scene_build_esdf_batch(const DseedEsdfJob *jobs_host, int n_jobs, cuda
 
 /* ------------------------------------------------------------ kinematics */
 
-/* Forward kinematics of N configurations q_dev [N][7]: flange poses
- * pose_dev [N][7] (qw >= 0) and, when spheres_dev is not NULL, the sphere
- * centres [N][n_spheres][3] in the order of the robot description. */
+/* Forward kinematics of N configurations q_dev [N][7] (FK of the goal term
+ * C_goal(X_d, FK(q_T)), App. A.5; the sphere placement c = R_L o + p_L of the
+ * collision model, Sec. 4.4): flange poses pose_dev [N][7] (qw >= 0) and, when
+ * spheres_dev is not NULL, the sphere centres [N][n_spheres][3] in the order
+ * of the robot description.  EINVAL on a null robot, N < 0, or (N > 0) a null
+ * q_dev or pose_dev; N = 0 enqueues nothing. */
 int dseed_fk(const DseedRobot *robot, const float *q_dev, int N, float *pose_dev,
              float *spheres_dev, cudaStream_t stream);
 
 /* ---------------------------------------------------------- cost, adjoint */
 
-/* Cost of trajectories x_dev [P][S][T][7] of the problems in `pr`:
- * cost_dev [P][S]; terms_dev (optional) [P][S][4] = C_world, C_smooth,
- * C_goal, C_limit. */
+/* Cost of trajectories x_dev [P][S][T][7] of the problems in `pr` (the
+ * objective of App. A.5, see the top of this file): cost_dev [P][S]; terms_dev
+ * (optional) [P][S][4] = C_world (+ C_self), C_smooth, C_goal, C_limit.
+ * desc->opt is not read.  EINVAL on a null robot, a bad descriptor (sizes, a
+ * non-finite or out-of-range parameter), a null problem array or (P > 0) a
+ * null x_dev or cost_dev.  A problem whose scene index is out of range gets a
+ * NaN cost rather than an out-of-bounds read. */
 int dseed_cost(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
                const float *x_dev, float *cost_dev, float *terms_dev, cudaStream_t stream);
 
 /* Cost and its gradient dC/dx by the hand-written adjoint (reverse pass
  * through the hinge, the trilinear lookup, the sphere placement and the
- * kinematic chain, plus the transposed finite-difference stencils):
- * cost_dev [P][S], grad_dev [P][S][T][7].  grad_scale_dev (optional) [P][S]
- * multiplies each trajectory's gradient (the incoming adjoint of a
- * reverse-mode caller). */
+ * kinematic chain, plus the transposed finite-difference stencils): the
+ * gradient the optimiser of Sec. 4.4 / App. A.5 descends.  cost_dev [P][S],
+ * grad_dev [P][S][T][7].  grad_scale_dev (optional) [P][S] multiplies each
+ * trajectory's gradient (the incoming adjoint of a reverse-mode caller).
+ * Errors as dseed_cost, and EINVAL for a null grad_dev when P > 0. */
 int dseed_cost_grad(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
                     const float *x_dev, const float *grad_scale_dev, float *cost_dev,
                     float *grad_dev, cudaStream_t stream);
 
-/* Success flags success_dev [P][S] (1 = success) and metrics_dev (optional)
- * [P][S][DSEED_N_METRICS] of trajectories x_dev [P][S][T][7]. */
+/* Success flags success_dev [P][S] (1 = success, the test of Sec. 5.1: no
+ * sphere inside an obstacle at any waypoint, translation error < delta_t,
+ * rotation error < delta_r, every waypoint within the limits) and metrics_dev
+ * (optional) [P][S][DSEED_N_METRICS] (the layout listed at DSEED_N_METRICS) of
+ * trajectories x_dev [P][S][T][7].
+ * Errors as dseed_cost, with success_dev in place of cost_dev. */
 int dseed_evaluate(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
                    const float *x_dev, uint8_t *success_dev, float *metrics_dev,
                    cudaStream_t stream);
@@ -281,33 +297,44 @@ typedef struct {
     size_t total;     /* bytes of the whole state */
 } DseedLbfgsLayout;
 
+/* Offsets of that state for desc (P, S, T, opt.m).  Host-only; EINVAL on a bad
+ * descriptor (opt included) or a null out. */
 int dseed_lbfgs_layout(const DseedPlanDesc *desc, DseedLbfgsLayout *out);
 
 /* Start every seed at x0_dev [B][n]: x_trial = x0, f = +inf, alpha = 1, empty
- * history.  state_dev: caller buffer of at least layout.total bytes. */
+ * history.  state_dev: caller buffer of at least layout.total bytes.  EINVAL on
+ * a bad descriptor or (B > 0) a null x0_dev or state_dev. */
 int dseed_lbfgs_init(const DseedPlanDesc *desc, const float *x0_dev, void *state_dev,
                      cudaStream_t stream);
 
 /* One L-BFGS update (K4) of every seed, given the cost f_trial_dev [B] and
  * gradient g_trial_dev [B][n] of the current trial point: accept/reject, history
- * update, two-loop direction, next trial point (see DseedOptParams). */
+ * update, two-loop direction, next trial point (see DseedOptParams; the
+ * optimiser of Sec. 4.4 takes one such step per cost evaluation, N_iters of them,
+ * Table 1).  EINVAL on a bad descriptor or (B > 0) a null pointer. */
 int dseed_lbfgs_step(const DseedPlanDesc *desc, const float *f_trial_dev,
                      const float *g_trial_dev, void *state_dev, cudaStream_t stream);
 
 /* ------------------------------------------------------------------ plan */
 
-/* Bytes of device workspace dseed_plan_batch needs for `desc`. */
+/* Bytes of device workspace dseed_plan_batch needs for `desc`.  Host-only;
+ * EINVAL on a bad descriptor (sizes, non-finite or out-of-range parameters) or
+ * a null bytes. */
 int dseed_plan_workspace_bytes(const DseedPlanDesc *desc, size_t *bytes);
 
 /* Optimise every seed of every problem for desc->opt.iters iterations, on
- * the device in one pass, then test success.
+ * the device in one pass, then test success (the seed-parallel optimisation of
+ * Sec. 4.4 with N_iters = desc->opt.iters, Table 1; success and the pick of the
+ * returned trajectory as in Sec. 5.1).
  * seeds_dev [P][S][T][7] initial trajectories; workspace_dev at least
  * dseed_plan_workspace_bytes (256-byte aligned; contents need not be set).
  * Outputs: traj_dev [P][S][T][7] last accepted point of each seed, cost_dev
  * [P][S] its cost, success_dev [P][S] (1 = success), metrics_dev (optional)
  * [P][S][DSEED_N_METRICS], best_dev [P] index of the lowest-cost successful
  * seed (ties -> lowest index), -1 when no seed succeeds.  traj_dev may alias
- * seeds_dev. */
+ * seeds_dev.  EINVAL on a null robot, a bad descriptor, a null problem array
+ * or (P > 0) a null plan buffer, or a workspace not 256-byte aligned; ENOMEM
+ * when workspace_bytes is below the size needed; P = 0 enqueues nothing. */
 int dseed_plan_batch(const DseedRobot *robot, const DseedPlanDesc *desc, const DseedProblems *pr,
                      const float *seeds_dev, void *workspace_dev, size_t workspace_bytes,
                      float *traj_dev, float *cost_dev, uint8_t *success_dev, float *metrics_dev,
