@@ -537,8 +537,8 @@ int dseed_nn_mse(const float *pred_dev, const float *target_dev, const float *w_
  * from the straight path: vector v stands for the joint configuration
  * q(v) = mid + half (lin + v / res_scale) per waypoint and joint, lin_dev
  * [N][T][7] the normalised straight start-goal path, mid and half the centre
- * and half-width of the robot's joint limits.  With c_k(q) the points sampled
- * on the robot's geometry -- for every collision sphere the six points of its
+ * and half-width of the robot's joint limits.  With c_k(q) the points on the
+ * robot's surface -- for every collision sphere the six points of its
  * surface along the axes of its frame, N_p = 6 N_s -- and w_dev [N] optional
  * weights (Eq. 2's 1 + alpha 1(tau); NULL = 1):
  *   loss = sum_n w_n sum_{t,k} |c_k(q(pred_nt)) - c_k(q(eps_nt))|^2 / (N T N_p 3),

@@ -20,8 +20,8 @@ of eps-free DDIM, the descent direction against central differences of the cost
 in the diffused space, the per-entry cap, and the guided-step count of the
 schedule).
 
-Also Eq. 2's loss measured on the robot (fk_mse, Sec. 4.3: points sampled on
-the robot's geometry across all links): the drawn and the predicted noise are
+Also Eq. 2's loss measured on the robot (fk_mse, Sec. 4.3: the error taken on
+points spread over the surface of every link): the drawn and the predicted noise are
 decoded to the joint configurations they stand for, and the points on the
 collision spheres' surfaces at the six axis directions of each sphere's frame
 are placed by a forward-kinematics chain of 4x4 modified-DH products written
