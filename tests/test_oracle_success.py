@@ -17,7 +17,7 @@ import pytest
 
 import oracle
 from paper_2410_16727_gb300 import inputs as I
-from tests.golden.read import read
+from golden.read import read
 
 ROBOT = I.make_robot()
 EMPTY = np.zeros((0, 6), np.float32)
