@@ -984,6 +984,10 @@ def run_reference(args, rank: int, world: int):
     the plans of its seeds, timed, plus its share of its scene's ESDF build
     (the build time, measured once, divided by the problems that share the scene)."""
     import oracle
+    if world > 1:
+        # the launcher gives every rank one OpenMP thread; rank 0 runs alone here
+        # (the other ranks exit without work), so it takes the host's cores
+        oracle.set_num_threads(len(os.sched_getaffinity(0)))
     spec = workload_spec(args, args.workload)
     n_needed = args.warmup + args.steps
     per_scene = max(1, spec.n_problems // spec.n_scenes)
@@ -1027,15 +1031,22 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     res, wl = run_gpu(args, rank, world)
-    if rank == 0 and args.sweep > 0:
+    # the swept check, serving, the learned comparisons and the CPU baseline are
+    # single-GPU measurements: with several ranks only the headline (and the
+    # workloads alongside it) run, so the GPUs are held for the timed work alone
+    single = world == 1
+    if not single:
+        res["sections"] = ("headline and alongside workloads only; the swept check, serving, learned "
+                           "comparisons and CPU baseline are measured at n_gpus = 1")
+    if rank == 0 and single and args.sweep > 0:
         res["sweep"] = run_sweep(args, wl)
-    if not args.no_serving:
+    if single and not args.no_serving:
         res["serving"] = run_serving(args, rank)
-    if rank == 0 and not args.no_learned:
+    if rank == 0 and single and not args.no_learned:
         res["learned"] = run_learned(args)
         if args.workload == "stress" and not args.no_learned_stress:
             res["learned_stress"] = run_learned_stress(args, wl)
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and single and not args.no_cpu_baseline:
         v, desc, cores = oracle_sample(workload_spec(args, args.workload))
         res["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                "cpu_model": host_cpu_model(), "sample": desc}

@@ -7,6 +7,6 @@ path.  See the header of ``dseed_oracle.c`` for what is computed and how each
 part is pinned.
 """
 from .oracle import (  # noqa: F401
-    build, load, Oracle, fk_frames, flange_pose, esdf_build, esdf_lookup, num_threads,
+    build, load, Oracle, fk_frames, flange_pose, esdf_build, esdf_lookup, num_threads, set_num_threads,
     lbfgs_quadratic, success_thresholds,
 )

@@ -97,6 +97,17 @@ int orc_num_threads(void)
 #endif
 }
 
+/* Threads of the calling thread's later parallel loops over seeds (n >= 1);
+ * every seed is planned by one thread, so the results do not depend on it. */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 /* ------------------------------------------------------------------------ */
 /* Small linear algebra on 4x4 homogeneous transforms (row-major)           */
 /* ------------------------------------------------------------------------ */

@@ -82,6 +82,8 @@ def load():
     lib.orc_lbfgs_quadratic.argtypes = [_dp, _dp, C.c_int, C.POINTER(_Opt), _dp, _dp, _dp, _dp]
     lib.orc_lbfgs_quadratic.restype = C.c_int
     lib.orc_num_threads.restype = C.c_int
+    lib.orc_set_num_threads.argtypes = [C.c_int]
+    lib.orc_set_num_threads.restype = None
     lib.orc_self_pairs.argtypes = [C.POINTER(_Robot), _dp, C.c_double, C.POINTER(C.c_ubyte)]
     lib.orc_self_pairs.restype = C.c_int
     _lib = lib
@@ -118,6 +120,11 @@ def success_thresholds() -> np.ndarray:
 
 def num_threads() -> int:
     return int(load().orc_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's later parallel loops over seeds (from this thread)."""
+    load().orc_set_num_threads(int(n))
 
 
 def fk_frames(dh, q) -> np.ndarray:
